@@ -1,0 +1,25 @@
+"""CPU FP64 oracle for the direct domain-decomposition solver.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path imports, calls or
+executes this package; only the tests, `__graft_entry__.smoke()` and the CPU
+baseline leg of `bench.py` do.  It shares no code with the GPU library: its
+only inputs are the seeded problems from `femgen`.
+
+Routes to the same solution x = A^{-1} b of the assembled FEM system:
+  * dense.lu_solve          - dense LU with partial pivoting (tiny systems);
+  * skyline.BandLDLT        - RCM + band-profile LDL^T of the undecomposed system;
+  * dd.DDOracle             - the paper's decomposition route (Section II):
+                              per-domain LDL^T, F = sum B_i A_i^{-1} B_i^T,
+                              F lambda = d, primal recovery;
+  * refine.residual_dd      - double-double residuals for iterative refinement.
+
+Parity status: pinned by closed forms and library special cases (see the
+tests); the paper prints no numerical values, so no value of the paper pins it.
+"""
+from .dense import lu_solve, ldlt, ldlt_solve
+from .skyline import BandLDLT, rcm
+from .dd import DDOracle, subdomain_schur, arrow_residual, local_B
+from .refine import residual_dd, refine, backward_error
+
+__all__ = ["lu_solve", "ldlt", "ldlt_solve", "BandLDLT", "rcm", "DDOracle", "subdomain_schur",
+           "arrow_residual", "local_B", "residual_dd", "refine", "backward_error"]
