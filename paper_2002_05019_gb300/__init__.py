@@ -1,0 +1,258 @@
+"""GB300 direct domain-decomposition solver: Python binding of include/dd.h.
+
+A thin ctypes layer over libdd_gb300.so: it marshals arrays into the C ABI
+(dd_setup / dd_factor / dd_solve / dd_get_schur / dd_get_stats / dd_free) and
+does no arithmetic of its own.  There is no CPU fallback: if the CUDA library
+is missing or no GPU is visible the calls raise.
+
+    from paper_2002_05019_gb300 import Solver
+    s = Solver.from_problem(problem, precision="mixed")
+    s.factor()
+    u, lam = s.solve(f)          # f: (sum n_i, nrhs) complex128, host or CUDA tensor
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "libdd_gb300.so")
+_lib = None
+
+DD_OK = 0
+STATUS = {0: "DD_OK", 1: "DD_ERR_INVALID_ARG", 2: "DD_ERR_NOT_SYMMETRIC", 3: "DD_ERR_SINGULAR_PIVOT",
+          4: "DD_ERR_OOM", 5: "DD_ERR_CUDA", 6: "DD_ERR_NOT_FACTORED", 7: "DD_ERR_NOT_CONVERGED",
+          8: "DD_ERR_TIMEOUT", 9: "DD_ERR_NO_DEVICE"}
+PRECISION = {"fp64": 0, "mixed": 1}
+
+
+class DDError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = _lib.dd_strerror(code).decode() if _lib is not None else STATUS.get(code, "?")
+        super().__init__(f"{where}: {STATUS.get(code, code)} ({msg})")
+
+
+class c128(C.Structure):
+    _fields_ = [("re", C.c_double), ("im", C.c_double)]
+
+
+class Subdomain(C.Structure):
+    _fields_ = [("n", C.c_int32), ("rowptr", C.POINTER(C.c_int32)), ("colind", C.POINTER(C.c_int32)),
+                ("val", C.c_void_p), ("nb", C.c_int32), ("b_dual", C.POINTER(C.c_int32)),
+                ("b_local", C.POINTER(C.c_int32)), ("b_sign", C.POINTER(C.c_int8))]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("refine_tol", C.c_double), ("max_refine", C.c_int32),
+                ("pivoting", C.c_int32), ("tree_parent", C.POINTER(C.c_int32)),
+                ("centroids", C.POINTER(C.c_double)), ("cuda_stream", C.c_void_p), ("device", C.c_int32),
+                ("time_kernels", C.c_int32)]
+
+KERNEL_CLASSES = ["diag", "trsm", "update", "assemble", "init"]
+
+
+class Stats(C.Structure):
+    _fields_ = [("n_sub", C.c_int32), ("n_dual", C.c_int32), ("n_fronts", C.c_int32), ("n_levels", C.c_int32),
+                ("n_primal", C.c_int64), ("max_front", C.c_int32), ("flops_factor", C.c_double),
+                ("flops_solve", C.c_double), ("bytes_factor", C.c_int64), ("bytes_device", C.c_int64),
+                ("t_setup_ms", C.c_double), ("t_factor_ms", C.c_double), ("t_solve_ms", C.c_double),
+                ("growth", C.c_double), ("min_pivot", C.c_double), ("refine_iters", C.c_int32),
+                ("refine_last", C.c_double), ("launches_factor", C.c_int32), ("launches_solve", C.c_int32),
+                ("kernel_ms", C.c_double * 5), ("kernel_launches", C.c_int32 * 5), ("kernel_flops", C.c_double * 5)]
+
+
+EXPORTS = ["dd_default_options", "dd_setup", "dd_set_values", "dd_factor", "dd_solve", "dd_get_schur",
+           "dd_get_stats", "dd_strerror", "dd_free"]
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load(build_if_missing: bool = True):
+    """Load libdd_gb300.so (building it with nvcc first if it is absent or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        from .build import build
+        build()
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"{_LIB_PATH} is missing: build it with paper_2002_05019_gb300.build.build()")
+    lib = C.CDLL(_LIB_PATH)
+    lib.dd_default_options.argtypes = [C.POINTER(Options)]
+    lib.dd_setup.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(Subdomain), C.c_int32, C.POINTER(Options)]
+    lib.dd_set_values.argtypes = [C.c_void_p, C.c_void_p]
+    lib.dd_factor.argtypes = [C.c_void_p]
+    lib.dd_solve.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
+                             C.c_int64]
+    lib.dd_get_schur.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    lib.dd_get_stats.argtypes = [C.c_void_p, C.POINTER(Stats)]
+    lib.dd_strerror.argtypes = [C.c_int]
+    lib.dd_strerror.restype = C.c_char_p
+    lib.dd_free.argtypes = [C.c_void_p]
+    lib.dd_free.restype = None
+    _lib = lib
+    return lib
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def _check(code: int, where: str, ok=(DD_OK,)):
+    if code not in ok:
+        raise DDError(code, where)
+    return code
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+class Solver:
+    """One factorization of an arrowhead system on one GPU."""
+
+    def __init__(self, subdomains, n_dual: int, precision: str = "fp64", refine_tol: float = 1e-13,
+                 max_refine: int | None = None, tree_parent=None, centroids=None, stream=None, device: int = 0,
+                 time_kernels: bool = False):
+        lib = load()
+        self._keep = []
+        subs = (Subdomain * len(subdomains))()
+        self.n = [int(s["n"]) for s in subdomains]
+        self.n_loc = int(sum(self.n))
+        self.n_dual = int(n_dual)
+        self.nnz = []
+        for k, s in enumerate(subdomains):
+            rp = np.ascontiguousarray(s["indptr"], dtype=np.int32)
+            ci = np.ascontiguousarray(s["indices"], dtype=np.int32)
+            va = np.ascontiguousarray(s["data"], dtype=np.complex128)
+            bd = np.ascontiguousarray(s["b_dual"], dtype=np.int32)
+            bl = np.ascontiguousarray(s["b_local"], dtype=np.int32)
+            bs = np.ascontiguousarray(s["b_sign"], dtype=np.int8)
+            self._keep += [rp, ci, va, bd, bl, bs]
+            subs[k] = Subdomain(int(s["n"]), _ptr(rp, C.c_int32), _ptr(ci, C.c_int32), va.ctypes.data, bd.size,
+                                _ptr(bd, C.c_int32), _ptr(bl, C.c_int32), _ptr(bs, C.c_int8))
+            self.nnz.append(int(ci.size))
+        opt = Options()
+        lib.dd_default_options(C.byref(opt))
+        opt.precision = PRECISION[precision]
+        opt.refine_tol = refine_tol
+        if max_refine is not None:
+            opt.max_refine = int(max_refine)
+        if tree_parent is not None:
+            tp = np.ascontiguousarray(tree_parent, dtype=np.int32)
+            self._keep.append(tp)
+            opt.tree_parent = _ptr(tp, C.c_int32)
+        if centroids is not None:
+            ce = np.ascontiguousarray(centroids, dtype=np.float64).ravel()
+            self._keep.append(ce)
+            opt.centroids = _ptr(ce, C.c_double)
+        if stream is not None:
+            opt.cuda_stream = C.c_void_p(int(stream))
+        opt.device = device
+        opt.time_kernels = 1 if time_kernels else 0
+        self.precision = precision
+        h = C.c_void_p()
+        _check(lib.dd_setup(C.byref(h), len(subdomains), subs, self.n_dual, C.byref(opt)), "dd_setup")
+        self._h = h
+        self._keep = []   # dd_setup deep-copied every input
+
+    @classmethod
+    def from_problem(cls, p, **kw):
+        """Build from a femgen.Problem (domain CSRs, B entries and the domain tree)."""
+        subs = [dict(n=s.n, indptr=s.indptr, indices=s.indices, data=s.data, b_dual=s.b_dual,
+                     b_local=s.b_local, b_sign=s.b_sign) for s in p.subs]
+        kw.setdefault("tree_parent", p.rcb.parent)
+        return cls(subs, p.n_dual, **kw)
+
+    def set_values(self, vals):
+        """New values for every A_i (same patterns), domain after domain: host array or CUDA tensor."""
+        if _is_torch(vals):
+            _check(_lib.dd_set_values(self._h, C.c_void_p(vals.data_ptr())), "dd_set_values")
+        else:
+            v = np.ascontiguousarray(vals, dtype=np.complex128)
+            _check(_lib.dd_set_values(self._h, C.c_void_p(v.ctypes.data)), "dd_set_values")
+
+    def factor(self):
+        _check(_lib.dd_factor(self._h), "dd_factor")
+
+    def solve(self, f, allow_not_converged: bool = False):
+        """Solve for the stacked local loads f (n_loc x nrhs, column-major).
+
+        numpy in -> numpy out; a CUDA torch tensor in -> CUDA tensors out.
+        Returns (u, lambda).
+        """
+        ok = (DD_OK, 7) if allow_not_converged else (DD_OK,)
+        if _is_torch(f):
+            import torch
+            ff = f if f.dim() == 2 else f[:, None]
+            nrhs = ff.shape[1]
+            ft = ff.t().contiguous()                  # (nrhs, n_loc): column-major f
+            ut = torch.empty((nrhs, self.n_loc), dtype=torch.complex128, device=f.device)
+            lt = torch.empty((nrhs, max(self.n_dual, 1)), dtype=torch.complex128, device=f.device)
+            code = _lib.dd_solve(self._h, nrhs, C.c_void_p(ft.data_ptr()), self.n_loc, C.c_void_p(ut.data_ptr()),
+                                 self.n_loc, C.c_void_p(lt.data_ptr()) if self.n_dual else None,
+                                 max(self.n_dual, 1))
+            _check(code, "dd_solve", ok)
+            self.last_status = code
+            uo, lo = ut.t(), lt[:, :self.n_dual].t()
+            return (uo[:, 0], lo[:, 0]) if f.dim() == 1 else (uo, lo)
+        fa = np.asarray(f, dtype=np.complex128)
+        vec = fa.ndim == 1
+        fa = np.asfortranarray(fa[:, None] if vec else fa)
+        nrhs = fa.shape[1]
+        uo = np.zeros((self.n_loc, nrhs), dtype=np.complex128, order="F")
+        lo = np.zeros((self.n_dual, nrhs), dtype=np.complex128, order="F")
+        code = _lib.dd_solve(self._h, nrhs, C.c_void_p(fa.ctypes.data), self.n_loc, C.c_void_p(uo.ctypes.data),
+                             self.n_loc, C.c_void_p(lo.ctypes.data) if self.n_dual else None, max(self.n_dual, 1))
+        _check(code, "dd_solve", ok)
+        self.last_status = code
+        return (uo[:, 0], lo[:, 0]) if vec else (uo, lo)
+
+    def schur(self, i: int):
+        """F_i = B_i A_i^{-1} B_i^T of domain i (m_i x m_i) and its ascending dual ids."""
+        m = C.c_int32()
+        _check(_lib.dd_get_schur(self._h, i, None, None, C.byref(m)), "dd_get_schur")
+        out = np.zeros((m.value, m.value), dtype=np.complex128, order="F")
+        duals = np.zeros(m.value, dtype=np.int32)
+        _check(_lib.dd_get_schur(self._h, i, C.c_void_p(out.ctypes.data), _ptr(duals, C.c_int32), C.byref(m)),
+               "dd_get_schur")
+        return out, duals
+
+    def stats(self) -> dict:
+        st = Stats()
+        _check(_lib.dd_get_stats(self._h, C.byref(st)), "dd_get_stats")
+        out = {}
+        for name, _ in Stats._fields_:
+            v = getattr(st, name)
+            out[name] = dict(zip(KERNEL_CLASSES, list(v))) if name.startswith("kernel_") else v
+        return out
+
+    def free(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.dd_free(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def stacked_loads(problem) -> np.ndarray:
+    """The local loads f_i of a femgen.Problem stacked domain after domain: (n_loc, nrhs)."""
+    return np.concatenate([s.f for s in problem.subs], axis=0)
+
+
+def unstack(problem, u: np.ndarray):
+    """Split a stacked (n_loc, nrhs) array back into per-domain blocks."""
+    offs = np.cumsum([0] + [s.n for s in problem.subs])
+    return [u[offs[k]:offs[k + 1]] for k in range(problem.n_sub)]
+
+
+__all__ = ["Solver", "DDError", "load", "library_path", "stacked_loads", "unstack", "EXPORTS", "PRECISION"]

@@ -1,0 +1,941 @@
+// Host side of the GB300 direct domain-decomposition solver: the C ABI of
+// include/dd.h, input validation, the symbolic analysis of the arrowhead
+// system, device memory, and the launch schedule of factor and solve.
+//
+// Symbolic analysis (Section II, "symbolic factorization step ... attributed
+// clique graph of the block-wise sparse matrix"):
+//   * each domain's unknowns are ordered interior first, interface last, so
+//     that the rows of B_i only meet the last n_Gamma columns of L_i;
+//   * every domain is a clique over the duals it touches; a dual coupling a set
+//     of domains is eliminated at the lowest common ancestor of those domains in
+//     the binary domain tree (a nested-dissection order of the dual unknowns:
+//     separators after their subtrees);
+//   * the front of a tree node holds its separator duals followed by the
+//     ancestor duals reached through its subtree's cliques; that structure is
+//     the block fill of the auxiliary factor.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <vector>
+
+#include "../../include/dd.h"
+#include "dd_internal.h"
+
+namespace {
+
+constexpr int T = DD_TILE;
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+struct StepRange {
+  int k;
+  int64_t diag_off, trsm_off, upd_off;
+  int n_diag, n_trsm, n_upd;
+};
+
+struct Level {
+  std::vector<int32_t> ids;       // fronts in this level
+  int64_t ids_off = 0;            // offset into d_level_ids
+  std::vector<StepRange> steps;   // factor schedule
+  int max_child_nu = 0;
+};
+
+struct DeviceArena {
+  std::vector<void*> ptrs;
+  size_t bytes = 0;
+  template <typename X>
+  cudaError_t alloc(X** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return cudaSuccess;
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(X));
+    if (e != cudaSuccess) return e;
+    ptrs.push_back(q);
+    bytes += count * sizeof(X);
+    *p = static_cast<X*>(q);
+    return cudaSuccess;
+  }
+  template <typename X>
+  cudaError_t upload(X** p, const std::vector<X>& v, cudaStream_t s) {
+    cudaError_t e = alloc(p, v.size());
+    if (e != cudaSuccess || v.empty()) return e;
+    return cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice, s);
+  }
+  void release() {
+    for (void* q : ptrs) cudaFree(q);
+    ptrs.clear();
+    bytes = 0;
+  }
+};
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct dd_handle {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int prec = DD_PREC_FP64;
+  double refine_tol = 1e-13;
+  int max_refine = 0;
+  int n_sub = 0, n_dual = 0;
+  int64_t n_loc = 0, nnz_total = 0;
+  size_t elem = 16;  // bytes per stored complex
+
+  // symbolic
+  std::vector<FrontDev> fronts;
+  std::vector<Level> levels;
+  std::vector<std::vector<int32_t>> leaf_duals;  // sorted duals of each domain
+  std::vector<int64_t> leaf_vec_off;
+  double max_abs_a = 1.0;
+  int64_t rows_total = 0;  // sum of front orders (right-hand-side rows)
+
+  // device
+  DeviceArena arena;
+  void* pool = nullptr;
+  size_t pool_bytes = 0;
+  FrontDev* d_fronts = nullptr;
+  LeafDev* d_leaves = nullptr;
+  int32_t *d_rowptr = nullptr, *d_colind = nullptr;
+  double2* d_val = nullptr;
+  int32_t *d_iperm = nullptr, *d_perm = nullptr;
+  int32_t *d_brow = nullptr, *d_blocal = nullptr;
+  int8_t* d_bsign = nullptr;
+  int32_t *d_blptr = nullptr, *d_bldual = nullptr;
+  int8_t* d_blsign = nullptr;
+  int32_t* d_btptr = nullptr;
+  int64_t* d_btrow = nullptr;
+  int8_t* d_btsign = nullptr;
+  int32_t *d_upd = nullptr, *d_sep = nullptr, *d_maps = nullptr;
+  int32_t *d_level_ids = nullptr, *d_diag_ids = nullptr;
+  Task *d_trsm = nullptr, *d_updt = nullptr;
+  DevStatus* d_status = nullptr;
+  double* d_partials = nullptr;
+
+  // solve work (grown on demand, freed with the handle)
+  int nrhs_cap = 0;
+  void* rpool = nullptr;
+  void* lam_work = nullptr;
+  double2 *d_f = nullptr, *d_u = nullptr, *d_r = nullptr, *d_du = nullptr;
+  double2 *d_lam = nullptr, *d_dlam = nullptr, *d_g = nullptr;
+  std::vector<void*> work_ptrs;
+
+  bool factored = false;
+  int time_kernels = 0;
+  std::vector<cudaEvent_t> kev;   // event pairs for per-launch timing
+  dd_stats stats{};
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  int launches = 0;
+
+  ~dd_handle() {
+    for (void* q : work_ptrs) cudaFree(q);
+    arena.release();
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    for (cudaEvent_t e : kev) cudaEventDestroy(e);
+  }
+};
+
+namespace {
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return DD_OK;
+  if (e == cudaErrorMemoryAllocation) return DD_ERR_OOM;
+  return DD_ERR_CUDA;
+}
+
+#define DD_CUDA(call)                          \
+  do {                                         \
+    cudaError_t _e = (call);                   \
+    if (_e != cudaSuccess) return cuda_status(_e); \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// validation
+// ---------------------------------------------------------------------------
+int validate_subdomain(const dd_subdomain& s, int32_t n_dual, double* max_abs) {
+  if (s.n < 1 || !s.rowptr || s.nb < 0) return DD_ERR_INVALID_ARG;
+  if (s.rowptr[0] != 0) return DD_ERR_INVALID_ARG;
+  const int64_t nnz = s.rowptr[s.n];
+  if (nnz < 0 || (nnz > 0 && (!s.colind || !s.val))) return DD_ERR_INVALID_ARG;
+  if (s.nb > 0 && (!s.b_dual || !s.b_local || !s.b_sign)) return DD_ERR_INVALID_ARG;
+  double amax = 0.0;
+  for (int r = 0; r < s.n; ++r) {
+    if (s.rowptr[r + 1] < s.rowptr[r]) return DD_ERR_INVALID_ARG;
+    bool diag = false;
+    for (int32_t q = s.rowptr[r]; q < s.rowptr[r + 1]; ++q) {
+      const int32_t c = s.colind[q];
+      if (c < 0 || c >= s.n) return DD_ERR_INVALID_ARG;
+      if (q > s.rowptr[r] && c <= s.colind[q - 1]) return DD_ERR_INVALID_ARG;
+      if (!std::isfinite(s.val[q].re) || !std::isfinite(s.val[q].im)) return DD_ERR_INVALID_ARG;
+      amax = std::max(amax, std::hypot(s.val[q].re, s.val[q].im));
+      diag |= (c == r);
+    }
+    if (!diag) return DD_ERR_INVALID_ARG;  // every diagonal entry must be stored
+  }
+  // symmetry A = A^T (pattern and values, relative 1e-12)
+  for (int r = 0; r < s.n; ++r) {
+    for (int32_t q = s.rowptr[r]; q < s.rowptr[r + 1]; ++q) {
+      const int32_t c = s.colind[q];
+      const int32_t* b = s.colind + s.rowptr[c];
+      const int32_t* e = s.colind + s.rowptr[c + 1];
+      const int32_t* it = std::lower_bound(b, e, r);
+      if (it == e || *it != r) return DD_ERR_NOT_SYMMETRIC;
+      const dd_c128 v = s.val[q], w = s.val[s.rowptr[c] + (it - b)];
+      if (std::hypot(v.re - w.re, v.im - w.im) > 1e-12 * amax) return DD_ERR_NOT_SYMMETRIC;
+    }
+  }
+  for (int q = 0; q < s.nb; ++q) {
+    if (s.b_dual[q] < 0 || s.b_dual[q] >= n_dual) return DD_ERR_INVALID_ARG;
+    if (s.b_local[q] < 0 || s.b_local[q] >= s.n) return DD_ERR_INVALID_ARG;
+    if (s.b_sign[q] != 1 && s.b_sign[q] != -1) return DD_ERR_INVALID_ARG;
+  }
+  *max_abs = amax;
+  return DD_OK;
+}
+
+// binary domain tree: parent[] over 2*ns-1 nodes, leaves 0..ns-1
+int build_tree(int ns, const dd_options* opt, std::vector<int32_t>& parent) {
+  const int nn = 2 * ns - 1;
+  parent.assign(nn, -1);
+  if (opt && opt->tree_parent) {
+    std::vector<int> nchild(nn, 0);
+    for (int x = 0; x < nn; ++x) {
+      const int p = opt->tree_parent[x];
+      if (x == nn - 1) {
+        if (p != -1) return DD_ERR_INVALID_ARG;
+        continue;
+      }
+      if (p <= x || p < ns || p >= nn) return DD_ERR_INVALID_ARG;
+      nchild[p]++;
+      parent[x] = p;
+    }
+    for (int x = ns; x < nn; ++x)
+      if (nchild[x] != 2) return DD_ERR_INVALID_ARG;
+    return DD_OK;
+  }
+  // recursive bisection of the domain centroids (longest extent, median split),
+  // or of the index range when no centroids are given; ids in post-order
+  int next = ns;
+  std::vector<int32_t> ids(ns);
+  std::iota(ids.begin(), ids.end(), 0);
+  const double* cen = opt ? opt->centroids : nullptr;
+  struct Rec {
+    static int go(std::vector<int32_t>& v, int lo, int hi, const double* cen, int& next, std::vector<int32_t>& par) {
+      if (hi - lo == 1) return v[lo];
+      if (cen) {
+        double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300};
+        for (int q = lo; q < hi; ++q)
+          for (int a = 0; a < 3; ++a) {
+            mn[a] = std::min(mn[a], cen[3 * v[q] + a]);
+            mx[a] = std::max(mx[a], cen[3 * v[q] + a]);
+          }
+        int ax = 0;
+        for (int a = 1; a < 3; ++a)
+          if (mx[a] - mn[a] > mx[ax] - mn[ax]) ax = a;
+        std::stable_sort(v.begin() + lo, v.begin() + hi, [&](int32_t x, int32_t y) {
+          return cen[3 * x + ax] < cen[3 * y + ax] || (cen[3 * x + ax] == cen[3 * y + ax] && x < y);
+        });
+      }
+      const int mid = lo + (hi - lo) / 2;
+      const int a = go(v, lo, mid, cen, next, par);
+      const int b = go(v, mid, hi, cen, next, par);
+      const int me = next++;
+      par[a] = me;
+      par[b] = me;
+      return me;
+    }
+  };
+  if (ns > 1) Rec::go(ids, 0, ns, cen, next, parent);
+  return DD_OK;
+}
+
+void add_flops(dd_handle* h, double ne, double nu, double n_gamma, bool leaf) {
+  if (leaf) {
+    h->stats.flops_factor += (4.0 / 3.0) * ne * ne * ne + 4.0 * n_gamma * n_gamma * nu + 4.0 * n_gamma * nu * nu;
+  } else {
+    h->stats.flops_factor += (4.0 / 3.0) * ne * ne * ne + 4.0 * ne * ne * nu + 4.0 * ne * nu * nu;
+  }
+  h->stats.flops_solve += 8.0 * (ne * ne + 2.0 * ne * nu);
+}
+
+int ensure_work(dd_handle* h, int nrhs) {
+  if (nrhs <= h->nrhs_cap) return DD_OK;
+  for (void* q : h->work_ptrs) cudaFree(q);
+  h->work_ptrs.clear();
+  h->nrhs_cap = 0;
+  auto get = [&](void** p, size_t bytes) -> cudaError_t {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) h->work_ptrs.push_back(*p);
+    return e;
+  };
+  const size_t nr = (size_t)nrhs;
+  DD_CUDA(get(&h->rpool, (size_t)h->rows_total * nr * h->elem));
+  DD_CUDA(get(&h->lam_work, (size_t)h->n_dual * nr * h->elem));
+  DD_CUDA(get((void**)&h->d_f, (size_t)h->n_loc * nr * 16));
+  DD_CUDA(get((void**)&h->d_u, (size_t)h->n_loc * nr * 16));
+  DD_CUDA(get((void**)&h->d_r, (size_t)h->n_loc * nr * 16));
+  DD_CUDA(get((void**)&h->d_du, (size_t)h->n_loc * nr * 16));
+  DD_CUDA(get((void**)&h->d_lam, (size_t)h->n_dual * nr * 16));
+  DD_CUDA(get((void**)&h->d_dlam, (size_t)h->n_dual * nr * 16));
+  DD_CUDA(get((void**)&h->d_g, (size_t)h->n_dual * nr * 16));
+  h->nrhs_cap = nrhs;
+  return DD_OK;
+}
+
+// one direct solve with the stored factors: (f [n_loc x nrhs], g [n_dual x nrhs] or NULL)
+// -> (u, lam) in FP64 (assign)
+void direct_solve(dd_handle* h, int nrhs, const double2* f, int64_t ldf, const double2* g, double2* u, double2* lam) {
+  cudaStream_t s = h->stream;
+  const int p = h->prec == DD_PREC_FP64 ? 0 : 1;
+  const Level& L0 = h->levels[0];
+  ddk::launch_rhs_leaf(p, h->rpool, h->d_fronts, h->d_leaves, h->n_sub, h->d_perm, f, ldf, nrhs, s);
+  ddk::launch_forward(p, h->pool, h->rpool, h->d_fronts, h->d_level_ids + L0.ids_off, (int)L0.ids.size(), nrhs, s);
+  h->launches += 2;
+  for (size_t l = 1; l < h->levels.size(); ++l) {
+    const Level& L = h->levels[l];
+    const int32_t* ids = h->d_level_ids + L.ids_off;
+    const int n = (int)L.ids.size();
+    ddk::launch_rhs_node(p, h->rpool, h->d_fronts, ids, n, h->d_sep, g, h->n_dual, nrhs, s);
+    ddk::launch_rhs_extend_add(p, h->rpool, h->d_fronts, ids, n, 0, h->d_maps, nrhs, s);
+    ddk::launch_rhs_extend_add(p, h->rpool, h->d_fronts, ids, n, 1, h->d_maps, nrhs, s);
+    ddk::launch_forward(p, h->pool, h->rpool, h->d_fronts, ids, n, nrhs, s);
+    h->launches += 4;
+  }
+  for (size_t l = h->levels.size(); l-- > 0;) {
+    const Level& L = h->levels[l];
+    ddk::launch_backward(p, h->pool, h->rpool, h->d_fronts, h->d_level_ids + L.ids_off, (int)L.ids.size(), nrhs,
+                         h->d_upd, h->d_sep, h->lam_work, h->n_dual, s);
+    h->launches += 1;
+  }
+  ddk::launch_leaf_out(p, h->rpool, h->d_fronts, h->d_leaves, h->n_sub, h->d_perm, u, h->n_loc, nrhs, 0, s);
+  ddk::launch_lam_out(p, h->lam_work, h->n_dual, h->n_dual, nrhs, lam, h->n_dual, 0, s);
+  h->launches += 2;
+}
+
+__global__ void k_axpy(double2* y, const double2* x, int64_t n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    y[e].x += x[e].x;
+    y[e].y += x[e].y;
+  }
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* dd_strerror(int code) {
+  switch (code) {
+    case DD_OK: return "ok";
+    case DD_ERR_INVALID_ARG: return "invalid argument";
+    case DD_ERR_NOT_SYMMETRIC: return "domain matrix is not symmetric";
+    case DD_ERR_SINGULAR_PIVOT: return "zero or non-finite pivot";
+    case DD_ERR_OOM: return "out of memory";
+    case DD_ERR_CUDA: return "CUDA runtime error";
+    case DD_ERR_NOT_FACTORED: return "handle is not factored";
+    case DD_ERR_NOT_CONVERGED: return "iterative refinement did not converge";
+    case DD_ERR_TIMEOUT: return "device wait timed out";
+    case DD_ERR_NO_DEVICE: return "no CUDA device";
+    default: return "unknown status";
+  }
+}
+
+int dd_default_options(dd_options* opt) {
+  if (!opt) return DD_ERR_INVALID_ARG;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->precision = DD_PREC_FP64;
+  opt->refine_tol = 1e-13;
+  opt->max_refine = 0;
+  opt->pivoting = 0;
+  return DD_OK;
+}
+
+void dd_free(dd_handle* h) {
+  if (!h) return;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->device);
+  delete h;
+  cudaSetDevice(cur);
+}
+
+int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n_dual, const dd_options* opt_in) {
+  if (!out) return DD_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n_sub < 1 || n_dual < 0 || !subs) return DD_ERR_INVALID_ARG;
+  dd_options opt;
+  dd_default_options(&opt);
+  if (opt_in) opt = *opt_in;
+  if (opt.precision != DD_PREC_FP64 && opt.precision != DD_PREC_MIXED) return DD_ERR_INVALID_ARG;
+  if (opt.pivoting != 0 || opt.max_refine < 0 || !(opt.refine_tol >= 0)) return DD_ERR_INVALID_ARG;
+  if (opt.device < 0) return DD_ERR_INVALID_ARG;
+
+  double amax = 0.0;
+  for (int i = 0; i < n_sub; ++i) {
+    double a = 0.0;
+    const int st = validate_subdomain(subs[i], n_dual, &a);
+    if (st != DD_OK) return st;
+    amax = std::max(amax, a);
+  }
+
+  std::unique_ptr<dd_handle> h(new dd_handle());
+  h->device = opt.device;
+  h->stream = (cudaStream_t)opt.cuda_stream;
+  h->prec = opt.precision;
+  h->refine_tol = opt.refine_tol > 0 ? opt.refine_tol : 1e-13;
+  h->max_refine = opt.precision == DD_PREC_MIXED ? (opt.max_refine > 0 ? opt.max_refine : 10) : opt.max_refine;
+  h->n_sub = n_sub;
+  h->n_dual = n_dual;
+  h->elem = opt.precision == DD_PREC_FP64 ? 16 : 8;
+  h->time_kernels = opt.time_kernels ? 1 : 0;
+  h->max_abs_a = std::max(amax, 1.0);
+  cudaStream_t s = h->stream;
+
+  // ---- tree and dual placement ---------------------------------------------
+  std::vector<int32_t> parent;
+  int st = build_tree(n_sub, &opt, parent);
+  if (st != DD_OK) return st;
+  const int n_tree = 2 * n_sub - 1;
+  // a lone domain with duals gets a root above it
+  const bool extra_root = (n_sub == 1 && n_dual > 0);
+  const int n_nodes = n_sub - 1 + (extra_root ? 1 : 0);
+  const int n_front = n_sub + n_nodes;
+  std::vector<int32_t> par(n_front, -1);
+  for (int x = 0; x < n_tree; ++x) par[x] = parent[x];
+  if (extra_root) par[0] = 1;
+  std::vector<int> depth(n_front, 0);
+  for (int x = n_front - 1; x >= 0; --x) depth[x] = par[x] < 0 ? 0 : depth[par[x]] + 1;
+  auto lca = [&](int a, int b) {
+    while (a != b) {
+      if (depth[a] >= depth[b]) a = par[a];
+      else b = par[b];
+    }
+    return a;
+  };
+  std::vector<int32_t> dual_node(n_dual, -1);
+  std::vector<int32_t> dual_first(n_dual, -1);
+  std::vector<int32_t> dual_count(n_dual, 0);
+  for (int i = 0; i < n_sub; ++i)
+    for (int q = 0; q < subs[i].nb; ++q) {
+      const int d = subs[i].b_dual[q];
+      dual_count[d]++;
+      dual_node[d] = dual_node[d] < 0 ? i : lca(dual_node[d], i);
+    }
+  for (int d = 0; d < n_dual; ++d) {
+    if (dual_node[d] < 0) return DD_ERR_INVALID_ARG;  // a dual with no B entry makes F singular
+    if (dual_node[d] < n_sub) dual_node[d] = par[dual_node[d]];  // touches one domain only
+    if (dual_node[d] < 0) return DD_ERR_INVALID_ARG;
+  }
+
+  // ---- leaf structures --------------------------------------------------------
+  h->fronts.assign(n_front, FrontDev{});
+  std::vector<int32_t> h_rowptr, h_colind, h_iperm, h_perm, h_brow, h_blocal, h_blptr, h_bldual;
+  std::vector<int8_t> h_bsign, h_blsign;
+  std::vector<double2> h_val;
+  std::vector<LeafDev> h_leaves(n_sub);
+  std::vector<int32_t> h_upd, h_sep, h_maps;
+  h->leaf_duals.resize(n_sub);
+  h->leaf_vec_off.resize(n_sub);
+  int64_t vec_off = 0, csr_off = 0;
+  int32_t rp_off = 0, b_off = 0;
+  for (int i = 0; i < n_sub; ++i) {
+    const dd_subdomain& sd = subs[i];
+    std::vector<char> is_if(sd.n, 0);
+    for (int q = 0; q < sd.nb; ++q) is_if[sd.b_local[q]] = 1;
+    std::vector<int32_t> perm;
+    perm.reserve(sd.n);
+    for (int r = 0; r < sd.n; ++r)
+      if (!is_if[r]) perm.push_back(r);
+    const int n_int = (int)perm.size();
+    for (int r = 0; r < sd.n; ++r)
+      if (is_if[r]) perm.push_back(r);
+    std::vector<int32_t> iperm(sd.n);
+    for (int r = 0; r < sd.n; ++r) iperm[perm[r]] = r;
+    std::vector<int32_t> duals(sd.b_dual, sd.b_dual + sd.nb);
+    std::sort(duals.begin(), duals.end());
+    duals.erase(std::unique(duals.begin(), duals.end()), duals.end());
+    h->leaf_duals[i] = duals;
+
+    LeafDev L{};
+    L.csr_off = csr_off;
+    L.vec_off = vec_off;
+    L.rowptr_off = rp_off;
+    L.n = sd.n;
+    L.perm_off = (int32_t)h_perm.size();
+    L.b_off = b_off;
+    L.nb = sd.nb;
+    L.front = i;
+    h_leaves[i] = L;
+    h->leaf_vec_off[i] = vec_off;
+
+    FrontDev& F = h->fronts[i];
+    F.kind = 0;
+    F.sub = i;
+    F.ne = sd.n;
+    F.ne_pad = (int32_t)round_up(sd.n, T);
+    F.nu = (int32_t)duals.size();
+    F.ld = F.ne_pad + (int32_t)round_up(F.nu, T);
+    F.n_int = n_int;
+    F.upd_off = (int32_t)h_upd.size();
+    F.sep_off = 0;
+    F.child[0] = F.child[1] = -1;
+    h_upd.insert(h_upd.end(), duals.begin(), duals.end());
+
+    const int nnz = sd.rowptr[sd.n];
+    h_rowptr.insert(h_rowptr.end(), sd.rowptr, sd.rowptr + sd.n + 1);
+    h_colind.insert(h_colind.end(), sd.colind, sd.colind + nnz);
+    for (int q = 0; q < nnz; ++q) h_val.push_back(make_double2(sd.val[q].re, sd.val[q].im));
+    h_perm.insert(h_perm.end(), perm.begin(), perm.end());
+    h_iperm.insert(h_iperm.end(), iperm.begin(), iperm.end());
+    for (int q = 0; q < sd.nb; ++q) {
+      h_brow.push_back((int32_t)(std::lower_bound(duals.begin(), duals.end(), sd.b_dual[q]) - duals.begin()));
+      h_blocal.push_back(sd.b_local[q]);
+      h_bsign.push_back(sd.b_sign[q]);
+    }
+    // B entries sorted by local row (FP64 residual)
+    std::vector<int32_t> ord(sd.nb);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return sd.b_local[a] < sd.b_local[b]; });
+    std::vector<int32_t> cnt(sd.n + 1, 0);
+    for (int q = 0; q < sd.nb; ++q) cnt[sd.b_local[q] + 1]++;
+    for (int r = 0; r < sd.n; ++r) cnt[r + 1] += cnt[r];
+    h_blptr.insert(h_blptr.end(), cnt.begin(), cnt.end());
+    for (int q : ord) {
+      h_bldual.push_back(sd.b_dual[q]);
+      h_blsign.push_back(sd.b_sign[q]);
+    }
+    vec_off += sd.n;
+    csr_off += nnz;
+    rp_off += sd.n + 1;
+    b_off += sd.nb;
+    const double ng = (double)(sd.n - n_int);
+    add_flops(h.get(), sd.n, F.nu, ng, true);
+  }
+  h->n_loc = vec_off;
+  h->nnz_total = csr_off;
+
+  // dual -> (stacked row, sign) in fixed order (FP64 residual of B u)
+  std::vector<int32_t> h_btptr(n_dual + 1, 0);
+  for (int i = 0; i < n_sub; ++i)
+    for (int q = 0; q < subs[i].nb; ++q) h_btptr[subs[i].b_dual[q] + 1]++;
+  for (int d = 0; d < n_dual; ++d) h_btptr[d + 1] += h_btptr[d];
+  std::vector<int64_t> h_btrow(h_btptr[n_dual]);
+  std::vector<int8_t> h_btsign(h_btptr[n_dual]);
+  {
+    std::vector<int32_t> fill(h_btptr.begin(), h_btptr.end() - 1);
+    for (int i = 0; i < n_sub; ++i)
+      for (int q = 0; q < subs[i].nb; ++q) {
+        const int d = subs[i].b_dual[q];
+        h_btrow[fill[d]] = h->leaf_vec_off[i] + subs[i].b_local[q];
+        h_btsign[fill[d]] = subs[i].b_sign[q];
+        fill[d]++;
+      }
+  }
+
+  // ---- node fronts (post-order: children before parents) ----------------------
+  std::vector<std::vector<int32_t>> sep(n_front), upd(n_front);
+  for (int d = 0; d < n_dual; ++d) sep[dual_node[d]].push_back(d);
+  for (int i = 0; i < n_sub; ++i) upd[i] = h->leaf_duals[i];
+  std::vector<std::vector<int32_t>> children(n_front);
+  for (int x = 0; x < n_front; ++x)
+    if (par[x] >= 0) children[par[x]].push_back(x);
+  std::vector<int> height(n_front, 0);
+  for (int v = n_sub; v < n_front; ++v) {
+    FrontDev& F = h->fronts[v];
+    F.kind = 1;
+    F.sub = -1;
+    std::vector<int32_t> all;
+    for (int c : children[v]) all.insert(all.end(), upd[c].begin(), upd[c].end());
+    std::sort(all.begin(), all.end());
+    all.erase(std::unique(all.begin(), all.end()), all.end());
+    std::vector<int32_t>& sp = sep[v];  // already sorted (increasing d)
+    std::vector<int32_t> up;
+    for (int d : all)
+      if (dual_node[d] != v) up.push_back(d);
+    // every separator dual must be reachable from below
+    for (int d : sp)
+      if (!std::binary_search(all.begin(), all.end(), d)) return DD_ERR_INVALID_ARG;
+    upd[v] = up;
+    F.ne = (int32_t)sp.size();
+    F.ne_pad = (int32_t)round_up(F.ne, T);
+    F.nu = (int32_t)up.size();
+    F.ld = F.ne_pad + (int32_t)round_up(F.nu, T);
+    F.n_int = 0;
+    F.upd_off = (int32_t)h_upd.size();
+    h_upd.insert(h_upd.end(), up.begin(), up.end());
+    F.sep_off = (int32_t)h_sep.size();
+    h_sep.insert(h_sep.end(), sp.begin(), sp.end());
+    F.child[0] = F.child[1] = -1;
+    int hgt = 0;
+    for (size_t slot = 0; slot < children[v].size() && slot < 2; ++slot) {
+      const int c = children[v][slot];
+      F.child[slot] = c;
+      F.map_off[slot] = (int32_t)h_maps.size();
+      for (int d : upd[c]) {
+        int row;
+        if (dual_node[d] == v) row = (int)(std::lower_bound(sp.begin(), sp.end(), d) - sp.begin());
+        else row = F.ne_pad + (int)(std::lower_bound(up.begin(), up.end(), d) - up.begin());
+        h_maps.push_back(row);
+      }
+      hgt = std::max(hgt, height[c] + 1);
+    }
+    height[v] = hgt;
+    if (par[v] < 0 && F.nu != 0) return DD_ERR_INVALID_ARG;
+    add_flops(h.get(), F.ne, F.nu, 0, false);
+    h->stats.max_front = std::max(h->stats.max_front, F.ld);
+  }
+
+  // ---- offsets, levels, task lists ----------------------------------------------
+  int64_t off = 0, roff = 0;
+  int64_t bytes_factor = 0;
+  for (int x = 0; x < n_front; ++x) {
+    FrontDev& F = h->fronts[x];
+    F.off = off;
+    F.roff = roff;
+    off += (int64_t)F.ld * F.ld;
+    roff += F.ld;
+    bytes_factor += ((int64_t)F.ne_pad * (F.ne_pad + 1) / 2 + (int64_t)F.ne_pad * (F.ld - F.ne_pad)) * (int64_t)h->elem;
+  }
+  h->pool_bytes = (size_t)off * h->elem;
+  h->rows_total = roff;
+  int max_h = 0;
+  for (int x = 0; x < n_front; ++x) max_h = std::max(max_h, height[x]);
+  h->levels.assign(max_h + 1, Level{});
+  for (int x = 0; x < n_front; ++x)
+    if (h->fronts[x].ld > 0 || x < n_sub) h->levels[height[x]].ids.push_back(x);
+  std::vector<int32_t> h_level_ids, h_diag;
+  std::vector<Task> h_trsm, h_updt;
+  for (auto& L : h->levels) {
+    L.ids_off = (int64_t)h_level_ids.size();
+    h_level_ids.insert(h_level_ids.end(), L.ids.begin(), L.ids.end());
+    int max_steps = 0;
+    for (int f : L.ids) {
+      max_steps = std::max(max_steps, h->fronts[f].ne_pad / T);
+      for (int slot = 0; slot < 2; ++slot) {
+        const int c = h->fronts[f].child[slot];
+        if (c >= 0) L.max_child_nu = std::max(L.max_child_nu, h->fronts[c].nu);
+      }
+    }
+    for (int k = 0; k < max_steps; ++k) {
+      StepRange R{};
+      R.k = k;
+      R.diag_off = (int64_t)h_diag.size();
+      R.trsm_off = (int64_t)h_trsm.size();
+      R.upd_off = (int64_t)h_updt.size();
+      for (int f : L.ids) {
+        const FrontDev& F = h->fronts[f];
+        const int nte = F.ne_pad / T, nt = F.ld / T;
+        if (k >= nte) continue;
+        h_diag.push_back(f);
+        // rows of B_i vanish on panels made only of interior columns
+        auto zero_tile = [&](int i) { return F.kind == 0 && i >= nte && (k + 1) * T <= F.n_int; };
+        for (int i = k + 1; i < nt; ++i)
+          if (!zero_tile(i)) h_trsm.push_back(Task{f, i, k, 0});
+        for (int j = k + 1; j < nt; ++j) {
+          if (zero_tile(j)) continue;
+          for (int i = j; i < nt; ++i)
+            if (!zero_tile(i)) h_updt.push_back(Task{f, i, j, 0});
+        }
+      }
+      R.n_diag = (int)((int64_t)h_diag.size() - R.diag_off);
+      for (int64_t q = R.upd_off; q < (int64_t)h_updt.size(); ++q)
+        h->stats.kernel_flops[DD_K_UPDATE] += 8.0 * T * (h_updt[q].i == h_updt[q].j ? T * (T + 1) / 2 : T * T);
+      h->stats.kernel_flops[DD_K_TRSM] += 8.0 * ((int64_t)h_trsm.size() - R.trsm_off) * T * T * (T - 1) / 2.0;
+      h->stats.kernel_flops[DD_K_DIAG] += 8.0 * ((int64_t)h_diag.size() - R.diag_off) * (double)T * T * T / 6.0;
+      R.n_trsm = (int)((int64_t)h_trsm.size() - R.trsm_off);
+      R.n_upd = (int)((int64_t)h_updt.size() - R.upd_off);
+      L.steps.push_back(R);
+    }
+  }
+
+  // ---- upload (everything above is host-only validation and analysis) -------------
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return DD_ERR_NO_DEVICE;
+  }
+  if (opt.device >= ndev) return DD_ERR_INVALID_ARG;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  if (cudaSetDevice(h->device) != cudaSuccess) return DD_ERR_CUDA;
+  struct Restore { int d; ~Restore() { cudaSetDevice(d); } } restore{cur};
+  DeviceArena& A = h->arena;
+  DD_CUDA(A.alloc((unsigned char**)&h->pool, h->pool_bytes));
+  DD_CUDA(A.upload(&h->d_fronts, h->fronts, s));
+  DD_CUDA(A.upload(&h->d_leaves, h_leaves, s));
+  DD_CUDA(A.upload(&h->d_rowptr, h_rowptr, s));
+  DD_CUDA(A.upload(&h->d_colind, h_colind, s));
+  DD_CUDA(A.upload(&h->d_val, h_val, s));
+  DD_CUDA(A.upload(&h->d_iperm, h_iperm, s));
+  DD_CUDA(A.upload(&h->d_perm, h_perm, s));
+  DD_CUDA(A.upload(&h->d_brow, h_brow, s));
+  DD_CUDA(A.upload(&h->d_blocal, h_blocal, s));
+  DD_CUDA(A.upload(&h->d_bsign, h_bsign, s));
+  DD_CUDA(A.upload(&h->d_blptr, h_blptr, s));
+  DD_CUDA(A.upload(&h->d_bldual, h_bldual, s));
+  DD_CUDA(A.upload(&h->d_blsign, h_blsign, s));
+  DD_CUDA(A.upload(&h->d_btptr, h_btptr, s));
+  DD_CUDA(A.upload(&h->d_btrow, h_btrow, s));
+  DD_CUDA(A.upload(&h->d_btsign, h_btsign, s));
+  DD_CUDA(A.upload(&h->d_upd, h_upd, s));
+  DD_CUDA(A.upload(&h->d_sep, h_sep, s));
+  DD_CUDA(A.upload(&h->d_maps, h_maps, s));
+  DD_CUDA(A.upload(&h->d_level_ids, h_level_ids, s));
+  DD_CUDA(A.upload(&h->d_diag_ids, h_diag, s));
+  DD_CUDA(A.upload(&h->d_trsm, h_trsm, s));
+  DD_CUDA(A.upload(&h->d_updt, h_updt, s));
+  DD_CUDA(A.alloc(&h->d_status, 1));
+  DD_CUDA(A.alloc(&h->d_partials, 1024));
+  DD_CUDA(cudaEventCreate(&h->ev0));
+  DD_CUDA(cudaEventCreate(&h->ev1));
+  DD_CUDA(cudaStreamSynchronize(s));
+
+  h->stats.n_sub = n_sub;
+  h->stats.n_dual = n_dual;
+  h->stats.n_fronts = n_front;
+  h->stats.n_levels = (int)h->levels.size();
+  h->stats.n_primal = h->n_loc;
+  h->stats.bytes_factor = bytes_factor;
+  h->stats.bytes_device = (int64_t)A.bytes;
+  *out = h.release();
+  return DD_OK;
+}
+
+int dd_set_values(dd_handle* h, const dd_c128* vals) {
+  if (!h || !vals) return DD_ERR_INVALID_ARG;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->device);
+  const cudaMemcpyKind kind = is_device_ptr(vals) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaError_t e = cudaMemcpyAsync(h->d_val, vals, (size_t)h->nnz_total * 16, kind, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  h->factored = false;
+  cudaSetDevice(cur);
+  return cuda_status(e);
+}
+
+int dd_factor(dd_handle* h) {
+  if (!h) return DD_ERR_INVALID_ARG;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->device);
+  struct Restore { int d; ~Restore() { cudaSetDevice(d); } } restore{cur};
+  cudaStream_t s = h->stream;
+  h->factored = false;
+  const int p = h->prec == DD_PREC_FP64 ? 0 : 1;
+  DevStatus st0{};
+  st0.min_abs_d = 0x7FF0000000000000ull;  // +inf
+  DD_CUDA(cudaEventRecord(h->ev0, s));
+  DD_CUDA(cudaMemcpyAsync(h->d_status, &st0, sizeof(st0), cudaMemcpyHostToDevice, s));
+  int launches = 0;
+  // optional per-launch timing: an event pair around every launch of a class
+  constexpr size_t kMaxTimed = 8192;
+  size_t nev = 0;
+  std::vector<int> cls_of(h->time_kernels ? kMaxTimed : 0);
+  auto mark = [&](int cls, bool begin) -> cudaError_t {
+    if (!h->time_kernels || nev >= 2 * kMaxTimed) return cudaSuccess;
+    if (begin) cls_of[nev / 2] = cls;
+    while (h->kev.size() <= nev) {
+      cudaEvent_t e;
+      cudaError_t err = cudaEventCreate(&e);
+      if (err != cudaSuccess) return err;
+      h->kev.push_back(e);
+    }
+    return cudaEventRecord(h->kev[nev++], s);
+  };
+  for (int c = 0; c < DD_K_NCLASS; ++c) {
+    h->stats.kernel_ms[c] = 0.0;
+    h->stats.kernel_launches[c] = 0;
+  }
+  auto count = [&](int cls, int n) {
+    if (n > 0) {
+      launches++;
+      h->stats.kernel_launches[cls]++;
+    }
+  };
+  ddk::launch_zero(h->pool, h->pool_bytes, s);
+  DD_CUDA(mark(DD_K_INIT, true));
+  ddk::launch_leaf_init(p, h->pool, h->d_fronts, h->d_leaves, h->n_sub, h->d_rowptr, h->d_colind, h->d_val,
+                        h->d_iperm, h->d_brow, h->d_blocal, h->d_bsign, s);
+  DD_CUDA(mark(DD_K_INIT, false));
+  count(DD_K_INIT, 1);
+  for (size_t l = 0; l < h->levels.size(); ++l) {
+    const Level& L = h->levels[l];
+    const int32_t* ids = h->d_level_ids + L.ids_off;
+    const int n = (int)L.ids.size();
+    if (l > 0) {
+      DD_CUDA(mark(DD_K_ASSEMBLE, true));
+      ddk::launch_node_init(p, h->pool, h->d_fronts, ids, n, s);
+      ddk::launch_extend_add(p, h->pool, h->d_fronts, ids, n, 0, h->d_maps, L.max_child_nu, s);
+      ddk::launch_extend_add(p, h->pool, h->d_fronts, ids, n, 1, h->d_maps, L.max_child_nu, s);
+      DD_CUDA(mark(DD_K_ASSEMBLE, false));
+      count(DD_K_ASSEMBLE, n);
+      count(DD_K_ASSEMBLE, n);
+      count(DD_K_ASSEMBLE, n);
+    }
+    const int diag64 = (l > 0) ? 1 : 0;  // mixed form: FP64 pivot blocks of the auxiliary matrix
+    for (const StepRange& R : L.steps) {
+      DD_CUDA(mark(DD_K_DIAG, true));
+      ddk::launch_diag(p, diag64, h->pool, h->d_fronts, h->d_diag_ids + R.diag_off, R.n_diag, R.k, h->d_status, s);
+      DD_CUDA(mark(DD_K_DIAG, false));
+      DD_CUDA(mark(DD_K_TRSM, true));
+      ddk::launch_trsm(p, h->pool, h->d_fronts, h->d_trsm + R.trsm_off, R.n_trsm, R.k, h->d_status, s);
+      DD_CUDA(mark(DD_K_TRSM, false));
+      DD_CUDA(mark(DD_K_UPDATE, true));
+      ddk::launch_update(p, h->pool, h->d_fronts, h->d_updt + R.upd_off, R.n_upd, R.k, s);
+      DD_CUDA(mark(DD_K_UPDATE, false));
+      count(DD_K_DIAG, R.n_diag);
+      count(DD_K_TRSM, R.n_trsm);
+      count(DD_K_UPDATE, R.n_upd);
+    }
+  }
+  DD_CUDA(cudaGetLastError());
+  DD_CUDA(cudaEventRecord(h->ev1, s));
+  DevStatus st{};
+  DD_CUDA(cudaMemcpyAsync(&st, h->d_status, sizeof(st), cudaMemcpyDeviceToHost, s));
+  DD_CUDA(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  h->stats.t_factor_ms = ms;
+  h->stats.launches_factor = launches;
+  for (size_t q = 0; q + 1 < nev; q += 2) {
+    float dt = 0.f;
+    if (cudaEventElapsedTime(&dt, h->kev[q], h->kev[q + 1]) == cudaSuccess) h->stats.kernel_ms[cls_of[q / 2]] += dt;
+  }
+  double maxd, mind, maxl;
+  std::memcpy(&maxd, &st.max_abs_d, 8);
+  std::memcpy(&mind, &st.min_abs_d, 8);
+  std::memcpy(&maxl, &st.max_abs_l, 8);
+  h->stats.growth = std::max(maxd, maxl) / h->max_abs_a;
+  h->stats.min_pivot = mind;
+  if (st.code != 0) return DD_ERR_SINGULAR_PIVOT;
+  h->factored = true;
+  return DD_OK;
+}
+
+int dd_solve(dd_handle* h, int32_t nrhs, const dd_c128* f, int64_t ldf, dd_c128* u, int64_t ldu, dd_c128* lambda,
+             int64_t ldl) {
+  if (!h || nrhs < 0) return DD_ERR_INVALID_ARG;
+  if (nrhs == 0) return DD_OK;
+  if (!f || !u || ldf < h->n_loc || ldu < h->n_loc) return DD_ERR_INVALID_ARG;
+  if (lambda && ldl < h->n_dual) return DD_ERR_INVALID_ARG;
+  if (!h->factored) return DD_ERR_NOT_FACTORED;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->device);
+  struct Restore { int d; ~Restore() { cudaSetDevice(d); } } restore{cur};
+  cudaStream_t s = h->stream;
+  int st = ensure_work(h, nrhs);
+  if (st != DD_OK) return st;
+  h->launches = 0;
+  const size_t row_b = (size_t)h->n_loc * 16;
+  DD_CUDA(cudaEventRecord(h->ev0, s));
+  DD_CUDA(cudaMemcpy2DAsync(h->d_f, row_b, f, (size_t)ldf * 16, row_b, nrhs,
+                            is_device_ptr(f) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  direct_solve(h, nrhs, h->d_f, h->n_loc, nullptr, h->d_u, h->d_lam);
+  int iters = 0;
+  double ratio = 0.0;
+  int status = DD_OK;
+  const int64_t nu_el = h->n_loc * (int64_t)nrhs;
+  const int64_t nl_el = (int64_t)h->n_dual * nrhs;
+  for (int it = 0; it < h->max_refine; ++it) {
+    ddk::launch_residual(h->d_leaves, h->n_sub, h->d_rowptr, h->d_colind, h->d_val, h->d_blptr, h->d_bldual,
+                         h->d_blsign, h->d_f, h->n_loc, h->d_u, h->n_loc, h->d_lam, h->n_dual, h->d_r, h->n_loc,
+                         nrhs, s);
+    ddk::launch_dual_residual(h->n_dual, h->d_btptr, h->d_btrow, h->d_btsign, h->d_u, h->n_loc, h->d_g, h->n_dual,
+                              nrhs, s);
+    direct_solve(h, nrhs, h->d_r, h->n_loc, h->d_g, h->d_du, h->d_dlam);
+    const int nb1 = ddk::launch_sumsq(h->d_du, nu_el, h->d_partials, 512, s);
+    const int nb2 = ddk::launch_sumsq(h->d_u, nu_el, h->d_partials + 512, 512, s);
+    k_axpy<<<1024, 256, 0, s>>>(h->d_u, h->d_du, nu_el);
+    if (nl_el) k_axpy<<<256, 256, 0, s>>>(h->d_lam, h->d_dlam, nl_el);
+    h->launches += 6;
+    double part[1024];
+    DD_CUDA(cudaMemcpyAsync(part, h->d_partials, sizeof(part), cudaMemcpyDeviceToHost, s));
+    DD_CUDA(cudaStreamSynchronize(s));
+    double sdu = 0, su = 0;
+    for (int q = 0; q < nb1; ++q) sdu += part[q];
+    for (int q = 0; q < nb2; ++q) su += part[512 + q];
+    ratio = su > 0 ? std::sqrt(sdu / su) : 0.0;
+    iters = it + 1;
+    if (!std::isfinite(ratio)) break;
+    if (ratio <= h->refine_tol) break;
+  }
+  if (h->prec == DD_PREC_MIXED && h->max_refine > 0 && !(ratio <= h->refine_tol)) status = DD_ERR_NOT_CONVERGED;
+  DD_CUDA(cudaMemcpy2DAsync(u, (size_t)ldu * 16, h->d_u, row_b, row_b, nrhs,
+                            is_device_ptr(u) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  if (lambda && h->n_dual)
+    DD_CUDA(cudaMemcpy2DAsync(lambda, (size_t)ldl * 16, h->d_lam, (size_t)h->n_dual * 16, (size_t)h->n_dual * 16,
+                              nrhs, is_device_ptr(lambda) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  DD_CUDA(cudaGetLastError());
+  DD_CUDA(cudaEventRecord(h->ev1, s));
+  DD_CUDA(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  h->stats.t_solve_ms = ms;
+  h->stats.refine_iters = iters;
+  h->stats.refine_last = ratio;
+  h->stats.launches_solve = h->launches;
+  return status;
+}
+
+int dd_get_schur(const dd_handle* h, int32_t i, dd_c128* out, int32_t* duals, int32_t* m_out) {
+  if (!h || i < 0 || i >= h->n_sub) return DD_ERR_INVALID_ARG;
+  const FrontDev& F = h->fronts[i];
+  const int m = F.nu;
+  if (m_out) *m_out = m;
+  if (duals) std::copy(h->leaf_duals[i].begin(), h->leaf_duals[i].end(), duals);
+  if (!out) return DD_OK;
+  if (!h->factored) return DD_ERR_NOT_FACTORED;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->device);
+  struct Restore { int d; ~Restore() { cudaSetDevice(d); } } restore{cur};
+  std::vector<unsigned char> blk((size_t)m * m * h->elem);
+  const unsigned char* src = (const unsigned char*)h->pool + ((size_t)F.off + (size_t)F.ne_pad * F.ld + F.ne_pad) * h->elem;
+  if (m) {
+    DD_CUDA(cudaMemcpy2D(blk.data(), (size_t)m * h->elem, src, (size_t)F.ld * h->elem, (size_t)m * h->elem, m,
+                         cudaMemcpyDeviceToHost));
+  }
+  // the trailing block holds -F_i in its lower triangle
+  for (int a = 0; a < m; ++a)
+    for (int b = 0; b < m; ++b) {
+      const int hi = std::max(a, b), lo = std::min(a, b);
+      double re, im;
+      if (h->elem == 16) {
+        const double* v = (const double*)blk.data() + 2 * ((size_t)hi * m + lo);
+        re = v[0];
+        im = v[1];
+      } else {
+        const float* v = (const float*)blk.data() + 2 * ((size_t)hi * m + lo);
+        re = v[0];
+        im = v[1];
+      }
+      out[(size_t)b * m + a] = dd_c128{-re, -im};
+    }
+  return DD_OK;
+}
+
+int dd_get_stats(const dd_handle* h, dd_stats* out) {
+  if (!h || !out) return DD_ERR_INVALID_ARG;
+  *out = h->stats;
+  out->bytes_device = (int64_t)h->arena.bytes;
+  return DD_OK;
+}
+
+}  // extern "C"

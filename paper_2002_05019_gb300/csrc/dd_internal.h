@@ -1,0 +1,113 @@
+// Internal data structures shared by the host driver and the device kernels.
+//
+// Every elimination in the solver is a partial dense LDL^T of a "front": a
+// square, symmetric block stored row-major (lower triangle used) whose first
+// ne_pad rows/columns are eliminated and whose trailing block becomes the
+// Schur contribution passed to the parent front.
+//   * a leaf front is one domain's arrowhead block [A_i B_i^T; B_i 0]
+//     (rows: interior unknowns, interface unknowns, identity padding, then the
+//     m_i dual unknowns touching the domain); eliminating its n_i primal rows
+//     leaves -F_i = -B_i A_i^{-1} B_i^T in the trailing block (Section II:
+//     primal elimination and the domain's auxiliary-matrix contribution);
+//   * a node front belongs to a node of the domain tree: its separator duals
+//     (interfaces whose domains meet first at this node) followed by the
+//     ancestor duals it couples to; it assembles its children's trailing
+//     blocks and eliminates its separator (Section II: block LDL^T of the
+//     block-wise sparse auxiliary matrix, structure from the clique graph).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define DD_TILE 64
+
+struct FrontDev {
+  int64_t off;       // element offset of the front in the front pool
+  int64_t roff;      // element offset of its right-hand-side block (ld * nrhs)
+  int32_t ld;        // padded order (multiple of DD_TILE)
+  int32_t ne;        // eliminated unknowns (unpadded)
+  int32_t ne_pad;    // eliminated unknowns padded to DD_TILE (identity padding)
+  int32_t nu;        // update (trailing) rows, unpadded
+  int32_t n_int;     // leaf: number of interior unknowns (B rows vanish before it); node: 0
+  int32_t kind;      // 0 leaf, 1 node
+  int32_t sub;       // leaf: domain id; node: -1
+  int32_t upd_off;   // offset of the nu dual ids of the update rows
+  int32_t sep_off;   // node: offset of the ne dual ids of the separator rows
+  int32_t child[2];  // node: child fronts (-1 if absent)
+  int32_t map_off[2];// node: offsets of the extend-add maps (child update row -> row here)
+};
+
+struct LeafDev {
+  int64_t csr_off;   // offset of the domain's nonzeros in the concatenated CSR arrays
+  int64_t vec_off;   // offset of the domain's rows in the stacked f / u vectors
+  int32_t rowptr_off;// offset of its n+1 row pointers
+  int32_t n;         // local unknowns
+  int32_t perm_off;  // offset of perm (front row -> local row) and iperm (local row -> front row)
+  int32_t b_off;     // offset of its B entries
+  int32_t nb;        // number of B entries
+  int32_t front;     // front id
+};
+
+// Task of the batched partial LDL^T: front f, row tile i, column tile j.
+struct Task { int32_t f, i, j, pad; };
+
+// Device status word: first error seen by any kernel.
+struct DevStatus {
+  int32_t code;      // 0 ok, 3 singular pivot
+  int32_t front;     // front where it happened
+  int32_t row;       // row inside the front
+  int32_t pad;
+  unsigned long long max_abs_d;   // bit pattern of a non-negative double: max |d|
+  unsigned long long min_abs_d;   // min |d| over real (unpadded) pivots
+  unsigned long long max_abs_l;   // max |l * d| entry written by the panel kernels
+};
+
+namespace ddk {
+
+// ---- factorization (templated on storage: 0 = double2, 1 = float2) -------------
+void launch_zero(void* p, size_t bytes, cudaStream_t s);
+void launch_leaf_init(int prec, void* pool, const FrontDev* fronts, const LeafDev* leaves, int n_leaves,
+                      const int32_t* rowptr, const int32_t* colind, const double2* val,
+                      const int32_t* iperm, const int32_t* b_row, const int32_t* b_local,
+                      const int8_t* b_sign, cudaStream_t s);
+void launch_node_init(int prec, void* pool, const FrontDev* fronts, const int32_t* node_ids, int n,
+                      cudaStream_t s);
+void launch_diag(int prec, int diag_fp64, void* pool, const FrontDev* fronts, const int32_t* fids, int n,
+                 int k, DevStatus* st, cudaStream_t s);
+void launch_trsm(int prec, void* pool, const FrontDev* fronts, const Task* tasks, int n, int k,
+                 DevStatus* st, cudaStream_t s);
+void launch_update(int prec, void* pool, const FrontDev* fronts, const Task* tasks, int n, int k,
+                   cudaStream_t s);
+void launch_extend_add(int prec, void* pool, const FrontDev* fronts, const int32_t* node_ids, int n,
+                       int slot, const int32_t* maps, int max_nu, cudaStream_t s);
+
+// ---- solve --------------------------------------------------------------------
+void launch_rhs_leaf(int prec, void* rpool, const FrontDev* fronts, const LeafDev* leaves, int n_leaves,
+                     const int32_t* perm, const double2* f, int64_t ldf, int nrhs, cudaStream_t s);
+void launch_rhs_node(int prec, void* rpool, const FrontDev* fronts, const int32_t* node_ids, int n,
+                     const int32_t* sep, const double2* g, int64_t ldg, int nrhs, cudaStream_t s);
+void launch_rhs_extend_add(int prec, void* rpool, const FrontDev* fronts, const int32_t* node_ids, int n,
+                           int slot, const int32_t* maps, int nrhs, cudaStream_t s);
+void launch_forward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const int32_t* fids,
+                    int n, int nrhs, cudaStream_t s);
+void launch_backward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const int32_t* fids,
+                     int n, int nrhs, const int32_t* upd, const int32_t* sep, void* lam_work,
+                     int64_t ld_lam, cudaStream_t s);
+void launch_leaf_out(int prec, const void* rpool, const FrontDev* fronts, const LeafDev* leaves,
+                     int n_leaves, const int32_t* perm, double2* u, int64_t ldu, int nrhs, int accumulate,
+                     cudaStream_t s);
+void launch_lam_out(int prec, const void* lam_work, int64_t ld_work, int n_dual, int nrhs, double2* lam,
+                    int64_t ldl, int accumulate, cudaStream_t s);
+
+// ---- FP64 arrowhead residual and refinement helpers -----------------------------
+void launch_residual(const LeafDev* leaves, int n_leaves, const int32_t* rowptr, const int32_t* colind,
+                     const double2* val, const int32_t* b_dual_glob, const int32_t* b_local,
+                     const int8_t* b_sign, const double2* f, int64_t ldf, const double2* u, int64_t ldu,
+                     const double2* lam, int64_t ldl, double2* r, int64_t ldr, int nrhs, cudaStream_t s);
+void launch_dual_residual(int n_dual, const int32_t* bt_ptr, const int64_t* bt_row, const int8_t* bt_sign,
+                          const double2* u, int64_t ldu, double2* rl, int64_t ldrl, int nrhs,
+                          cudaStream_t s);
+// partial sums of |x|^2 per block into out[blocks]; returns block count used
+int launch_sumsq(const double2* x, int64_t n, double* out, int max_blocks, cudaStream_t s);
+
+}  // namespace ddk

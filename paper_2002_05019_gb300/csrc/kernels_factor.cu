@@ -1,0 +1,309 @@
+// Batched partial LDL^T of dense fronts (Section II: many independent domain
+// factorizations, and the block LDL^T of the auxiliary matrix).
+//
+// One blocked right-looking step k of the elimination of every front in a
+// batch is three launches over a host-built task list:
+//   k_diag    (front)        : A_kk = L_kk D_k L_kk^T, 64 x 64, in shared memory
+//   k_trsm    (front, i)     : L_ik = A_ik L_kk^{-T} D_k^{-1}
+//   k_update  (front, i, j)  : A_ij -= L_ik D_k L_jk^T   (k < j <= i)
+// Complex symmetric: plain transposes, no conjugation.  Fronts are stored
+// row-major (lower triangle), interleaved complex, double2 (FP64 form) or
+// float2 (mixed form).
+#include "dd_complex.cuh"
+#include "dd_internal.h"
+
+namespace ddk {
+
+namespace {
+
+constexpr int T = DD_TILE;
+
+__device__ __forceinline__ int tri(int i, int c) { return (i * (i + 1)) / 2 + c; }
+
+__device__ void status_pivot(DevStatus* st, int front, int row) {
+  if (atomicCAS(&st->code, 0, 3) == 0) {
+    st->front = front;
+    st->row = row;
+  }
+}
+
+__device__ __forceinline__ void atomic_max_pos(unsigned long long* p, double v) {
+  atomicMax(p, (unsigned long long)__double_as_longlong(v));
+}
+__device__ __forceinline__ void atomic_min_pos(unsigned long long* p, double v) {
+  atomicMin(p, (unsigned long long)__double_as_longlong(v));
+}
+
+// ---------------------------------------------------------------------------
+// leaf front initialisation: permuted A_i (lower part), identity padding, B_i
+// ---------------------------------------------------------------------------
+template <typename S>
+__global__ void k_leaf_init(S* pool, const FrontDev* fr, const LeafDev* lv, const int32_t* rowptr,
+                            const int32_t* colind, const double2* val, const int32_t* iperm,
+                            const int32_t* b_row, const int32_t* b_local, const int8_t* b_sign) {
+  const LeafDev L = lv[blockIdx.x];
+  const FrontDev F = fr[L.front];
+  S* A = pool + F.off;
+  const int32_t* rp = rowptr + L.rowptr_off;
+  const int32_t* ip = iperm + L.perm_off;
+  const int32_t* ci = colind + L.csr_off;
+  const double2* va = val + L.csr_off;
+  for (int r = threadIdx.x; r < L.n; r += blockDim.x) {
+    const int pr = ip[r];
+    for (int q = rp[r]; q < rp[r + 1]; ++q) {
+      const int pc = ip[ci[q]];
+      if (pr >= pc) A[(int64_t)pr * F.ld + pc] = cconv<S>(va[q]);
+    }
+  }
+  for (int r = F.ne + threadIdx.x; r < F.ne_pad; r += blockDim.x)
+    A[(int64_t)r * F.ld + r] = cmake<S>(1, 0);
+  for (int q = threadIdx.x; q < L.nb; q += blockDim.x) {
+    const int row = F.ne_pad + b_row[L.b_off + q];
+    const int col = ip[b_local[L.b_off + q]];
+    A[(int64_t)row * F.ld + col] = cmake<S>((float)b_sign[L.b_off + q], 0);
+  }
+}
+
+template <typename S>
+__global__ void k_node_init(S* pool, const FrontDev* fr, const int32_t* ids) {
+  const FrontDev F = fr[ids[blockIdx.x]];
+  S* A = pool + F.off;
+  for (int r = F.ne + threadIdx.x; r < F.ne_pad; r += blockDim.x)
+    A[(int64_t)r * F.ld + r] = cmake<S>(1, 0);
+}
+
+// ---------------------------------------------------------------------------
+// diagonal tile: unpivoted LDL^T of a 64 x 64 block in shared memory (packed
+// lower triangle), computed in precision C (FP64 for the auxiliary pivot
+// blocks of the mixed form)
+// ---------------------------------------------------------------------------
+template <typename S, typename C>
+__global__ void __launch_bounds__(256) k_diag(S* pool, const FrontDev* fr, const int32_t* fids, int k,
+                                              DevStatus* st) {
+  __shared__ C a[T * (T + 1) / 2];
+  const int f = fids[blockIdx.x];
+  const FrontDev F = fr[f];
+  S* base = pool + F.off + (int64_t)(k * T) * F.ld + k * T;
+  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+    const int i = idx / T, c = idx % T;
+    if (c <= i) a[tri(i, c)] = cconv<C>(base[(int64_t)i * F.ld + c]);
+  }
+  __syncthreads();
+  for (int j = 0; j < T; ++j) {
+    const C d = a[tri(j, j)];
+    for (int i = j + 1 + threadIdx.x; i < T; i += blockDim.x) a[tri(i, j)] = cdiv(a[tri(i, j)], d);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+      const int i = idx / T, c = idx % T;
+      if (c > j && c <= i) a[tri(i, c)] = cfms(a[tri(i, j)], cmul(d, a[tri(c, j)]), a[tri(i, c)]);
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+    const int i = idx / T, c = idx % T;
+    if (c <= i) base[(int64_t)i * F.ld + c] = cconv<S>(a[tri(i, c)]);
+  }
+  if (threadIdx.x < T) {
+    const int row = k * T + threadIdx.x;
+    if (row < F.ne) {
+      const double m2 = cabs2d(a[tri(threadIdx.x, threadIdx.x)]);
+      if (!(m2 > 0.0) || !isfinite(m2)) status_pivot(st, f, row);
+      const double m = sqrt(m2);
+      if (isfinite(m)) {
+        atomic_max_pos(&st->max_abs_d, m);
+        atomic_min_pos(&st->min_abs_d, m);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// panel: X = A_ik L_kk^{-T} (= L_ik D_k), then L_ik = X D_k^{-1}
+// dynamic shared memory: Lt[64][64] (Lt[j][p] = L_kk[p][j]) + X[64][65] + d[64]
+// ---------------------------------------------------------------------------
+template <typename S>
+__global__ void __launch_bounds__(256) k_trsm(S* pool, const FrontDev* fr, const Task* tasks, int k,
+                                              DevStatus* st) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  S* Lt = reinterpret_cast<S*>(smem_raw);
+  S* X = Lt + T * T;
+  S* dd = X + T * (T + 1);
+  const Task t = tasks[blockIdx.x];
+  const FrontDev F = fr[t.f];
+  const S* Lkk = pool + F.off + (int64_t)(k * T) * F.ld + k * T;
+  S* Aik = pool + F.off + (int64_t)(t.i * T) * F.ld + k * T;
+  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+    const int p = idx / T, j = idx % T;  // read row p of L_kk coalesced
+    Lt[j * T + p] = (j < p) ? Lkk[(int64_t)p * F.ld + j] : czero<S>();
+    X[p * (T + 1) + j] = Aik[(int64_t)p * F.ld + j];
+  }
+  if (threadIdx.x < T) dd[threadIdx.x] = Lkk[(int64_t)threadIdx.x * F.ld + threadIdx.x];
+  __syncthreads();
+  for (int j = 0; j < T - 1; ++j) {
+    for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+      const int r = idx / T, p = idx % T;
+      if (p > j) X[r * (T + 1) + p] = cfms(X[r * (T + 1) + j], Lt[j * T + p], X[r * (T + 1) + p]);
+    }
+    __syncthreads();
+  }
+  double mx = 0.0;
+  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+    const int r = idx / T, p = idx % T;
+    const S x = X[r * (T + 1) + p];
+    mx = fmax(mx, cabs2d(x));
+    Aik[(int64_t)r * F.ld + p] = cdiv(x, dd[p]);
+  }
+  // block max of |L D| for the growth statistic
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx > 0.0 && isfinite(mx)) atomic_max_pos(&st->max_abs_l, sqrt(mx));
+}
+
+// ---------------------------------------------------------------------------
+// trailing update C_ij -= L_ik D_k L_jk^T, one 64 x 64 tile per CTA, 256
+// threads with a 4 x 4 register block each (rows ty + 16 r, cols tx + 16 c)
+// ---------------------------------------------------------------------------
+template <typename S, int KC>
+__global__ void __launch_bounds__(256) k_update(S* pool, const FrontDev* fr, const Task* tasks, int k) {
+  __shared__ S As[KC][T + 1];
+  __shared__ S Bs[KC][T + 1];
+  __shared__ S dk[T];
+  const Task t = tasks[blockIdx.x];
+  const FrontDev F = fr[t.f];
+  const int64_t ld = F.ld;
+  const S* Li = pool + F.off + (int64_t)(t.i * T) * ld + k * T;
+  const S* Lj = pool + F.off + (int64_t)(t.j * T) * ld + k * T;
+  S* Cij = pool + F.off + (int64_t)(t.i * T) * ld + t.j * T;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  if (threadIdx.x < T) dk[threadIdx.x] = pool[F.off + (int64_t)(k * T + threadIdx.x) * (ld + 1)];
+  S acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = czero<S>();
+  for (int kc = 0; kc < T; kc += KC) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < T * KC; idx += blockDim.x) {
+      const int r = idx / KC, kk = idx % KC;
+      As[kk][r] = Li[(int64_t)r * ld + kc + kk];
+      Bs[kk][r] = cmul(Lj[(int64_t)r * ld + kc + kk], dk[kc + kk]);
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < KC; ++kk) {
+      S a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = cfma(a[r], b[c], acc[r][c]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      S* p = Cij + (int64_t)(ty + 16 * r) * ld + tx + 16 * c;
+      *p = csub(*p, acc[r][c]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// extend-add of one child's trailing block into its parent front.  Within one
+// launch every destination entry is written by at most one thread (the map is
+// injective), and the two children are added in two launches in a fixed
+// order, so the assembly is deterministic without atomics.
+// ---------------------------------------------------------------------------
+template <typename S>
+__global__ void k_extend_add(S* pool, const FrontDev* fr, const int32_t* nodes, int slot, const int32_t* maps) {
+  const FrontDev P = fr[nodes[blockIdx.x]];
+  const int c = P.child[slot];
+  if (c < 0) return;
+  const FrontDev Cf = fr[c];
+  const int32_t* map = maps + P.map_off[slot];
+  const S* src = pool + Cf.off + (int64_t)Cf.ne_pad * Cf.ld + Cf.ne_pad;
+  S* dst = pool + P.off;
+  for (int a = blockIdx.y; a < Cf.nu; a += gridDim.y) {
+    const int ra = map[a];
+    for (int b = threadIdx.x; b <= a; b += blockDim.x) {
+      const int rb = map[b];
+      const S v = src[(int64_t)a * Cf.ld + b];
+      const int hi = ra > rb ? ra : rb, lo = ra > rb ? rb : ra;
+      S* p = dst + (int64_t)hi * P.ld + lo;
+      *p = cadd(*p, v);
+    }
+  }
+}
+
+template <typename S> constexpr int trsm_smem() { return (T * T + T * (T + 1) + T) * (int)sizeof(S); }
+
+template <typename S>
+void set_trsm_attr() {
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(k_trsm<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, trsm_smem<S>());
+    done = true;
+  }
+}
+
+}  // namespace
+
+void launch_zero(void* p, size_t bytes, cudaStream_t s) {
+  if (bytes) cudaMemsetAsync(p, 0, bytes, s);
+}
+
+void launch_leaf_init(int prec, void* pool, const FrontDev* fronts, const LeafDev* leaves, int n_leaves,
+                      const int32_t* rowptr, const int32_t* colind, const double2* val, const int32_t* iperm,
+                      const int32_t* b_row, const int32_t* b_local, const int8_t* b_sign, cudaStream_t s) {
+  if (n_leaves <= 0) return;
+  if (prec == 0)
+    k_leaf_init<double2><<<n_leaves, 256, 0, s>>>((double2*)pool, fronts, leaves, rowptr, colind, val, iperm,
+                                                  b_row, b_local, b_sign);
+  else
+    k_leaf_init<float2><<<n_leaves, 256, 0, s>>>((float2*)pool, fronts, leaves, rowptr, colind, val, iperm,
+                                                 b_row, b_local, b_sign);
+}
+
+void launch_node_init(int prec, void* pool, const FrontDev* fronts, const int32_t* ids, int n, cudaStream_t s) {
+  if (n <= 0) return;
+  if (prec == 0) k_node_init<double2><<<n, 64, 0, s>>>((double2*)pool, fronts, ids);
+  else k_node_init<float2><<<n, 64, 0, s>>>((float2*)pool, fronts, ids);
+}
+
+void launch_diag(int prec, int diag_fp64, void* pool, const FrontDev* fronts, const int32_t* fids, int n, int k,
+                 DevStatus* st, cudaStream_t s) {
+  if (n <= 0) return;
+  if (prec == 0) k_diag<double2, double2><<<n, 256, 0, s>>>((double2*)pool, fronts, fids, k, st);
+  else if (diag_fp64) k_diag<float2, double2><<<n, 256, 0, s>>>((float2*)pool, fronts, fids, k, st);
+  else k_diag<float2, float2><<<n, 256, 0, s>>>((float2*)pool, fronts, fids, k, st);
+}
+
+void launch_trsm(int prec, void* pool, const FrontDev* fronts, const Task* tasks, int n, int k, DevStatus* st,
+                 cudaStream_t s) {
+  if (n <= 0) return;
+  if (prec == 0) {
+    set_trsm_attr<double2>();
+    k_trsm<double2><<<n, 256, trsm_smem<double2>(), s>>>((double2*)pool, fronts, tasks, k, st);
+  } else {
+    set_trsm_attr<float2>();
+    k_trsm<float2><<<n, 256, trsm_smem<float2>(), s>>>((float2*)pool, fronts, tasks, k, st);
+  }
+}
+
+void launch_update(int prec, void* pool, const FrontDev* fronts, const Task* tasks, int n, int k, cudaStream_t s) {
+  if (n <= 0) return;
+  if (prec == 0) k_update<double2, 16><<<n, 256, 0, s>>>((double2*)pool, fronts, tasks, k);
+  else k_update<float2, 32><<<n, 256, 0, s>>>((float2*)pool, fronts, tasks, k);
+}
+
+void launch_extend_add(int prec, void* pool, const FrontDev* fronts, const int32_t* node_ids, int n, int slot,
+                       const int32_t* maps, int max_nu, cudaStream_t s) {
+  if (n <= 0 || max_nu <= 0) return;
+  dim3 grid(n, max_nu < 256 ? max_nu : 256);
+  if (prec == 0) k_extend_add<double2><<<grid, 256, 0, s>>>((double2*)pool, fronts, node_ids, slot, maps);
+  else k_extend_add<float2><<<grid, 256, 0, s>>>((float2*)pool, fronts, node_ids, slot, maps);
+}
+
+}  // namespace ddk

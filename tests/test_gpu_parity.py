@@ -1,0 +1,174 @@
+"""GPU parity: the CUDA library against the CPU oracle, through the C ABI.
+
+Tolerances (relative 2-norm errors of the global primal solution, of lambda
+and of F_i): 1e-12 for the FP64 form and 1e-10 for the mixed form after FP64
+refinement - the accuracy the solver is specified to reach.  Sizes span
+several 64-wide tiles with ragged tails (domains of 98..2,477 unknowns).
+"""
+import numpy as np
+import pytest
+
+import femgen
+import oracle
+import paper_2002_05019_gb300 as dd
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "mixed": 1e-10}
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+def gather(p, u):
+    """Global vector from stacked local copies (lowest-index domain's copy)."""
+    x = np.zeros((p.n,) + u.shape[1:], dtype=np.complex128)
+    seen = np.zeros(p.n, dtype=bool)
+    off = 0
+    for s in p.subs:
+        new = ~seen[s.l2g]
+        x[s.l2g[new]] = u[off:off + s.n][new]
+        seen[s.l2g] = True
+        off += s.n
+    return x
+
+
+def copy_mismatch(p, u):
+    x = gather(p, u)
+    off, m = 0, 0.0
+    for s in p.subs:
+        m = max(m, float(np.abs(u[off:off + s.n] - x[s.l2g]).max()))
+        off += s.n
+    return m
+
+
+def run(p, precision, **kw):
+    s = dd.Solver.from_problem(p, precision=precision, **kw)
+    s.factor()
+    u, lam = s.solve(dd.stacked_loads(p))
+    return s, u, lam
+
+
+TINY = [(2, 1, False), (2, 3, False), (3, 2, False), (4, 3, True), (5, 4, True), (6, 2, True)]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("n,levels,jit", TINY)
+def test_tiny_against_oracle(precision, n, levels, jit):
+    p = femgen.tiny(n, levels, jittered=jit, eps="random" if jit else "uniform")
+    o = oracle.DDOracle(p)
+    uo, lo = o.solve([s.f for s in p.subs])
+    xo, _ = o.gather(uo)
+    s, u, lam = run(p, precision)
+    assert rel(gather(p, u), xo) <= TOL[precision]
+    assert rel(lam, lo) <= TOL[precision] * 10
+    assert copy_mismatch(p, u) <= TOL[precision] * np.abs(xo).max()
+    # F_i of every domain (first-step parity: domain LDL^T + Schur contribution)
+    if precision == "fp64":
+        for i, sub in enumerate(p.subs):
+            Fi, duals = s.schur(i)
+            Fo, do = oracle.subdomain_schur(sub, o.facs[i])
+            assert np.array_equal(duals, do)
+            assert rel(Fi, Fo) <= 1e-12
+    s.free()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_plain_8_domains_against_oracle(c1, precision):
+    o = oracle.DDOracle(c1)
+    uo, lo = o.solve([s.f for s in c1.subs])
+    xo, _ = o.gather(uo)
+    s, u, lam = run(c1, precision)
+    x = gather(c1, u)
+    assert rel(x, xo) <= TOL[precision]
+    assert rel(lam, lo) <= TOL[precision] * 10
+    assert oracle.backward_error(c1.A_indptr, c1.A_indices, c1.A_data, x, c1.b) < (1e-15 if precision == "fp64" else 1e-13)
+    st = s.stats()
+    assert st["n_sub"] == 8 and st["n_dual"] == 648
+    assert st["flops_factor"] > 8 * (4 / 3) * 604 ** 3
+    if precision == "mixed":
+        assert 1 <= st["refine_iters"] <= 10
+    for i in (0, 7):
+        Fi, _ = s.schur(i)
+        Fo, _ = oracle.subdomain_schur(c1.subs[i], o.facs[i])
+        assert rel(Fi, Fo) <= (1e-12 if precision == "fp64" else 1e-5)
+    s.free()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_linear_field_closed_form(c1_linear, precision):
+    """E = a + b x r is in the discrete space: the solution is its edge interpolant."""
+    s, u, _ = run(c1_linear, precision)
+    assert rel(gather(c1_linear, u), c1_linear.x_exact) <= TOL[precision]
+    s.free()
+
+
+def test_multiple_rhs_and_device_tensors():
+    import torch
+    p = femgen.multi_rhs_c5(n_edges=5)
+    o = oracle.DDOracle(p)
+    uo, lo = o.solve([s.f for s in p.subs])
+    xo, _ = o.gather(uo)
+    for precision in ("fp64", "mixed"):
+        s = dd.Solver.from_problem(p, precision=precision)
+        s.factor()
+        f = dd.stacked_loads(p)
+        u, lam = s.solve(f)
+        for c in range(f.shape[1]):
+            assert rel(gather(p, u)[:, c], xo[:, c]) <= TOL[precision]
+        ut, lt = s.solve(torch.from_numpy(f).cuda())
+        assert rel(ut.cpu().numpy(), u) <= 1e-14 and rel(lt.cpu().numpy(), lam) <= 1e-14
+        s.free()
+
+
+def test_single_domain_and_refactor():
+    p = femgen.tiny(3, 1)
+    sub = p.subs[0]
+    A = sub.dense()
+    f = np.random.default_rng(0).normal(size=(sub.n, 2)) + 0j
+    s = dd.Solver([dict(n=sub.n, indptr=sub.indptr, indices=sub.indices, data=sub.data,
+                        b_dual=np.zeros(0, np.int32), b_local=np.zeros(0, np.int32),
+                        b_sign=np.zeros(0, np.int8))], 0)
+    with pytest.raises(dd.DDError) as e:
+        s.solve(f)
+    assert e.value.code == 6  # not factored
+    s.factor()
+    u, _ = s.solve(f)
+    assert rel(u, np.linalg.solve(A, f)) <= 1e-12
+    # new values, same pattern
+    s.set_values(2.0 * sub.data)
+    with pytest.raises(dd.DDError):
+        s.solve(f)
+    s.factor()
+    u2, _ = s.solve(f)
+    assert rel(u2, 0.5 * np.linalg.solve(A, f)) <= 1e-12
+    s.free()
+
+
+@pytest.fixture(scope="module")
+def c2_linear():
+    return femgen.batched_c2(rhs="linear")
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batched_512_domains_full_size(c2_linear, precision):
+    """The 512-domain workload at full size: closed-form solution, arrowhead
+    residual, interface continuity, and the F_i of sampled domains."""
+    p = c2_linear
+    s, u, lam = run(p, precision)
+    x = gather(p, u)
+    assert rel(x, p.x_exact) <= TOL[precision]
+    assert copy_mismatch(p, u) <= TOL[precision] * np.abs(p.x_exact).max() * 10
+    rp, ru = oracle.arrow_residual(p, dd.unstack(p, u), lam)
+    fn = np.linalg.norm(dd.stacked_loads(p))
+    assert np.linalg.norm(np.concatenate(rp)) <= 1e-12 * fn * 1e3
+    st = s.stats()
+    assert st["n_sub"] == 512 and st["growth"] < 1e3
+    sizes = np.array([sub.n for sub in p.subs])
+    for i in [int(np.argmin(sizes)), int(np.argsort(sizes)[len(sizes) // 4])]:
+        Fi, duals = s.schur(i)
+        Fo, do = oracle.subdomain_schur(p.subs[i])
+        assert np.array_equal(duals, do)
+        assert rel(Fi, Fo) <= (1e-12 if precision == "fp64" else 1e-5)
+    s.free()
