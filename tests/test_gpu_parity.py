@@ -15,6 +15,9 @@ import paper_2002_05019_gb300 as dd
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-12, "mixed": 1e-10}
+# F_i itself is not refined: in the mixed form it carries the complex64 LDL^T
+# error, about cond(A_i) * u32 with cond(A_i) <~ 1e3 and u32 = 6e-8
+TOL_F = {"fp64": 1e-12, "mixed": 1e-4}
 
 
 def rel(a, b):
@@ -92,7 +95,7 @@ def test_plain_8_domains_against_oracle(c1, precision):
     for i in (0, 7):
         Fi, _ = s.schur(i)
         Fo, _ = oracle.subdomain_schur(c1.subs[i], o.facs[i])
-        assert rel(Fi, Fo) <= (1e-12 if precision == "fp64" else 1e-5)
+        assert rel(Fi, Fo) <= TOL_F[precision]
     s.free()
 
 
@@ -170,5 +173,5 @@ def test_batched_512_domains_full_size(c2_linear, precision):
         Fi, duals = s.schur(i)
         Fo, do = oracle.subdomain_schur(p.subs[i])
         assert np.array_equal(duals, do)
-        assert rel(Fi, Fo) <= (1e-12 if precision == "fp64" else 1e-5)
+        assert rel(Fi, Fo) <= TOL_F[precision]
     s.free()
