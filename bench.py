@@ -38,6 +38,7 @@ METRIC = "factor+solve DoF/s & TFLOP/s, mixed vs FP64 GPU form at rel. err <=1e-
 WORKLOADS = {
     "batched": ("batched_c2", "box n=41 Kuhn tets, 512 jittered-RCB domains (500..2477 unknowns), "
                 "per-domain eps_r, 1 edge-current RHS"),
+    "medium": ("medium", "box n=24 Kuhn tets, 64 jittered-RCB domains, per-domain eps_r, 1 edge-current RHS"),
     "plain": ("plain_c1", "box n=8 Kuhn tets, 8 equal domains, eps_r=2-0.1j, 1 edge-current RHS"),
     "large": ("large_c4", "box n=65 Kuhn tets, 2048 jittered-RCB domains, per-domain eps_r, 1 edge-current RHS"),
 }

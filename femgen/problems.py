@@ -259,6 +259,12 @@ def batched_c2(rhs="edge", **kw) -> Problem:
                          eps="random", rhs=rhs, **kw)
 
 
+def medium(rhs="edge", **kw) -> Problem:
+    """n = 24, 64 jittered-bisection domains of 500..2500 edges (profiling-sized)."""
+    return build_problem("medium-n24-s64", 24, 6, split_range=(0.37, 0.63), size_range=(500, 2500),
+                         eps="random", rhs=rhs, **kw)
+
+
 def large_c4(rhs="edge", **kw) -> Problem:
     """n = 65, 2048 jittered-bisection domains of 500..2500 edges: 1,960,595 DoFs."""
     return build_problem("large-n65-s2048", 65, 11, split_range=(0.37, 0.63), size_range=(500, 2500),

@@ -41,6 +41,8 @@ struct Level {
   int64_t ids_off = 0;            // offset into d_level_ids
   std::vector<StepRange> steps;   // factor schedule
   int max_child_nu = 0;
+  int64_t fwd_off = 0, bwd_off = 0;   // solve tasks (forward by row tile, backward by column tile)
+  int n_fwd = 0, n_bwd = 0;
 };
 
 struct DeviceArena {
@@ -119,7 +121,12 @@ struct dd_handle {
   int32_t *d_upd = nullptr, *d_sep = nullptr, *d_maps = nullptr;
   int32_t *d_level_ids = nullptr, *d_diag_ids = nullptr;
   Task *d_trsm = nullptr, *d_updt = nullptr;
+  Task *d_fwd = nullptr, *d_bwd = nullptr;
+  int32_t *d_flag_f = nullptr, *d_flag_b = nullptr;
+  int64_t n_tiles = 0;
+  int epoch = 0;
   DevStatus* d_status = nullptr;
+  DevStatus* d_solve_status = nullptr;
   double* d_partials = nullptr;
 
   // solve work (grown on demand, freed with the handle)
@@ -300,24 +307,27 @@ int ensure_work(dd_handle* h, int nrhs) {
 void direct_solve(dd_handle* h, int nrhs, const double2* f, int64_t ldf, const double2* g, double2* u, double2* lam) {
   cudaStream_t s = h->stream;
   const int p = h->prec == DD_PREC_FP64 ? 0 : 1;
-  const Level& L0 = h->levels[0];
+  const int ep = ++h->epoch;
   ddk::launch_rhs_leaf(p, h->rpool, h->d_fronts, h->d_leaves, h->n_sub, h->d_perm, f, ldf, nrhs, s);
-  ddk::launch_forward(p, h->pool, h->rpool, h->d_fronts, h->d_level_ids + L0.ids_off, (int)L0.ids.size(), nrhs, s);
-  h->launches += 2;
-  for (size_t l = 1; l < h->levels.size(); ++l) {
+  h->launches += 1;
+  for (size_t l = 0; l < h->levels.size(); ++l) {
     const Level& L = h->levels[l];
     const int32_t* ids = h->d_level_ids + L.ids_off;
     const int n = (int)L.ids.size();
-    ddk::launch_rhs_node(p, h->rpool, h->d_fronts, ids, n, h->d_sep, g, h->n_dual, nrhs, s);
-    ddk::launch_rhs_extend_add(p, h->rpool, h->d_fronts, ids, n, 0, h->d_maps, nrhs, s);
-    ddk::launch_rhs_extend_add(p, h->rpool, h->d_fronts, ids, n, 1, h->d_maps, nrhs, s);
-    ddk::launch_forward(p, h->pool, h->rpool, h->d_fronts, ids, n, nrhs, s);
-    h->launches += 4;
+    if (l > 0) {
+      ddk::launch_rhs_node(p, h->rpool, h->d_fronts, ids, n, h->d_sep, g, h->n_dual, nrhs, s);
+      ddk::launch_rhs_extend_add(p, h->rpool, h->d_fronts, ids, n, 0, h->d_maps, nrhs, s);
+      ddk::launch_rhs_extend_add(p, h->rpool, h->d_fronts, ids, n, 1, h->d_maps, nrhs, s);
+      h->launches += 3;
+    }
+    ddk::launch_forward(p, h->pool, h->rpool, h->d_fronts, h->d_fwd + L.fwd_off, L.n_fwd, nrhs, h->d_flag_f, ep,
+                        h->d_solve_status, s);
+    h->launches += 1;
   }
   for (size_t l = h->levels.size(); l-- > 0;) {
     const Level& L = h->levels[l];
-    ddk::launch_backward(p, h->pool, h->rpool, h->d_fronts, h->d_level_ids + L.ids_off, (int)L.ids.size(), nrhs,
-                         h->d_upd, h->d_sep, h->lam_work, h->n_dual, s);
+    ddk::launch_backward(p, h->pool, h->rpool, h->d_fronts, h->d_bwd + L.bwd_off, L.n_bwd, nrhs, h->d_upd, h->d_sep,
+                         h->lam_work, h->n_dual, h->d_flag_b, ep, h->d_solve_status, s);
     h->launches += 1;
   }
   ddk::launch_leaf_out(p, h->rpool, h->d_fronts, h->d_leaves, h->n_sub, h->d_perm, u, h->n_loc, nrhs, 0, s);
@@ -601,18 +611,21 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
   }
 
   // ---- offsets, levels, task lists ----------------------------------------------
-  int64_t off = 0, roff = 0;
+  int64_t off = 0, roff = 0, toff = 0;
   int64_t bytes_factor = 0;
   for (int x = 0; x < n_front; ++x) {
     FrontDev& F = h->fronts[x];
     F.off = off;
     F.roff = roff;
+    F.tile_off = (int32_t)toff;
+    toff += F.ld / T;
     off += (int64_t)F.ld * F.ld;
     roff += F.ld;
     bytes_factor += ((int64_t)F.ne_pad * (F.ne_pad + 1) / 2 + (int64_t)F.ne_pad * (F.ld - F.ne_pad)) * (int64_t)h->elem;
   }
   h->pool_bytes = (size_t)off * h->elem;
   h->rows_total = roff;
+  h->n_tiles = toff;
   int max_h = 0;
   for (int x = 0; x < n_front; ++x) max_h = std::max(max_h, height[x]);
   h->levels.assign(max_h + 1, Level{});
@@ -662,6 +675,27 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
       L.steps.push_back(R);
     }
   }
+  // solve tasks: forward (front, row tile) by increasing tile, backward (front,
+  // eliminated tile) by decreasing tile, so that every CTA waits only on CTAs
+  // with a smaller block index
+  std::vector<Task> h_fwd, h_bwd;
+  for (auto& L : h->levels) {
+    int max_nt = 0, max_nte = 0;
+    for (int f : L.ids) {
+      max_nt = std::max(max_nt, h->fronts[f].ld / T);
+      max_nte = std::max(max_nte, h->fronts[f].ne_pad / T);
+    }
+    L.fwd_off = (int64_t)h_fwd.size();
+    for (int i = 0; i < max_nt; ++i)
+      for (int f : L.ids)
+        if (i < h->fronts[f].ld / T) h_fwd.push_back(Task{f, i, 0, 0});
+    L.n_fwd = (int)((int64_t)h_fwd.size() - L.fwd_off);
+    L.bwd_off = (int64_t)h_bwd.size();
+    for (int j = max_nte - 1; j >= 0; --j)
+      for (int f : L.ids)
+        if (j < h->fronts[f].ne_pad / T) h_bwd.push_back(Task{f, j, 0, 0});
+    L.n_bwd = (int)((int64_t)h_bwd.size() - L.bwd_off);
+  }
 
   // ---- upload (everything above is host-only validation and analysis) -------------
   int ndev = 0;
@@ -699,6 +733,14 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
   DD_CUDA(A.upload(&h->d_diag_ids, h_diag, s));
   DD_CUDA(A.upload(&h->d_trsm, h_trsm, s));
   DD_CUDA(A.upload(&h->d_updt, h_updt, s));
+  DD_CUDA(A.upload(&h->d_fwd, h_fwd, s));
+  DD_CUDA(A.upload(&h->d_bwd, h_bwd, s));
+  DD_CUDA(A.alloc(&h->d_flag_f, (size_t)std::max<int64_t>(h->n_tiles, 1)));
+  DD_CUDA(A.alloc(&h->d_flag_b, (size_t)std::max<int64_t>(h->n_tiles, 1)));
+  DD_CUDA(cudaMemsetAsync(h->d_flag_f, 0, sizeof(int32_t) * std::max<int64_t>(h->n_tiles, 1), s));
+  DD_CUDA(cudaMemsetAsync(h->d_flag_b, 0, sizeof(int32_t) * std::max<int64_t>(h->n_tiles, 1), s));
+  DD_CUDA(A.alloc(&h->d_solve_status, 1));
+  DD_CUDA(cudaMemsetAsync(h->d_solve_status, 0, sizeof(DevStatus), s));
   DD_CUDA(A.alloc(&h->d_status, 1));
   DD_CUDA(A.alloc(&h->d_partials, 1024));
   DD_CUDA(cudaEventCreate(&h->ev0));
@@ -866,8 +908,11 @@ int dd_solve(dd_handle* h, int32_t nrhs, const dd_c128* f, int64_t ldf, dd_c128*
     if (nl_el) k_axpy<<<256, 256, 0, s>>>(h->d_lam, h->d_dlam, nl_el);
     h->launches += 6;
     double part[1024];
+    DevStatus sst{};
     DD_CUDA(cudaMemcpyAsync(part, h->d_partials, sizeof(part), cudaMemcpyDeviceToHost, s));
+    DD_CUDA(cudaMemcpyAsync(&sst, h->d_solve_status, sizeof(sst), cudaMemcpyDeviceToHost, s));
     DD_CUDA(cudaStreamSynchronize(s));
+    if (sst.code != 0) break;  // reported after the loop
     double sdu = 0, su = 0;
     for (int q = 0; q < nb1; ++q) sdu += part[q];
     for (int q = 0; q < nb2; ++q) su += part[512 + q];
@@ -884,7 +929,14 @@ int dd_solve(dd_handle* h, int32_t nrhs, const dd_c128* f, int64_t ldf, dd_c128*
                               nrhs, is_device_ptr(lambda) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
   DD_CUDA(cudaGetLastError());
   DD_CUDA(cudaEventRecord(h->ev1, s));
+  DevStatus sst{};
+  DD_CUDA(cudaMemcpyAsync(&sst, h->d_solve_status, sizeof(sst), cudaMemcpyDeviceToHost, s));
   DD_CUDA(cudaStreamSynchronize(s));
+  if (sst.code != 0) {
+    DD_CUDA(cudaMemsetAsync(h->d_solve_status, 0, sizeof(DevStatus), s));
+    DD_CUDA(cudaStreamSynchronize(s));
+    return sst.code == 8 ? DD_ERR_TIMEOUT : DD_ERR_CUDA;
+  }
   float ms = 0.f;
   cudaEventElapsedTime(&ms, h->ev0, h->ev1);
   h->stats.t_solve_ms = ms;

@@ -35,6 +35,8 @@ struct FrontDev {
   int32_t sep_off;   // node: offset of the ne dual ids of the separator rows
   int32_t child[2];  // node: child fronts (-1 if absent)
   int32_t map_off[2];// node: offsets of the extend-add maps (child update row -> row here)
+  int32_t tile_off;  // offset of this front's per-tile ready flags (ld / DD_TILE of them)
+  int32_t pad_;
 };
 
 struct LeafDev {
@@ -53,7 +55,7 @@ struct Task { int32_t f, i, j, pad; };
 
 // Device status word: first error seen by any kernel.
 struct DevStatus {
-  int32_t code;      // 0 ok, 3 singular pivot
+  int32_t code;      // 0 ok, 3 singular pivot, 8 a bounded wait gave up
   int32_t front;     // front where it happened
   int32_t row;       // row inside the front
   int32_t pad;
@@ -88,11 +90,13 @@ void launch_rhs_node(int prec, void* rpool, const FrontDev* fronts, const int32_
                      const int32_t* sep, const double2* g, int64_t ldg, int nrhs, cudaStream_t s);
 void launch_rhs_extend_add(int prec, void* rpool, const FrontDev* fronts, const int32_t* node_ids, int n,
                            int slot, const int32_t* maps, int nrhs, cudaStream_t s);
-void launch_forward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const int32_t* fids,
-                    int n, int nrhs, cudaStream_t s);
-void launch_backward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const int32_t* fids,
-                     int n, int nrhs, const int32_t* upd, const int32_t* sep, void* lam_work,
-                     int64_t ld_lam, cudaStream_t s);
+// tile-parallel substitution: one CTA per (front, tile) task of a level; a
+// CTA waits (bounded) on the ready flags of the tiles it depends on
+void launch_forward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const Task* tasks, int n,
+                    int nrhs, int32_t* flags, int epoch, DevStatus* st, cudaStream_t s);
+void launch_backward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const Task* tasks, int n,
+                     int nrhs, const int32_t* upd, const int32_t* sep, void* lam_work, int64_t ld_lam,
+                     int32_t* flags, int epoch, DevStatus* st, cudaStream_t s);
 void launch_leaf_out(int prec, const void* rpool, const FrontDev* fronts, const LeafDev* leaves,
                      int n_leaves, const int32_t* perm, double2* u, int64_t ldu, int nrhs, int accumulate,
                      cudaStream_t s);

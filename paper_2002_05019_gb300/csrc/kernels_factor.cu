@@ -81,6 +81,8 @@ template <typename S, typename C>
 __global__ void __launch_bounds__(256) k_diag(S* pool, const FrontDev* fr, const int32_t* fids, int k,
                                               DevStatus* st) {
   __shared__ C a[T * (T + 1) / 2];
+  __shared__ C w[T];        // column j before scaling: w_c = d_j * l_cj
+  __shared__ C rinv;        // 1 / d_j
   const int f = fids[blockIdx.x];
   const FrontDev F = fr[f];
   S* base = pool + F.off + (int64_t)(k * T) * F.ld + k * T;
@@ -89,13 +91,22 @@ __global__ void __launch_bounds__(256) k_diag(S* pool, const FrontDev* fr, const
     if (c <= i) a[tri(i, c)] = cconv<C>(base[(int64_t)i * F.ld + c]);
   }
   __syncthreads();
+  if (threadIdx.x == 0) rinv = cdiv(cmake<C>(1, 0), a[0]);
+  __syncthreads();
+  const int row = threadIdx.x >> 2, sub = threadIdx.x & 3;   // 4 threads per row
   for (int j = 0; j < T; ++j) {
-    const C d = a[tri(j, j)];
-    for (int i = j + 1 + threadIdx.x; i < T; i += blockDim.x) a[tri(i, j)] = cdiv(a[tri(i, j)], d);
+    // l_ij = a_ij / d_j, keeping the unscaled value for the update
+    if (sub == 0 && row > j) {
+      const C v = a[tri(row, j)];
+      w[row] = v;
+      a[tri(row, j)] = cmul(v, rinv);
+    }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
-      const int i = idx / T, c = idx % T;
-      if (c > j && c <= i) a[tri(i, c)] = cfms(a[tri(i, j)], cmul(d, a[tri(c, j)]), a[tri(i, c)]);
+    // a_ic -= l_ij * (d_j l_cj) for j < c <= i
+    if (row > j) {
+      const C l = a[tri(row, j)];
+      for (int c = j + 1 + sub; c <= row; c += 4) a[tri(row, c)] = cfms(l, w[c], a[tri(row, c)]);
+      if (row == j + 1 && sub == 0) rinv = cdiv(cmake<C>(1, 0), a[tri(j + 1, j + 1)]);
     }
     __syncthreads();
   }
@@ -104,10 +115,10 @@ __global__ void __launch_bounds__(256) k_diag(S* pool, const FrontDev* fr, const
     if (c <= i) base[(int64_t)i * F.ld + c] = cconv<S>(a[tri(i, c)]);
   }
   if (threadIdx.x < T) {
-    const int row = k * T + threadIdx.x;
-    if (row < F.ne) {
+    const int r = k * T + threadIdx.x;
+    if (r < F.ne) {
       const double m2 = cabs2d(a[tri(threadIdx.x, threadIdx.x)]);
-      if (!(m2 > 0.0) || !isfinite(m2)) status_pivot(st, f, row);
+      if (!(m2 > 0.0) || !isfinite(m2)) status_pivot(st, f, r);
       const double m = sqrt(m2);
       if (isfinite(m)) {
         atomic_max_pos(&st->max_abs_d, m);
@@ -125,33 +136,33 @@ template <typename S>
 __global__ void __launch_bounds__(256) k_trsm(S* pool, const FrontDev* fr, const Task* tasks, int k,
                                               DevStatus* st) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  S* Lt = reinterpret_cast<S*>(smem_raw);
-  S* X = Lt + T * T;
-  S* dd = X + T * (T + 1);
+  S* Lt = reinterpret_cast<S*>(smem_raw);  // Lt[j * T + p] = L_kk[p][j]
+  S* X = Lt + T * T;                       // X[p * (T + 1) + r] = row r, column p
+  S* rinv = X + T * (T + 1);               // 1 / d_p
   const Task t = tasks[blockIdx.x];
   const FrontDev F = fr[t.f];
   const S* Lkk = pool + F.off + (int64_t)(k * T) * F.ld + k * T;
   S* Aik = pool + F.off + (int64_t)(t.i * T) * F.ld + k * T;
   for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
-    const int p = idx / T, j = idx % T;  // read row p of L_kk coalesced
+    const int p = idx / T, j = idx % T;  // coalesced reads along rows
     Lt[j * T + p] = (j < p) ? Lkk[(int64_t)p * F.ld + j] : czero<S>();
-    X[p * (T + 1) + j] = Aik[(int64_t)p * F.ld + j];
+    X[j * (T + 1) + p] = Aik[(int64_t)p * F.ld + j];
   }
-  if (threadIdx.x < T) dd[threadIdx.x] = Lkk[(int64_t)threadIdx.x * F.ld + threadIdx.x];
+  if (threadIdx.x < T) rinv[threadIdx.x] = cdiv(cmake<S>(1, 0), Lkk[(int64_t)threadIdx.x * F.ld + threadIdx.x]);
   __syncthreads();
+  // X L_kk^T = A_ik, column by column: X[:, p] -= X[:, j] L_kk[p][j] for p > j
+  const int r = threadIdx.x & (T - 1), g = threadIdx.x >> 6;  // 4 column groups
   for (int j = 0; j < T - 1; ++j) {
-    for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
-      const int r = idx / T, p = idx % T;
-      if (p > j) X[r * (T + 1) + p] = cfms(X[r * (T + 1) + j], Lt[j * T + p], X[r * (T + 1) + p]);
-    }
+    const S xj = X[j * (T + 1) + r];
+    for (int p = j + 1 + ((g - j - 1) & 3); p < T; p += 4) X[p * (T + 1) + r] = cfms(xj, Lt[j * T + p], X[p * (T + 1) + r]);
     __syncthreads();
   }
   double mx = 0.0;
   for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
-    const int r = idx / T, p = idx % T;
-    const S x = X[r * (T + 1) + p];
+    const int rr = idx / T, p = idx % T;
+    const S x = X[p * (T + 1) + rr];
     mx = fmax(mx, cabs2d(x));
-    Aik[(int64_t)r * F.ld + p] = cdiv(x, dd[p]);
+    Aik[(int64_t)rr * F.ld + p] = cmul(x, rinv[p]);
   }
   // block max of |L D| for the growth statistic
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));

@@ -70,127 +70,198 @@ __global__ void k_rhs_extend_add(S* rpool, const FrontDev* fr, const int32_t* id
   }
 }
 
-// forward substitution + diagonal scaling of one front per CTA
+__device__ __forceinline__ int ld_acquire(const int32_t* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int32_t* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Wait until *flag >= epoch.  Bounded: after ~2^22 polls (about a second) the
+// wait gives up, records DD_ERR_TIMEOUT (8) in the status word and returns
+// false; the caller then returns without publishing its own flag.
+__device__ bool wait_ready(const int32_t* flag, int epoch, DevStatus* st, int front, int tile) {
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    int it = 0;
+    ok = 1;
+    while (ld_acquire(flag) < epoch) {
+      if (++it > (1 << 22)) {
+        if (atomicCAS(&st->code, 0, 8) == 0) {
+          st->front = front;
+          st->row = tile;
+        }
+        ok = 0;
+        break;
+      }
+      __nanosleep(128);
+    }
+  }
+  __syncthreads();
+  const int r = ok;
+  __syncthreads();
+  return r != 0;
+}
+
+// packed lower triangle (with diagonal) of a 64 x 64 tile
+__device__ __forceinline__ int tri(int r, int c) { return (r * (r + 1)) / 2 + c; }
+
+template <typename S>
+__device__ __forceinline__ S ldcg(const S* p);
+template <>
+__device__ __forceinline__ double2 ldcg<double2>(const double2* p) { return __ldcg(p); }
+template <>
+__device__ __forceinline__ float2 ldcg<float2>(const float2* p) { return __ldcg(p); }
+
+// Forward substitution, one CTA per (front, row tile i).  Rows of tile i
+// accumulate L_ik z_k for every eliminated tile k < i as soon as tile k is
+// final (its ready flag), then tile i is solved with the unit-lower diagonal
+// block.  Tasks are ordered by tile index, so a CTA only waits on CTAs with a
+// smaller block index.  Update tiles (i >= ne_pad / 64) only accumulate.
 template <typename S>
 __global__ void __launch_bounds__(SOLVE_THREADS) k_forward(const S* pool, S* rpool, const FrontDev* fr,
-                                                           const int32_t* fids, int nrhs) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  S* Lt = reinterpret_cast<S*>(smem_raw);  // [T][T+1] diagonal tile
-  const FrontDev F = fr[fids[blockIdx.x]];
+                                                           const Task* tasks, int nrhs, int32_t* flags, int epoch,
+                                                           DevStatus* st) {
+  __shared__ S Lt[T * (T + 1) / 2];
+  __shared__ S zi[T];
+  const Task t = tasks[blockIdx.x];
+  const FrontDev F = fr[t.f];
   const S* L = pool + F.off;
   S* z = rpool + F.roff * nrhs;
   const int64_t ld = F.ld;
   const int nte = F.ne_pad / T;
-  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32, nw = blockDim.x / 32;
+  const int i = t.i, r0 = i * T;
+  const int kmax = i < nte ? i : nte;
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  int32_t* flg = flags + F.tile_off;
+  constexpr int RW = T / (SOLVE_THREADS / 32);  // rows per warp
+  if (i < nte) {
+    for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+      const int rr = idx / T, c = idx % T;
+      if (c <= rr) Lt[tri(rr, c)] = L[(r0 + rr) * ld + r0 + c];
+    }
+  }
   for (int j = 0; j < nrhs; ++j) {
-    for (int t = 0; t < nte; ++t) {
-      const int r0 = t * T;
-      // rows of tile t: subtract the contributions of all earlier (final) rows
-      for (int rr = warp; rr < T; rr += nw) {
-        const int r = r0 + rr;
-        S acc = czero<S>();
-        for (int c = lane; c < r0; c += 32) acc = cfma(L[r * ld + c], z[(int64_t)c * nrhs + j], acc);
-        acc = warp_sum(acc);
-        if (lane == 0) z[(int64_t)r * nrhs + j] = csub(z[(int64_t)r * nrhs + j], acc);
+    S acc[RW];
+#pragma unroll
+    for (int q = 0; q < RW; ++q) acc[q] = czero<S>();
+    for (int k = 0; k < kmax; ++k) {
+      if (j == 0 && !wait_ready(flg + k, epoch, st, t.f, k)) return;
+      const int c0 = k * T;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = c0 + lane + 32 * h;
+        const S zc = ldcg(z + (int64_t)c * nrhs + j);
+#pragma unroll
+        for (int q = 0; q < RW; ++q) acc[q] = cfma(L[(r0 + warp * RW + q) * ld + c], zc, acc[q]);
       }
-      for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
-        const int rr = idx / T, c = idx % T;
-        Lt[rr * (T + 1) + c] = L[(r0 + rr) * ld + r0 + c];
-      }
-      __syncthreads();
-      // unit lower solve inside the tile: lane owns rows lane and lane + 32
+    }
+#pragma unroll
+    for (int q = 0; q < RW; ++q) {
+      const S v = warp_sum(acc[q]);
+      if (lane == 0) zi[warp * RW + q] = csub(ldcg(z + (int64_t)(r0 + warp * RW + q) * nrhs + j), v);
+    }
+    __syncthreads();
+    if (i < nte) {
       if (warp == 0) {
-        S v0 = z[(int64_t)(r0 + lane) * nrhs + j];
-        S v1 = z[(int64_t)(r0 + lane + 32) * nrhs + j];
+        S v0 = zi[lane], v1 = zi[lane + 32];
         for (int c = 0; c < T; ++c) {
-          const int owner = c & 31;
-          S xc;
           const S src = (c < 32) ? v0 : v1;
-          xc.x = __shfl_sync(0xffffffffu, src.x, owner);
-          xc.y = __shfl_sync(0xffffffffu, src.y, owner);
-          if (lane > c) v0 = cfms(Lt[lane * (T + 1) + c], xc, v0);
-          if (lane + 32 > c) v1 = cfms(Lt[(lane + 32) * (T + 1) + c], xc, v1);
+          S xc;
+          xc.x = __shfl_sync(0xffffffffu, src.x, c & 31);
+          xc.y = __shfl_sync(0xffffffffu, src.y, c & 31);
+          if (lane > c) v0 = cfms(Lt[tri(lane, c)], xc, v0);
+          if (lane + 32 > c) v1 = cfms(Lt[tri(lane + 32, c)], xc, v1);
         }
-        z[(int64_t)(r0 + lane) * nrhs + j] = v0;
-        z[(int64_t)(r0 + lane + 32) * nrhs + j] = v1;
+        zi[lane] = v0;
+        zi[lane + 32] = v1;
       }
       __syncthreads();
     }
-    // update rows: z_u -= L_ue z_e
-    for (int rr = warp; rr < F.nu; rr += nw) {
-      const int r = F.ne_pad + rr;
-      S acc = czero<S>();
-      for (int c = lane; c < F.ne_pad; c += 32) acc = cfma(L[r * ld + c], z[(int64_t)c * nrhs + j], acc);
-      acc = warp_sum(acc);
-      if (lane == 0) z[(int64_t)r * nrhs + j] = csub(z[(int64_t)r * nrhs + j], acc);
-    }
+    if (threadIdx.x < T) z[(int64_t)(r0 + threadIdx.x) * nrhs + j] = zi[threadIdx.x];
     __syncthreads();
-    for (int r = threadIdx.x; r < F.ne_pad; r += blockDim.x)
-      z[(int64_t)r * nrhs + j] = cdiv(z[(int64_t)r * nrhs + j], L[r * (ld + 1)]);
+  }
+  if (i < nte) {
+    __threadfence();
     __syncthreads();
+    if (threadIdx.x == 0) st_release(flg + i, epoch);
   }
 }
 
-// backward substitution of one front per CTA; node fronts publish their
-// separator solution into lam (dual id order)
+// Backward substitution, one CTA per (front, eliminated column tile j), tasks
+// ordered by decreasing j.  y_j = D_j^{-1} z_j - L_uj^T x_u (update rows: the
+// already solved ancestor duals) - sum_{i>j} L_ij^T x_i (as tiles i finish),
+// then x_j = L_jj^{-T} y_j.  Node fronts publish x into lam.
 template <typename S>
 __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rpool, const FrontDev* fr,
-                                                            const int32_t* fids, int nrhs, const int32_t* upd,
-                                                            const int32_t* sep, S* lam, int64_t ld_lam) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  S* Lt = reinterpret_cast<S*>(smem_raw);
-  const FrontDev F = fr[fids[blockIdx.x]];
+                                                            const Task* tasks, int nrhs, const int32_t* upd,
+                                                            const int32_t* sep, S* lam, int64_t ld_lam,
+                                                            int32_t* flags, int epoch, DevStatus* st) {
+  __shared__ S Lt[T * (T + 1) / 2];
+  __shared__ S part[SOLVE_THREADS];
+  __shared__ S yj[T];
+  const Task t = tasks[blockIdx.x];
+  const FrontDev F = fr[t.f];
   const S* L = pool + F.off;
   S* z = rpool + F.roff * nrhs;
   const int64_t ld = F.ld;
   const int nte = F.ne_pad / T;
+  const int j = t.i, c0 = j * T;
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  for (int j = 0; j < nrhs; ++j) {
-    // known ancestor duals on the update rows
-    for (int rr = threadIdx.x; rr < F.nu; rr += blockDim.x)
-      z[(int64_t)(F.ne_pad + rr) * nrhs + j] = lam[upd[F.upd_off + rr] + j * ld_lam];
+  const int col = threadIdx.x % T, grp = threadIdx.x / T;  // 64 columns x 4 row groups
+  constexpr int NG = SOLVE_THREADS / T;
+  int32_t* flg = flags + F.tile_off;
+  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+    const int rr = idx / T, c = idx % T;
+    if (c <= rr) Lt[tri(rr, c)] = L[(c0 + rr) * ld + c0 + c];
+  }
+  for (int jj = 0; jj < nrhs; ++jj) {
+    S acc = czero<S>();
+    for (int u = grp; u < F.nu; u += NG)
+      acc = cfma(L[(F.ne_pad + u) * ld + c0 + col], ldcg(lam + upd[F.upd_off + u] + jj * ld_lam), acc);
+    for (int i = nte - 1; i > j; --i) {
+      if (jj == 0 && !wait_ready(flg + i, epoch, st, t.f, i)) return;
+      for (int rr = grp; rr < T; rr += NG) {
+        const int r = i * T + rr;
+        acc = cfma(L[r * ld + c0 + col], ldcg(z + (int64_t)r * nrhs + jj), acc);
+      }
+    }
+    part[threadIdx.x] = acc;
     __syncthreads();
-    for (int c = threadIdx.x; c < F.ne_pad; c += blockDim.x) {
-      S acc = czero<S>();
-      for (int rr = 0; rr < F.nu; ++rr)
-        acc = cfma(L[(F.ne_pad + rr) * ld + c], z[(int64_t)(F.ne_pad + rr) * nrhs + j], acc);
-      z[(int64_t)c * nrhs + j] = csub(z[(int64_t)c * nrhs + j], acc);
+    if (threadIdx.x < T) {
+      S sum = part[threadIdx.x];
+#pragma unroll
+      for (int g = 1; g < NG; ++g) sum = cadd(sum, part[g * T + threadIdx.x]);
+      const S d = Lt[tri(threadIdx.x, threadIdx.x)];
+      yj[threadIdx.x] = csub(cdiv(ldcg(z + (int64_t)(c0 + threadIdx.x) * nrhs + jj), d), sum);
     }
     __syncthreads();
-    for (int t = nte - 1; t >= 0; --t) {
-      const int r0 = t * T;
-      for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
-        const int rr = idx / T, c = idx % T;
-        Lt[rr * (T + 1) + c] = L[(r0 + rr) * ld + r0 + c];
+    if (warp == 0) {
+      S v0 = yj[lane], v1 = yj[lane + 32];
+      for (int c = T - 1; c >= 0; --c) {
+        const S src = (c < 32) ? v0 : v1;
+        S xc;
+        xc.x = __shfl_sync(0xffffffffu, src.x, c & 31);
+        xc.y = __shfl_sync(0xffffffffu, src.y, c & 31);
+        if (lane < c) v0 = cfms(Lt[tri(c, lane)], xc, v0);
+        if (lane + 32 < c) v1 = cfms(Lt[tri(c, lane + 32)], xc, v1);
       }
-      __syncthreads();
-      if (warp == 0) {
-        S v0 = z[(int64_t)(r0 + lane) * nrhs + j];
-        S v1 = z[(int64_t)(r0 + lane + 32) * nrhs + j];
-        for (int c = T - 1; c >= 0; --c) {
-          const int owner = c & 31;
-          S xc;
-          const S src = (c < 32) ? v0 : v1;
-          xc.x = __shfl_sync(0xffffffffu, src.x, owner);
-          xc.y = __shfl_sync(0xffffffffu, src.y, owner);
-          if (lane < c) v0 = cfms(Lt[c * (T + 1) + lane], xc, v0);
-          if (lane + 32 < c) v1 = cfms(Lt[c * (T + 1) + lane + 32], xc, v1);
-        }
-        z[(int64_t)(r0 + lane) * nrhs + j] = v0;
-        z[(int64_t)(r0 + lane + 32) * nrhs + j] = v1;
-      }
-      __syncthreads();
-      for (int c = threadIdx.x; c < r0; c += blockDim.x) {
-        S acc = czero<S>();
-        for (int rr = 0; rr < T; ++rr) acc = cfma(L[(r0 + rr) * ld + c], z[(int64_t)(r0 + rr) * nrhs + j], acc);
-        z[(int64_t)c * nrhs + j] = csub(z[(int64_t)c * nrhs + j], acc);
-      }
-      __syncthreads();
+      yj[lane] = v0;
+      yj[lane + 32] = v1;
     }
-    if (F.kind == 1)
-      for (int r = threadIdx.x; r < F.ne; r += blockDim.x) lam[sep[F.sep_off + r] + j * ld_lam] = z[(int64_t)r * nrhs + j];
+    __syncthreads();
+    if (threadIdx.x < T) {
+      const int r = c0 + threadIdx.x;
+      z[(int64_t)r * nrhs + jj] = yj[threadIdx.x];
+      if (F.kind == 1 && r < F.ne) lam[sep[F.sep_off + r] + jj * ld_lam] = yj[threadIdx.x];
+    }
     __syncthreads();
   }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) st_release(flg + j, epoch);
 }
 
 template <typename S>
@@ -274,18 +345,6 @@ __global__ void k_sumsq(const double2* x, int64_t n, double* out) {
   if (threadIdx.x == 0) out[blockIdx.x] = sh[0];
 }
 
-template <typename S> constexpr int tile_smem() { return T * (T + 1) * (int)sizeof(S); }
-
-template <typename S>
-void set_solve_attr() {
-  static bool done = false;
-  if (!done) {
-    cudaFuncSetAttribute(k_forward<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, tile_smem<S>());
-    cudaFuncSetAttribute(k_backward<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, tile_smem<S>());
-    done = true;
-  }
-}
-
 }  // namespace
 
 void launch_rhs_leaf(int prec, void* rpool, const FrontDev* fronts, const LeafDev* leaves, int n_leaves,
@@ -309,33 +368,27 @@ void launch_rhs_extend_add(int prec, void* rpool, const FrontDev* fronts, const 
   else k_rhs_extend_add<float2><<<n, 256, 0, s>>>((float2*)rpool, fronts, ids, slot, maps, nrhs);
 }
 
-void launch_forward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const int32_t* fids, int n,
-                    int nrhs, cudaStream_t s) {
+void launch_forward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const Task* tasks, int n,
+                    int nrhs, int32_t* flags, int epoch, DevStatus* st, cudaStream_t s) {
   if (n <= 0) return;
-  if (prec == 0) {
-    set_solve_attr<double2>();
-    k_forward<double2><<<n, SOLVE_THREADS, tile_smem<double2>(), s>>>((const double2*)pool, (double2*)rpool, fronts,
-                                                                       fids, nrhs);
-  } else {
-    set_solve_attr<float2>();
-    k_forward<float2><<<n, SOLVE_THREADS, tile_smem<float2>(), s>>>((const float2*)pool, (float2*)rpool, fronts,
-                                                                     fids, nrhs);
-  }
+  if (prec == 0)
+    k_forward<double2><<<n, SOLVE_THREADS, 0, s>>>((const double2*)pool, (double2*)rpool, fronts, tasks, nrhs, flags,
+                                                   epoch, st);
+  else
+    k_forward<float2><<<n, SOLVE_THREADS, 0, s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs, flags,
+                                                  epoch, st);
 }
 
-void launch_backward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const int32_t* fids, int n,
+void launch_backward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const Task* tasks, int n,
                      int nrhs, const int32_t* upd, const int32_t* sep, void* lam_work, int64_t ld_lam,
-                     cudaStream_t s) {
+                     int32_t* flags, int epoch, DevStatus* st, cudaStream_t s) {
   if (n <= 0) return;
-  if (prec == 0) {
-    set_solve_attr<double2>();
-    k_backward<double2><<<n, SOLVE_THREADS, tile_smem<double2>(), s>>>(
-        (const double2*)pool, (double2*)rpool, fronts, fids, nrhs, upd, sep, (double2*)lam_work, ld_lam);
-  } else {
-    set_solve_attr<float2>();
-    k_backward<float2><<<n, SOLVE_THREADS, tile_smem<float2>(), s>>>(
-        (const float2*)pool, (float2*)rpool, fronts, fids, nrhs, upd, sep, (float2*)lam_work, ld_lam);
-  }
+  if (prec == 0)
+    k_backward<double2><<<n, SOLVE_THREADS, 0, s>>>((const double2*)pool, (double2*)rpool, fronts, tasks, nrhs, upd,
+                                                    sep, (double2*)lam_work, ld_lam, flags, epoch, st);
+  else
+    k_backward<float2><<<n, SOLVE_THREADS, 0, s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs, upd, sep,
+                                                   (float2*)lam_work, ld_lam, flags, epoch, st);
 }
 
 void launch_leaf_out(int prec, const void* rpool, const FrontDev* fronts, const LeafDev* leaves, int n_leaves,
