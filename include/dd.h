@@ -176,6 +176,34 @@ const char* dd_strerror(int code);
 /* Release the handle and all its device memory.  NULL is a no-op. */
 void dd_free(dd_handle* h);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free dense solve.  The paper has no counterpart: this is a
+ * service for callers that cannot allocate device memory once they are
+ * running (an application whose own allocator owns all device memory, or a
+ * loop that cannot afford cudaMalloc's implicit synchronisation or failure).
+ *
+ * Solves A X = B for one dense complex-symmetric A (A = A^T, lower triangle
+ * read, unpivoted LDL^T in FP64 with the same kernels as dd_factor/dd_solve).
+ *   n      1..DD_NOALLOC_MAX_N;  nrhs  1..DD_NOALLOC_MAX_NRHS
+ *   A      DEVICE memory, n x n column-major, leading dimension lda >= n
+ *   b      DEVICE memory, n x nrhs column-major (ldb >= n)
+ *   x      DEVICE memory, n x nrhs column-major (ldx >= n), written
+ *   cuda_stream  stream for all work (NULL = legacy default stream)
+ * Allocates nothing: all scratch is one static device array of about 4.3 MB
+ * that every GPU loading this library holds until the process exits.  The
+ * first call on a device looks up that array's device address; make that
+ * first call before any stream capture.  Every call clears what must start
+ * at zero, but all calls share the one array: calls that overlap on the GPU
+ * (other streams, other host threads) race and must be serialised by the
+ * caller.  Returns after the stream has finished the solve.  Errors:
+ * DD_ERR_INVALID_ARG (sizes beyond the limits, NULL or host pointers),
+ * DD_ERR_SINGULAR_PIVOT, DD_ERR_TIMEOUT, DD_ERR_CUDA.
+ * ------------------------------------------------------------------------- */
+#define DD_NOALLOC_MAX_N 512
+#define DD_NOALLOC_MAX_NRHS 16
+int dd_dense_solve_noalloc(int32_t n, const dd_c128* A, int64_t lda, int32_t nrhs, const dd_c128* b,
+                           int64_t ldb, dd_c128* x, int64_t ldx, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif
