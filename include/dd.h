@@ -96,6 +96,8 @@ typedef struct {
   int32_t device;           /* CUDA device ordinal */
   int32_t time_kernels;     /* 1: dd_factor brackets every launch with CUDA events and reports
                                per-kernel-class device time in dd_stats (slower; default 0) */
+  int32_t simt_update;      /* MIXED: 1 runs the trailing updates on the FP32 FMA pipes instead of
+                               the tensor cores (comparison baseline; default 0) */
 } dd_options;
 
 /* Kernel classes of dd_stats.kernel_ms / kernel_launches / kernel_flops. */

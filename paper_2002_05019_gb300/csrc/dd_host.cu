@@ -32,8 +32,8 @@ inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 struct StepRange {
   int k;
-  int64_t diag_off, trsm_off, upd_off;
-  int n_diag, n_trsm, n_upd;
+  int64_t diag_off, trsm_off, upd_off, tc_off;
+  int n_diag, n_trsm, n_upd, n_tc;
 };
 
 struct Level {
@@ -122,6 +122,10 @@ struct dd_handle {
   int32_t *d_level_ids = nullptr, *d_diag_ids = nullptr;
   Task *d_trsm = nullptr, *d_updt = nullptr;
   Task *d_fwd = nullptr, *d_bwd = nullptr;
+  Task* d_tc = nullptr;            // tensor-core update tasks (mixed form)
+  unsigned char* d_ws = nullptr;   // panel operand images (mixed form)
+  size_t ws_bytes = 0;
+  int use_tc = 0;
   int32_t *d_flag_f = nullptr, *d_flag_b = nullptr;
   int64_t n_tiles = 0;
   int epoch = 0;
@@ -413,6 +417,7 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
   h->n_dual = n_dual;
   h->elem = opt.precision == DD_PREC_FP64 ? 16 : 8;
   h->time_kernels = opt.time_kernels ? 1 : 0;
+  h->use_tc = (opt.precision == DD_PREC_MIXED && !opt.simt_update) ? 1 : 0;
   h->max_abs_a = std::max(amax, 1.0);
   cudaStream_t s = h->stream;
 
@@ -631,8 +636,25 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
   h->levels.assign(max_h + 1, Level{});
   for (int x = 0; x < n_front; ++x)
     if (h->fronts[x].ld > 0 || x < n_sub) h->levels[height[x]].ids.push_back(x);
+  // mixed form: panel image workspace, reused level after level
+  if (h->use_tc) {
+    size_t need = 0;
+    for (auto& L : h->levels) {
+      int64_t w = 0;
+      for (int f : L.ids) {
+        FrontDev& F = h->fronts[f];
+        const int64_t ntr = F.ld / T - 1;  // trailing tiles at the first step
+        F.ws_off = w;
+        w += ((ntr + 1) / 2) * (int64_t)DD_TC_ABLOCK;
+        F.ws_boff = w;
+        w += ntr * (int64_t)DD_TC_BTILE;
+      }
+      need = std::max(need, (size_t)w);
+    }
+    h->ws_bytes = need;
+  }
   std::vector<int32_t> h_level_ids, h_diag;
-  std::vector<Task> h_trsm, h_updt;
+  std::vector<Task> h_trsm, h_updt, h_tc;
   for (auto& L : h->levels) {
     L.ids_off = (int64_t)h_level_ids.size();
     h_level_ids.insert(h_level_ids.end(), L.ids.begin(), L.ids.end());
@@ -650,6 +672,7 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
       R.diag_off = (int64_t)h_diag.size();
       R.trsm_off = (int64_t)h_trsm.size();
       R.upd_off = (int64_t)h_updt.size();
+      R.tc_off = (int64_t)h_tc.size();
       for (int f : L.ids) {
         const FrontDev& F = h->fronts[f];
         const int nte = F.ne_pad / T, nt = F.ld / T;
@@ -664,6 +687,15 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
           for (int i = j; i < nt; ++i)
             if (!zero_tile(i)) h_updt.push_back(Task{f, i, j, 0});
         }
+        // tensor-core tasks: 128-row blocks (tiles i0, i0 + 1) x column tile j
+        if (h->use_tc)
+          for (int i0 = k + 1; i0 < nt; i0 += 2)
+            for (int j = k + 1; j <= std::min(i0 + 1, nt - 1); ++j) {
+              if (zero_tile(j)) continue;
+              const int lo = (i0 >= j && !zero_tile(i0)) ? 1 : 0;
+              const int hi = (i0 + 1 < nt && !zero_tile(i0 + 1)) ? 2 : 0;
+              if (lo | hi) h_tc.push_back(Task{f, i0, j, lo | hi});
+            }
       }
       R.n_diag = (int)((int64_t)h_diag.size() - R.diag_off);
       for (int64_t q = R.upd_off; q < (int64_t)h_updt.size(); ++q)
@@ -672,6 +704,7 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
       h->stats.kernel_flops[DD_K_DIAG] += 8.0 * ((int64_t)h_diag.size() - R.diag_off) * (double)T * T * T / 6.0;
       R.n_trsm = (int)((int64_t)h_trsm.size() - R.trsm_off);
       R.n_upd = (int)((int64_t)h_updt.size() - R.upd_off);
+      R.n_tc = (int)((int64_t)h_tc.size() - R.tc_off);
       L.steps.push_back(R);
     }
   }
@@ -734,6 +767,8 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
   DD_CUDA(A.upload(&h->d_trsm, h_trsm, s));
   DD_CUDA(A.upload(&h->d_updt, h_updt, s));
   DD_CUDA(A.upload(&h->d_fwd, h_fwd, s));
+  DD_CUDA(A.upload(&h->d_tc, h_tc, s));
+  if (h->use_tc) DD_CUDA(A.alloc(&h->d_ws, h->ws_bytes));
   DD_CUDA(A.upload(&h->d_bwd, h_bwd, s));
   DD_CUDA(A.alloc(&h->d_flag_f, (size_t)std::max<int64_t>(h->n_tiles, 1)));
   DD_CUDA(A.alloc(&h->d_flag_b, (size_t)std::max<int64_t>(h->n_tiles, 1)));
@@ -836,14 +871,18 @@ int dd_factor(dd_handle* h) {
       ddk::launch_diag(p, diag64, h->pool, h->d_fronts, h->d_diag_ids + R.diag_off, R.n_diag, R.k, h->d_status, s);
       DD_CUDA(mark(DD_K_DIAG, false));
       DD_CUDA(mark(DD_K_TRSM, true));
-      ddk::launch_trsm(p, h->pool, h->d_fronts, h->d_trsm + R.trsm_off, R.n_trsm, R.k, h->d_status, s);
+      ddk::launch_trsm(p, h->pool, h->d_fronts, h->d_trsm + R.trsm_off, R.n_trsm, R.k, h->d_status, s,
+                       h->use_tc ? h->d_ws : nullptr);
       DD_CUDA(mark(DD_K_TRSM, false));
       DD_CUDA(mark(DD_K_UPDATE, true));
-      ddk::launch_update(p, h->pool, h->d_fronts, h->d_updt + R.upd_off, R.n_upd, R.k, s);
+      if (h->use_tc)
+        ddk::launch_update_tc(h->pool, h->d_fronts, h->d_tc + R.tc_off, R.n_tc, R.k, h->d_ws, h->d_status, s);
+      else
+        ddk::launch_update(p, h->pool, h->d_fronts, h->d_updt + R.upd_off, R.n_upd, R.k, s);
       DD_CUDA(mark(DD_K_UPDATE, false));
       count(DD_K_DIAG, R.n_diag);
       count(DD_K_TRSM, R.n_trsm);
-      count(DD_K_UPDATE, R.n_upd);
+      count(DD_K_UPDATE, h->use_tc ? R.n_tc : R.n_upd);
     }
   }
   DD_CUDA(cudaGetLastError());
@@ -865,6 +904,7 @@ int dd_factor(dd_handle* h) {
   std::memcpy(&maxl, &st.max_abs_l, 8);
   h->stats.growth = std::max(maxd, maxl) / h->max_abs_a;
   h->stats.min_pivot = mind;
+  if (st.code == 8) return DD_ERR_TIMEOUT;
   if (st.code != 0) return DD_ERR_SINGULAR_PIVOT;
   h->factored = true;
   return DD_OK;

@@ -37,7 +37,19 @@ struct FrontDev {
   int32_t map_off[2];// node: offsets of the extend-add maps (child update row -> row here)
   int32_t tile_off;  // offset of this front's per-tile ready flags (ld / DD_TILE of them)
   int32_t pad_;
+  int64_t ws_off;    // mixed form: byte offset of this front's A operand images in the panel workspace
+  int64_t ws_boff;   // mixed form: byte offset of its B operand images
 };
+
+// Panel operand images for the tensor-core trailing update (mixed form).
+// A image of a 128-row block: planes (Re hi, Re lo, Im hi, Im lo) x 2 K-atoms of
+// 32 tf32 each, 16 KB per (plane, atom), 128B-swizzled K-major; the two 64-row
+// tiles of the block fill its first and second 8 KB half.  B image of a 64-row
+// column tile: split (hi, lo) x 2 K-atoms x [-Im W][Re W][Im W], 8 KB each.
+#define DD_TC_ATOM 16384
+#define DD_TC_HALF 8192
+#define DD_TC_ABLOCK (4 * 2 * DD_TC_ATOM)
+#define DD_TC_BTILE (2 * 2 * 3 * DD_TC_HALF)
 
 struct LeafDev {
   int64_t csr_off;   // offset of the domain's nonzeros in the concatenated CSR arrays
@@ -77,7 +89,11 @@ void launch_node_init(int prec, void* pool, const FrontDev* fronts, const int32_
 void launch_diag(int prec, int diag_fp64, void* pool, const FrontDev* fronts, const int32_t* fids, int n,
                  int k, DevStatus* st, cudaStream_t s);
 void launch_trsm(int prec, void* pool, const FrontDev* fronts, const Task* tasks, int n, int k,
-                 DevStatus* st, cudaStream_t s);
+                 DevStatus* st, cudaStream_t s, unsigned char* ws = nullptr);
+// tensor-core trailing update (mixed form): task (front, first row tile i0 of a
+// 128-row block, column tile j, store mask in .pad: bit 0 rows of i0, bit 1 rows of i0+1)
+void launch_update_tc(void* pool, const FrontDev* fronts, const Task* tasks, int n, int k,
+                      const unsigned char* ws, DevStatus* st, cudaStream_t s);
 void launch_update(int prec, void* pool, const FrontDev* fronts, const Task* tasks, int n, int k,
                    cudaStream_t s);
 void launch_extend_add(int prec, void* pool, const FrontDev* fronts, const int32_t* node_ids, int n,

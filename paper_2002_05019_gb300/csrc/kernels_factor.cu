@@ -20,6 +20,50 @@ constexpr int T = DD_TILE;
 
 __device__ __forceinline__ int tri(int i, int c) { return (i * (i + 1)) / 2 + c; }
 
+// byte offset of element (row, k), k in 0..31, in a 128B-swizzled K-major atom
+// (8-row groups of 1024 B; the 16-byte chunk index is XORed with row % 8)
+__device__ __forceinline__ int swz128(int row, int k) {
+  return (row >> 3) * 1024 + (row & 7) * 128 + ((((k >> 2) ^ (row & 7))) << 4) + (k & 3) * 4;
+}
+// x = hi + lo with hi, lo representable in tf32 (round to nearest, ties away)
+__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
+  uint32_t h, l;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+  const float r = x - __uint_as_float(h);
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(r));
+  hi = __uint_as_float(h);
+  lo = __uint_as_float(l);
+}
+__device__ __forceinline__ void put_img(unsigned char* base, int row, int k, float v) {
+  *reinterpret_cast<float*>(base + swz128(row, k)) = v;
+}
+
+template <typename S>
+__device__ __forceinline__ void write_images(unsigned char*, const FrontDev&, int, int, S, S) {}
+// mixed form: A planes of L_ik and B planes of W_ik = L_ik D_k for the tensor-core update
+template <>
+__device__ __forceinline__ void write_images<float2>(unsigned char* ws, const FrontDev& F, int ti, int rc, float2 L,
+                                                     float2 W) {
+  const int r = rc >> 6, p = rc & 63;              // row of the tile, K index
+  const int a = p >> 5, kk = p & 31;
+  unsigned char* Ab = ws + F.ws_off + (int64_t)(ti >> 1) * DD_TC_ABLOCK + (ti & 1) * DD_TC_HALF;
+  unsigned char* Bb = ws + F.ws_boff + (int64_t)ti * DD_TC_BTILE;
+  float h, l;
+  split_tf32(L.x, h, l);
+  put_img(Ab + (0 * 2 + a) * DD_TC_ATOM, r, kk, h);
+  put_img(Ab + (1 * 2 + a) * DD_TC_ATOM, r, kk, l);
+  split_tf32(L.y, h, l);
+  put_img(Ab + (2 * 2 + a) * DD_TC_ATOM, r, kk, h);
+  put_img(Ab + (3 * 2 + a) * DD_TC_ATOM, r, kk, l);
+  const float parts[3] = {-W.y, W.x, W.y};
+#pragma unroll
+  for (int v = 0; v < 3; ++v) {
+    split_tf32(parts[v], h, l);
+    put_img(Bb + ((0 * 2 + a) * 3 + v) * DD_TC_HALF, r, kk, h);
+    put_img(Bb + ((1 * 2 + a) * 3 + v) * DD_TC_HALF, r, kk, l);
+  }
+}
+
 __device__ void status_pivot(DevStatus* st, int front, int row) {
   if (atomicCAS(&st->code, 0, 3) == 0) {
     st->front = front;
@@ -134,7 +178,7 @@ __global__ void __launch_bounds__(256) k_diag(S* pool, const FrontDev* fr, const
 // ---------------------------------------------------------------------------
 template <typename S>
 __global__ void __launch_bounds__(256) k_trsm(S* pool, const FrontDev* fr, const Task* tasks, int k,
-                                              DevStatus* st) {
+                                              DevStatus* st, unsigned char* ws) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   S* Lt = reinterpret_cast<S*>(smem_raw);  // Lt[j * T + p] = L_kk[p][j]
   S* X = Lt + T * T;                       // X[p * (T + 1) + r] = row r, column p
@@ -162,7 +206,9 @@ __global__ void __launch_bounds__(256) k_trsm(S* pool, const FrontDev* fr, const
     const int rr = idx / T, p = idx % T;
     const S x = X[p * (T + 1) + rr];
     mx = fmax(mx, cabs2d(x));
-    Aik[(int64_t)rr * F.ld + p] = cmul(x, rinv[p]);
+    const S lv = cmul(x, rinv[p]);
+    Aik[(int64_t)rr * F.ld + p] = lv;
+    if (ws) write_images<S>(ws, F, t.i - k - 1, idx, lv, x);
   }
   // block max of |L D| for the growth statistic
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -292,14 +338,14 @@ void launch_diag(int prec, int diag_fp64, void* pool, const FrontDev* fronts, co
 }
 
 void launch_trsm(int prec, void* pool, const FrontDev* fronts, const Task* tasks, int n, int k, DevStatus* st,
-                 cudaStream_t s) {
+                 cudaStream_t s, unsigned char* ws) {
   if (n <= 0) return;
   if (prec == 0) {
     set_trsm_attr<double2>();
-    k_trsm<double2><<<n, 256, trsm_smem<double2>(), s>>>((double2*)pool, fronts, tasks, k, st);
+    k_trsm<double2><<<n, 256, trsm_smem<double2>(), s>>>((double2*)pool, fronts, tasks, k, st, nullptr);
   } else {
     set_trsm_attr<float2>();
-    k_trsm<float2><<<n, 256, trsm_smem<float2>(), s>>>((float2*)pool, fronts, tasks, k, st);
+    k_trsm<float2><<<n, 256, trsm_smem<float2>(), s>>>((float2*)pool, fronts, tasks, k, st, ws);
   }
 }
 

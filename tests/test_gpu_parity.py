@@ -175,3 +175,21 @@ def test_batched_512_domains_full_size(c2_linear, precision):
         assert np.array_equal(duals, do)
         assert rel(Fi, Fo) <= TOL_F[precision]
     s.free()
+
+
+def test_tensor_core_update_matches_simt_update(c1):
+    """The tcgen05 3xTF32 trailing update and the FP32 FMA-pipe update give the
+    same F_i to FP32 accuracy and both refine to the mixed tolerance."""
+    o = oracle.DDOracle(c1)
+    uo, _ = o.solve([s.f for s in c1.subs])
+    xo, _ = o.gather(uo)
+    res = {}
+    for simt in (False, True):
+        s = dd.Solver.from_problem(c1, precision="mixed", simt_update=simt)
+        s.factor()
+        u, _ = s.solve(dd.stacked_loads(c1))
+        assert rel(gather(c1, u), xo) <= TOL["mixed"]
+        res[simt] = [s.schur(i)[0] for i in range(c1.n_sub)]
+        s.free()
+    for a, b in zip(res[False], res[True]):
+        assert rel(a, b) <= 1e-5
