@@ -2,8 +2,8 @@
 // updates of the domain and auxiliary-matrix factorizations run as level-3
 // BLAS; here on the 5th-generation tensor cores).
 //
-// One CTA computes a 128 x 64 complex block of  C -= L_ik D_k L_jk^T  (rows of
-// the tiles i0 and i0+1, column tile j) with tcgen05.mma kind::tf32:
+// A task is a 128 x 64 complex block of  C -= L_ik D_k L_jk^T  (rows of the
+// tiles i0 and i0+1, column tile j), computed with tcgen05.mma kind::tf32:
 //   * complex product as one real GEMM with a [Re | Im] accumulator:
 //       acc[:, 0:64]   = Lr Wr^T - Li Wi^T,   acc[:, 64:128] = Lr Wi^T + Li Wr^T
 //     = Lr [Wr; Wi]^T + Li [-Wi; Wr]^T  (B operands of N = 128 rows);
@@ -12,8 +12,8 @@
 //     panel kernel, brought into shared memory by bulk asynchronous copies
 //     (TMA engine) completing on an mbarrier; the accumulator lives in TMEM
 //     (128 lanes x 128 fp32 columns) and is read back with tcgen05.ld.
-// Every wait is bounded: on timeout the CTA records DD_ERR_TIMEOUT, waits once
-// more (bounded) for its copies, frees its TMEM and returns.
+// Every wait is bounded: on timeout the CTA records DD_ERR_TIMEOUT, its roles
+// stop, and it frees its TMEM and returns.
 #include "dd_complex.cuh"
 #include "dd_internal.h"
 
@@ -24,7 +24,6 @@ namespace {
 constexpr int T = DD_TILE;
 constexpr int kA = DD_TC_ABLOCK;   // 128 KB
 constexpr int kB = DD_TC_BTILE;    // 96 KB
-constexpr int kSmem = kA + kB + 1024;
 constexpr int kWaitPolls = 1 << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -67,31 +66,49 @@ __device__ __forceinline__ void tmem_ld32(uint32_t ta, uint32_t (&r)[32]) {
       : "r"(ta));
 }
 
-__global__ void __launch_bounds__(128, 1) k_update_tc(float2* pool, const FrontDev* fr, const Task* tasks, int k,
-                                                      const unsigned char* ws, DevStatus* st) {
+// Persistent, warp-specialised form: grid = one CTA per SM, tasks taken
+// round-robin.  Warp 0 lane 0 loads operand stages (one K-atom of A and B per
+// stage, two stages in shared memory), warp 1 lane 0 issues the MMAs into one
+// of two TMEM accumulators, warps 2-5 drain the other accumulator into C.
+constexpr int kStageA = 4 * DD_TC_ATOM;          // 4 planes x 1 atom = 64 KB
+constexpr int kStageB = 2 * 3 * DD_TC_HALF;      // 2 splits x [-Wi][Wr][Wi] = 48 KB
+constexpr int kStage = kStageA + kStageB;        // 112 KB
+constexpr int kSmemP = 2 * kStage + 1024;
+
+struct PipeBars {
+  uint64_t full[2], empty[2], acc_full[2], acc_empty[2];
+};
+
+__device__ __forceinline__ void mbar_init(uint32_t b, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b) : "memory");
+}
+
+__global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontDev* fr, const Task* tasks, int n_tasks,
+                                                      int k, const unsigned char* ws, DevStatus* st) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
-  unsigned char* sA = smem;
-  unsigned char* sB = smem + kA;
-  __shared__ __align__(8) uint64_t bar_load, bar_mma;
+  __shared__ __align__(8) PipeBars bars;
   __shared__ uint32_t tmem_slot;
-  __shared__ int ok_sh;
+  __shared__ volatile int fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const Task t = tasks[blockIdx.x];
-  const FrontDev F = fr[t.f];
-  const uint32_t mb_load = smem_u32(&bar_load), mb_mma = smem_u32(&bar_mma);
-  const unsigned char* gA = ws + F.ws_off + (int64_t)((t.i - k - 1) >> 1) * kA;
-  const unsigned char* gB = ws + F.ws_boff + (int64_t)(t.j - k - 1) * kB;
-
+  const uint32_t b_full0 = smem_u32(&bars.full[0]), b_empty0 = smem_u32(&bars.empty[0]);
+  const uint32_t b_accf0 = smem_u32(&bars.acc_full[0]), b_acce0 = smem_u32(&bars.acc_empty[0]);
   if (tid == 0) {
-    ok_sh = 1;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_load));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_mma));
+    fail = 0;
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(b_full0 + 8 * i, 1);
+      mbar_init(b_empty0 + 8 * i, 1);
+      mbar_init(b_accf0 + 8 * i, 1);
+      mbar_init(b_acce0 + 8 * i, 4);   // one arrival per epilogue warp
+    }
     asm volatile("fence.mbarrier_init.release.cluster;");
     asm volatile("fence.proxy.async.shared::cta;");
   }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(&tmem_slot)));
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_u32(&tmem_slot)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -99,82 +116,121 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(float2* pool, const FrontD
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
 
-  if (tid == 0) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb_load), "r"(kA + kB) : "memory");
-    for (int c = 0; c < kA / DD_TC_ATOM; ++c)
-      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                       smem_u32(sA + c * DD_TC_ATOM)),
-                   "l"(gA + c * DD_TC_ATOM), "r"(DD_TC_ATOM), "r"(mb_load)
-                   : "memory");
-    for (int c = 0; c < kB / DD_TC_HALF; ++c)
-      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                       smem_u32(sB + c * DD_TC_HALF)),
-                   "l"(gB + c * DD_TC_HALF), "r"(DD_TC_HALF), "r"(mb_load)
-                   : "memory");
-    if (!mbar_wait(mb_load, 0)) {
-      ok_sh = 0;
-      mbar_wait(mb_load, 0);  // second bounded wait for the copies in flight
-    } else {
+  if (warp == 0 && lane == 0) {
+    // ---------------- producer ----------------
+    int u = 0;
+    for (int q = blockIdx.x; q < n_tasks && !fail; q += gridDim.x) {
+      const Task t = tasks[q];
+      const FrontDev F = fr[t.f];
+      const unsigned char* gA = ws + F.ws_off + (int64_t)((t.i - k - 1) >> 1) * kA;
+      const unsigned char* gB = ws + F.ws_boff + (int64_t)(t.j - k - 1) * kB;
+      for (int a = 0; a < 2; ++a, ++u) {
+        const int sidx = u & 1;
+        const uint32_t par = ((u >> 1) & 1) ^ 1;
+        if (!mbar_wait(b_empty0 + 8 * sidx, par)) { fail = 1; break; }
+        unsigned char* sA = smem + sidx * kStage;
+        unsigned char* sB = sA + kStageA;
+        const uint32_t fb = b_full0 + 8 * sidx;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(kStage) : "memory");
+        for (int pl = 0; pl < 4; ++pl)
+          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                           smem_u32(sA + pl * DD_TC_ATOM)),
+                       "l"(gA + (pl * 2 + a) * DD_TC_ATOM), "r"(DD_TC_ATOM), "r"(fb)
+                       : "memory");
+        for (int sp = 0; sp < 2; ++sp)
+          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                           smem_u32(sB + sp * 3 * DD_TC_HALF)),
+                       "l"(gB + (sp * 2 + a) * 3 * DD_TC_HALF), "r"(3 * DD_TC_HALF), "r"(fb)
+                       : "memory");
+      }
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer ----------------
+    int u = 0, tl = 0;
+    const int pl[6] = {0, 0, 1, 2, 2, 3};
+    const int bs[6] = {0, 1, 0, 0, 1, 0};
+    const int bv[6] = {1, 1, 1, 0, 0, 0};
+    for (int q = blockIdx.x; q < n_tasks && !fail; q += gridDim.x, ++tl) {
+      const int ab = tl & 1;
+      if (!mbar_wait(b_acce0 + 8 * ab, ((tl >> 1) & 1) ^ 1)) { fail = 1; break; }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
-      // (A plane, B split, B variant): variant 1 = [Wr; Wi] (+8 KB), 0 = [-Wi; Wr]
-      const int pl[6] = {0, 0, 1, 2, 2, 3};
-      const int bs[6] = {0, 1, 0, 0, 1, 0};
-      const int bv[6] = {1, 1, 1, 0, 0, 0};
+      const uint32_t dacc = tmem + ab * 128;
       uint32_t acc = 0;
-      for (int a = 0; a < 2; ++a)
-        for (int s = 0; s < 4; ++s)
+      for (int a = 0; a < 2; ++a, ++u) {
+        const int sidx = u & 1;
+        if (!mbar_wait(b_full0 + 8 * sidx, (u >> 1) & 1)) { fail = 1; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t a0 = smem_u32(smem + sidx * kStage), b0 = a0 + kStageA;
+        for (int s4 = 0; s4 < 4; ++s4)
 #pragma unroll
-          for (int q = 0; q < 6; ++q) {
-            const uint64_t ad = desc_sw128(a0 + (pl[q] * 2 + a) * DD_TC_ATOM + s * 32);
-            const uint64_t bd = desc_sw128(b0 + ((bs[q] * 2 + a) * 3 + bv[q]) * DD_TC_HALF + s * 32);
+          for (int qq = 0; qq < 6; ++qq) {
+            const uint64_t ad = desc_sw128(a0 + pl[qq] * DD_TC_ATOM + s4 * 32);
+            const uint64_t bd = desc_sw128(b0 + (bs[qq] * 3 + bv[qq]) * DD_TC_HALF + s4 * 32);
             asm volatile(
                 "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dacc),
                 "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
             acc = 1;
           }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb_mma)
+        // the stage is free once these MMAs have read it
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         b_empty0 + 8 * sidx)
+                     : "memory");
+      }
+      if (fail) break;
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b_accf0 + 8 * ab)
                    : "memory");
-      if (!mbar_wait(mb_mma, 0)) ok_sh = 0;
     }
-  }
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  if (ok_sh) {
-    // epilogue: warp w owns rows 32w..32w+31 (its TMEM lanes)
-    const int row = warp * 32 + lane;
-    const bool store = (row < T) ? (t.pad & 1) : (t.pad & 2);
-    float2* crow = pool + F.off + (int64_t)(t.i * T + row) * F.ld + t.j * T;
+  } else if (warp >= 2) {
+    // ---------------- epilogue: TMEM -> C -= acc ----------------
+    const int sub = warp & 3;                 // TMEM sub-partition of this warp
+    const int row = sub * 32 + lane;
+    int tl = 0;
+    for (int q = blockIdx.x; q < n_tasks; q += gridDim.x, ++tl) {
+      const Task t = tasks[q];
+      const FrontDev F = fr[t.f];
+      const int ab = tl & 1;
+      bool ok = !fail;
+      if (ok && lane == 0) ok = mbar_wait(b_accf0 + 8 * ab, (tl >> 1) & 1);
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok) { fail = 1; break; }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const bool store = (row < T) ? (t.pad & 1) : (t.pad & 2);
+      float2* crow = pool + F.off + (int64_t)(t.i * T + row) * F.ld + t.j * T;
 #pragma unroll 1
-    for (int h = 0; h < 2; ++h) {
-      uint32_t vr[32], vi[32];
-      const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + h * 32;
-      tmem_ld32(ta, vr);
-      tmem_ld32(ta + 64, vi);
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
-      if (store) {
-        float4* c4 = reinterpret_cast<float4*>(crow + h * 32);
+      for (int h = 0; h < 2; ++h) {
+        uint32_t vr[32], vi[32];
+        const uint32_t ta = tmem + ab * 128 + ((uint32_t)(sub * 32) << 16) + h * 32;
+        tmem_ld32(ta, vr);
+        tmem_ld32(ta + 64, vi);
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        if (store) {
+          float4* c4 = reinterpret_cast<float4*>(crow + h * 32);
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          float4 v = c4[q];
-          v.x -= __uint_as_float(vr[2 * q]);
-          v.y -= __uint_as_float(vi[2 * q]);
-          v.z -= __uint_as_float(vr[2 * q + 1]);
-          v.w -= __uint_as_float(vi[2 * q + 1]);
-          c4[q] = v;
+          for (int c = 0; c < 16; ++c) {
+            float4 v = c4[c];
+            v.x -= __uint_as_float(vr[2 * c]);
+            v.y -= __uint_as_float(vi[2 * c]);
+            v.z -= __uint_as_float(vr[2 * c + 1]);
+            v.w -= __uint_as_float(vi[2 * c + 1]);
+            c4[c] = v;
+          }
         }
       }
-    }
-  } else if (tid == 0) {
-    if (atomicCAS(&st->code, 0, 8) == 0) {
-      st->front = t.f;
-      st->row = t.i * T;
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(b_acce0 + 8 * ab);
     }
   }
-  asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem));
+  if (fail && tid == 0) {
+    if (atomicCAS(&st->code, 0, 8) == 0) {
+      st->front = -1;
+      st->row = k;
+    }
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem));
 }
 
 }  // namespace
@@ -182,12 +238,16 @@ __global__ void __launch_bounds__(128, 1) k_update_tc(float2* pool, const FrontD
 void launch_update_tc(void* pool, const FrontDev* fronts, const Task* tasks, int n, int k, const unsigned char* ws,
                       DevStatus* st, cudaStream_t s) {
   if (n <= 0) return;
-  static bool attr = false;
-  if (!attr) {
-    cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
-    attr = true;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+    cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemP);
   }
-  k_update_tc<<<n, 128, kSmem, s>>>((float2*)pool, fronts, tasks, k, ws, st);
+  const int grid = n < sms ? n : sms;
+  k_update_tc<<<grid, 192, kSmemP, s>>>((float2*)pool, fronts, tasks, n, k, ws, st);
 }
 
 }  // namespace ddk
