@@ -124,6 +124,7 @@ struct dd_handle {
   Task *d_fwd = nullptr, *d_bwd = nullptr;
   Task* d_tc = nullptr;            // tensor-core update tasks (mixed form)
   unsigned char* d_ws = nullptr;   // panel operand images (mixed form)
+  float2* d_linv = nullptr;        // mixed form: L_kk^{-1} of the current diagonal tile, per front
   size_t ws_bytes = 0;
   int use_tc = 0;
   int32_t *d_flag_f = nullptr, *d_flag_b = nullptr;
@@ -769,6 +770,7 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
   DD_CUDA(A.upload(&h->d_fwd, h_fwd, s));
   DD_CUDA(A.upload(&h->d_tc, h_tc, s));
   if (h->use_tc) DD_CUDA(A.alloc(&h->d_ws, h->ws_bytes));
+  if (h->prec == DD_PREC_MIXED) DD_CUDA(A.alloc(&h->d_linv, (size_t)n_front * T * T));
   DD_CUDA(A.upload(&h->d_bwd, h_bwd, s));
   DD_CUDA(A.alloc(&h->d_flag_f, (size_t)std::max<int64_t>(h->n_tiles, 1)));
   DD_CUDA(A.alloc(&h->d_flag_b, (size_t)std::max<int64_t>(h->n_tiles, 1)));
@@ -868,11 +870,18 @@ int dd_factor(dd_handle* h) {
     const int diag64 = (l > 0) ? 1 : 0;  // mixed form: FP64 pivot blocks of the auxiliary matrix
     for (const StepRange& R : L.steps) {
       DD_CUDA(mark(DD_K_DIAG, true));
-      ddk::launch_diag(p, diag64, h->pool, h->d_fronts, h->d_diag_ids + R.diag_off, R.n_diag, R.k, h->d_status, s);
+      if (p == 0)
+        ddk::launch_diag(p, 0, h->pool, h->d_fronts, h->d_diag_ids + R.diag_off, R.n_diag, R.k, h->d_status, s);
+      else
+        ddk::launch_diag_mx(diag64, h->pool, h->d_fronts, h->d_diag_ids + R.diag_off, R.n_diag, R.k, h->d_status,
+                            h->d_linv, s);
       DD_CUDA(mark(DD_K_DIAG, false));
       DD_CUDA(mark(DD_K_TRSM, true));
-      ddk::launch_trsm(p, h->pool, h->d_fronts, h->d_trsm + R.trsm_off, R.n_trsm, R.k, h->d_status, s,
-                       h->use_tc ? h->d_ws : nullptr);
+      if (p == 0)
+        ddk::launch_trsm(p, h->pool, h->d_fronts, h->d_trsm + R.trsm_off, R.n_trsm, R.k, h->d_status, s, nullptr);
+      else
+        ddk::launch_trsm_mx(h->pool, h->d_fronts, h->d_trsm + R.trsm_off, R.n_trsm, R.k, h->d_status, h->d_linv,
+                            h->use_tc ? h->d_ws : nullptr, s);
       DD_CUDA(mark(DD_K_TRSM, false));
       DD_CUDA(mark(DD_K_UPDATE, true));
       if (h->use_tc)

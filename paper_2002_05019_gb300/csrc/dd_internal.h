@@ -90,6 +90,12 @@ void launch_diag(int prec, int diag_fp64, void* pool, const FrontDev* fronts, co
                  int k, DevStatus* st, cudaStream_t s);
 void launch_trsm(int prec, void* pool, const FrontDev* fronts, const Task* tasks, int n, int k,
                  DevStatus* st, cudaStream_t s, unsigned char* ws = nullptr);
+// mixed form: 64 x 64 diagonal tile with 32 x 32 pivot blocks (FP64 if
+// diag_fp64) and L_kk^{-1} (FP32, 64 x 64 per front id) for the panel product
+void launch_diag_mx(int diag_fp64, void* pool, const FrontDev* fronts, const int32_t* fids, int n, int k,
+                    DevStatus* st, void* linv, cudaStream_t s);
+void launch_trsm_mx(void* pool, const FrontDev* fronts, const Task* tasks, int n, int k, DevStatus* st,
+                    const void* linv, unsigned char* ws, cudaStream_t s);
 // tensor-core trailing update (mixed form): task (front, first row tile i0 of a
 // 128-row block, column tile j, store mask in .pad: bit 0 rows of i0, bit 1 rows of i0+1)
 void launch_update_tc(void* pool, const FrontDev* fronts, const Task* tasks, int n, int k,

@@ -173,6 +173,202 @@ __global__ void __launch_bounds__(256) k_diag(S* pool, const FrontDev* fr, const
 }
 
 // ---------------------------------------------------------------------------
+// mixed form diagonal tile: the 64 x 64 tile is factored as 2 x 2 blocks of
+// 32; the two 32 x 32 pivot blocks in precision C (FP64 for the auxiliary
+// matrix, FP32 for the domains), the off-diagonal block solve and the Schur
+// update of the second pivot block in FP32.  Also writes L_kk^{-1} (FP32) for
+// the panel kernel, which then is a product instead of a substitution.
+// ---------------------------------------------------------------------------
+constexpr int PB = 32;
+
+template <typename C>
+__device__ void factor_pivot32(float2* a, int jb, C* ap, C* w, C* rinv, int nthreads) {
+  // ap: packed lower 32 x 32 in precision C; a: packed lower 64 x 64 tile (FP32)
+  for (int idx = threadIdx.x; idx < PB * PB; idx += nthreads) {
+    const int i = idx / PB, c = idx % PB;
+    if (c <= i) ap[tri(i, c)] = cconv<C>(a[tri(jb + i, jb + c)]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *rinv = cdiv(cmake<C>(1, 0), ap[0]);
+  __syncthreads();
+  const int row = threadIdx.x >> 3, sub = threadIdx.x & 7;   // 8 threads per row
+  for (int j = 0; j < PB; ++j) {
+    if (sub == 0 && row > j && row < PB) {
+      const C v = ap[tri(row, j)];
+      w[row] = v;
+      ap[tri(row, j)] = cmul(v, *rinv);
+    }
+    __syncthreads();
+    if (row > j && row < PB) {
+      const C l = ap[tri(row, j)];
+      for (int c = j + 1 + sub; c <= row; c += 8) ap[tri(row, c)] = cfms(l, w[c], ap[tri(row, c)]);
+      if (row == j + 1 && sub == 0) *rinv = cdiv(cmake<C>(1, 0), ap[tri(j + 1, j + 1)]);
+    }
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < PB * PB; idx += nthreads) {
+    const int i = idx / PB, c = idx % PB;
+    if (c <= i) a[tri(jb + i, jb + c)] = cconv<float2>(ap[tri(i, c)]);
+  }
+  __syncthreads();
+}
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_diag_mx(float2* pool, const FrontDev* fr, const int32_t* fids, int k,
+                                                 DevStatus* st, float2* linv) {
+  __shared__ float2 a[T * (T + 1) / 2];
+  __shared__ C ap[PB * (PB + 1) / 2];
+  __shared__ C w[PB];
+  __shared__ C rinv;
+  __shared__ float2 d1inv[PB];
+  // x21 (unscaled A21 L11^{-T}, 32 x 33) and later L^{-1} (packed lower 64 x 64) share storage
+  __shared__ float2 scratch[T * (T + 1) / 2];
+  float2 (*x21)[PB + 1] = reinterpret_cast<float2 (*)[PB + 1]>(scratch);
+  float2* li = scratch;
+  const int f = fids[blockIdx.x];
+  const FrontDev F = fr[f];
+  float2* base = pool + F.off + (int64_t)(k * T) * F.ld + k * T;
+  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+    const int i = idx / T, c = idx % T;
+    if (c <= i) a[tri(i, c)] = base[(int64_t)i * F.ld + c];
+  }
+  __syncthreads();
+  factor_pivot32<C>(a, 0, ap, w, &rinv, blockDim.x);
+  // X = A21 L11^{-T}, column by column; then L21 = X D1^{-1}
+  {
+    const int r = threadIdx.x & (PB - 1), g = threadIdx.x >> 5;   // 8 column groups
+    for (int idx = threadIdx.x; idx < PB * PB; idx += blockDim.x) {
+      const int rr = idx / PB, c = idx % PB;
+      x21[rr][c] = a[tri(PB + rr, c)];
+    }
+    if (threadIdx.x < PB) d1inv[threadIdx.x] = cdiv(make_float2(1.f, 0.f), a[tri(threadIdx.x, threadIdx.x)]);
+    __syncthreads();
+    for (int j = 0; j < PB - 1; ++j) {
+      const float2 xj = x21[r][j];
+      for (int p = j + 1 + ((g - j - 1) & 7); p < PB; p += 8) x21[r][p] = cfms(xj, a[tri(p, j)], x21[r][p]);
+      __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < PB * PB; idx += blockDim.x) {
+      const int rr = idx / PB, c = idx % PB;
+      a[tri(PB + rr, c)] = cmul(x21[rr][c], d1inv[c]);
+    }
+    __syncthreads();
+    // A22 -= L21 X^T (lower part)
+    for (int idx = threadIdx.x; idx < PB * PB; idx += blockDim.x) {
+      const int i = idx / PB, c = idx % PB;
+      if (c <= i) {
+        float2 acc = a[tri(PB + i, PB + c)];
+        for (int q = 0; q < PB; ++q) acc = cfms(a[tri(PB + i, q)], x21[c][q], acc);
+        a[tri(PB + i, PB + c)] = acc;
+      }
+    }
+    __syncthreads();
+  }
+  factor_pivot32<C>(a, PB, ap, w, &rinv, blockDim.x);
+  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+    const int i = idx / T, c = idx % T;
+    if (c <= i) base[(int64_t)i * F.ld + c] = a[tri(i, c)];
+  }
+  // L^{-1} of the unit lower tile, column by column: 4 lanes per column share the dot products
+  {
+    const int col = threadIdx.x >> 2, part = threadIdx.x & 3;
+    __syncthreads();   // x21 is dead from here on
+    if (part == 0) li[tri(col, col)] = make_float2(1.f, 0.f);
+    __syncwarp();
+    // the loop bound is uniform over the warp (its 8 columns start at col0)
+    const int col0 = (threadIdx.x >> 5) * 8;
+    for (int i = col0 + 1; i < T; ++i) {
+      float2 acc = make_float2(0.f, 0.f);
+      if (i > col)
+        for (int q = col + part; q < i; q += 4) acc = cfma(a[tri(i, q)], li[tri(q, col)], acc);
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
+      if (part == 0 && i > col) li[tri(i, col)] = make_float2(-acc.x, -acc.y);
+      __syncwarp();
+    }
+    __syncthreads();
+    float2* out = linv + (int64_t)f * T * T;
+    for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+      const int i = idx / T, c = idx % T;
+      out[idx] = c <= i ? li[tri(i, c)] : make_float2(0.f, 0.f);
+    }
+  }
+  if (threadIdx.x < T) {
+    const int r = k * T + threadIdx.x;
+    if (r < F.ne) {
+      const double m2 = cabs2d(a[tri(threadIdx.x, threadIdx.x)]);
+      if (!(m2 > 0.0) || !isfinite(m2)) status_pivot(st, f, r);
+      const double m = sqrt(m2);
+      if (isfinite(m)) {
+        atomic_max_pos(&st->max_abs_d, m);
+        atomic_min_pos(&st->min_abs_d, m);
+      }
+    }
+  }
+}
+
+// mixed form panel: X = A_ik L_kk^{-T} as a product with the stored inverse,
+// L_ik = X D_k^{-1}; 4 x 4 register blocking like the trailing update
+__global__ void __launch_bounds__(256) k_trsm_mx(float2* pool, const FrontDev* fr, const Task* tasks, int k,
+                                                 DevStatus* st, const float2* linv, unsigned char* ws) {
+  constexpr int KC = 32;
+  __shared__ float2 As[KC][T + 1];
+  __shared__ float2 Bs[KC][T + 1];
+  __shared__ float2 rinv[T];
+  const Task t = tasks[blockIdx.x];
+  const FrontDev F = fr[t.f];
+  const int64_t ld = F.ld;
+  float2* Aik = pool + F.off + (int64_t)(t.i * T) * ld + k * T;
+  const float2* Li = linv + (int64_t)t.f * T * T;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  if (threadIdx.x < T)
+    rinv[threadIdx.x] = cdiv(make_float2(1.f, 0.f), pool[F.off + (int64_t)(k * T + threadIdx.x) * (ld + 1)]);
+  float2 acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(0.f, 0.f);
+  for (int kc = 0; kc < T; kc += KC) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < T * KC; idx += blockDim.x) {
+      const int r = idx / KC, kk = idx % KC;
+      As[kk][r] = Aik[(int64_t)r * ld + kc + kk];
+      Bs[kk][r] = Li[r * T + kc + kk];   // Linv[p][q], p = r
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < KC; ++kk) {
+      float2 av[4], bv[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) av[r] = As[kk][ty + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) bv[c] = Bs[kk][tx + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = cfma(av[r], bv[c], acc[r][c]);
+    }
+  }
+  __syncthreads();
+  double mx = 0.0;
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int rr = ty + 16 * r, p = tx + 16 * c;
+      const float2 x = acc[r][c];
+      mx = fmax(mx, cabs2d(x));
+      const float2 lv = cmul(x, rinv[p]);
+      Aik[(int64_t)rr * ld + p] = lv;
+      if (ws) write_images<float2>(ws, F, t.i - k - 1, rr * T + p, lv, x);
+    }
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx > 0.0 && isfinite(mx)) atomic_max_pos(&st->max_abs_l, sqrt(mx));
+}
+
+// ---------------------------------------------------------------------------
 // panel: X = A_ik L_kk^{-T} (= L_ik D_k), then L_ik = X D_k^{-1}
 // dynamic shared memory: Lt[64][64] (Lt[j][p] = L_kk[p][j]) + X[64][65] + d[64]
 // ---------------------------------------------------------------------------
@@ -335,6 +531,19 @@ void launch_diag(int prec, int diag_fp64, void* pool, const FrontDev* fronts, co
   if (prec == 0) k_diag<double2, double2><<<n, 256, 0, s>>>((double2*)pool, fronts, fids, k, st);
   else if (diag_fp64) k_diag<float2, double2><<<n, 256, 0, s>>>((float2*)pool, fronts, fids, k, st);
   else k_diag<float2, float2><<<n, 256, 0, s>>>((float2*)pool, fronts, fids, k, st);
+}
+
+void launch_diag_mx(int diag_fp64, void* pool, const FrontDev* fronts, const int32_t* fids, int n, int k,
+                    DevStatus* st, void* linv, cudaStream_t s) {
+  if (n <= 0) return;
+  if (diag_fp64) k_diag_mx<double2><<<n, 256, 0, s>>>((float2*)pool, fronts, fids, k, st, (float2*)linv);
+  else k_diag_mx<float2><<<n, 256, 0, s>>>((float2*)pool, fronts, fids, k, st, (float2*)linv);
+}
+
+void launch_trsm_mx(void* pool, const FrontDev* fronts, const Task* tasks, int n, int k, DevStatus* st,
+                    const void* linv, unsigned char* ws, cudaStream_t s) {
+  if (n <= 0) return;
+  k_trsm_mx<<<n, 256, 0, s>>>((float2*)pool, fronts, tasks, k, st, (const float2*)linv, ws);
 }
 
 void launch_trsm(int prec, void* pool, const FrontDev* fronts, const Task* tasks, int n, int k, DevStatus* st,
