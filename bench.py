@@ -209,7 +209,7 @@ def backward_error(p, u):
 def time_form(p, precision, args, torch, stream):
     import paper_2002_05019_gb300 as dd
     s = dd.Solver.from_problem(p, precision=precision, stream=stream.cuda_stream, device=torch.cuda.current_device(),
-                               time_kernels=True)
+                               time_kernels=True, refine_tol=args.refine_tol)
     f_host = dd.stacked_loads(p)
     f_dev = torch.from_numpy(f_host).cuda()
     for _ in range(args.warmup):
@@ -325,7 +325,7 @@ def ours_arm(args):
                    "l2": "working set (front pool) far larger than the 129 MB L2",
                    "parallelism": f"replicas x{ws}"},
         "tflops": flops_step / t_step / 1e12,
-        "refine_iters": iters, "backward_error": main["backward_error"],
+        "refine_iters": iters, "refine_tol": args.refine_tol, "backward_error": main["backward_error"],
         "roofline": roofline,
         "gpu_launches": main["launches"],
         "clocks": main["clocks"],
@@ -365,6 +365,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--refine-tol", type=float, default=1e-11,
+                    help="mixed form: stop refinement at this relative correction (1e-11 keeps the error <= 1e-10)")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)

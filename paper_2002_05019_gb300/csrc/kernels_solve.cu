@@ -79,7 +79,7 @@ __device__ __forceinline__ void st_release(int32_t* p, int v) {
   asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Wait until *flag >= epoch.  Bounded: after ~2^22 polls (about a second) the
+// Wait until *flag >= epoch.  Bounded: after 2^24 polls (about a second) the
 // wait gives up, records DD_ERR_TIMEOUT (8) in the status word and returns
 // false; the caller then returns without publishing its own flag.
 __device__ bool wait_ready(const int32_t* flag, int epoch, DevStatus* st, int front, int tile) {
@@ -88,7 +88,7 @@ __device__ bool wait_ready(const int32_t* flag, int epoch, DevStatus* st, int fr
     int it = 0;
     ok = 1;
     while (ld_acquire(flag) < epoch) {
-      if (++it > (1 << 22)) {
+      if (++it > (1 << 24)) {
         if (atomicCAS(&st->code, 0, 8) == 0) {
           st->front = front;
           st->row = tile;
@@ -96,7 +96,7 @@ __device__ bool wait_ready(const int32_t* flag, int epoch, DevStatus* st, int fr
         ok = 0;
         break;
       }
-      __nanosleep(128);
+      if (it > 4096) __nanosleep(64);   // spin first: most waits are short
     }
   }
   __syncthreads();
@@ -223,6 +223,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rp
       acc = cfma(L[(F.ne_pad + u) * ld + c0 + col], ldcg(lam + upd[F.upd_off + u] + jj * ld_lam), acc);
     for (int i = nte - 1; i > j; --i) {
       if (jj == 0 && !wait_ready(flg + i, epoch, st, t.f, i)) return;
+#pragma unroll
       for (int rr = grp; rr < T; rr += NG) {
         const int r = i * T + rr;
         acc = cfma(L[r * ld + c0 + col], ldcg(z + (int64_t)r * nrhs + jj), acc);

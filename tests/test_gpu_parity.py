@@ -193,3 +193,19 @@ def test_tensor_core_update_matches_simt_update(c1):
         s.free()
     for a, b in zip(res[False], res[True]):
         assert rel(a, b) <= 1e-5
+
+
+def test_refinement_stop_at_1e11_meets_1e10(c1, c2_linear):
+    """Stopping the FP64 refinement at a relative correction of 1e-11 (the
+    benchmark setting) still gives <= 1e-10 error: against the oracle on the
+    8-domain mesh and against the closed form on the 512-domain mesh."""
+    o = oracle.DDOracle(c1)
+    uo, _ = o.solve([s.f for s in c1.subs])
+    xo, _ = o.gather(uo)
+    for p, ref in ((c1, xo), (c2_linear, c2_linear.x_exact)):
+        s = dd.Solver.from_problem(p, precision="mixed", refine_tol=1e-11)
+        s.factor()
+        u, _ = s.solve(dd.stacked_loads(p))
+        assert rel(gather(p, u), ref) <= TOL["mixed"]
+        assert s.stats()["refine_last"] <= 1e-11
+        s.free()
