@@ -34,6 +34,7 @@ struct StepRange {
   int k;
   int64_t diag_off, trsm_off, upd_off, tc_off;
   int n_diag, n_trsm, n_upd, n_tc;
+  int n_upd_next, n_tc_next;   // the first tasks of each list update only the next panel column (j = k + 1)
 };
 
 struct Level {
@@ -125,6 +126,8 @@ struct dd_handle {
   Task* d_tc = nullptr;            // tensor-core update tasks (mixed form)
   unsigned char* d_ws = nullptr;   // panel operand images (mixed form)
   float2* d_linv = nullptr;        // mixed form: L_kk^{-1} of the current diagonal tile, per front
+  cudaStream_t s2 = nullptr;       // look-ahead: bulk trailing updates run here
+  cudaEvent_t ev_panel = nullptr, ev_rest = nullptr;
   size_t ws_bytes = 0;
   int use_tc = 0;
   int32_t *d_flag_f = nullptr, *d_flag_b = nullptr;
@@ -155,6 +158,9 @@ struct dd_handle {
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
     for (cudaEvent_t e : kev) cudaEventDestroy(e);
+    if (ev_panel) cudaEventDestroy(ev_panel);
+    if (ev_rest) cudaEventDestroy(ev_rest);
+    if (s2) cudaStreamDestroy(s2);
   }
 };
 
@@ -674,6 +680,7 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
       R.trsm_off = (int64_t)h_trsm.size();
       R.upd_off = (int64_t)h_updt.size();
       R.tc_off = (int64_t)h_tc.size();
+      std::vector<Task> upd_next, upd_rest, tc_next, tc_rest;
       for (int f : L.ids) {
         const FrontDev& F = h->fronts[f];
         const int nte = F.ne_pad / T, nt = F.ld / T;
@@ -686,7 +693,7 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
         for (int j = k + 1; j < nt; ++j) {
           if (zero_tile(j)) continue;
           for (int i = j; i < nt; ++i)
-            if (!zero_tile(i)) h_updt.push_back(Task{f, i, j, 0});
+            if (!zero_tile(i)) (j == k + 1 ? upd_next : upd_rest).push_back(Task{f, i, j, 0});
         }
         // tensor-core tasks: 128-row blocks (tiles i0, i0 + 1) x column tile j
         if (h->use_tc)
@@ -695,9 +702,15 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
               if (zero_tile(j)) continue;
               const int lo = (i0 >= j && !zero_tile(i0)) ? 1 : 0;
               const int hi = (i0 + 1 < nt && !zero_tile(i0 + 1)) ? 2 : 0;
-              if (lo | hi) h_tc.push_back(Task{f, i0, j, lo | hi});
+              if (lo | hi) (j == k + 1 ? tc_next : tc_rest).push_back(Task{f, i0, j, lo | hi});
             }
       }
+      R.n_upd_next = (int)upd_next.size();
+      R.n_tc_next = (int)tc_next.size();
+      h_updt.insert(h_updt.end(), upd_next.begin(), upd_next.end());
+      h_updt.insert(h_updt.end(), upd_rest.begin(), upd_rest.end());
+      h_tc.insert(h_tc.end(), tc_next.begin(), tc_next.end());
+      h_tc.insert(h_tc.end(), tc_rest.begin(), tc_rest.end());
       R.n_diag = (int)((int64_t)h_diag.size() - R.diag_off);
       for (int64_t q = R.upd_off; q < (int64_t)h_updt.size(); ++q)
         h->stats.kernel_flops[DD_K_UPDATE] += 8.0 * T * (h_updt[q].i == h_updt[q].j ? T * (T + 1) / 2 : T * T);
@@ -769,7 +782,10 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
   DD_CUDA(A.upload(&h->d_updt, h_updt, s));
   DD_CUDA(A.upload(&h->d_fwd, h_fwd, s));
   DD_CUDA(A.upload(&h->d_tc, h_tc, s));
-  if (h->use_tc) DD_CUDA(A.alloc(&h->d_ws, h->ws_bytes));
+  if (h->use_tc) DD_CUDA(A.alloc(&h->d_ws, 2 * h->ws_bytes));   // two step parities (look-ahead)
+  DD_CUDA(cudaStreamCreateWithFlags(&h->s2, cudaStreamNonBlocking));
+  DD_CUDA(cudaEventCreateWithFlags(&h->ev_panel, cudaEventDisableTiming));
+  DD_CUDA(cudaEventCreateWithFlags(&h->ev_rest, cudaEventDisableTiming));
   if (h->prec == DD_PREC_MIXED) DD_CUDA(A.alloc(&h->d_linv, (size_t)n_front * T * T));
   DD_CUDA(A.upload(&h->d_bwd, h_bwd, s));
   DD_CUDA(A.alloc(&h->d_flag_f, (size_t)std::max<int64_t>(h->n_tiles, 1)));
@@ -826,7 +842,7 @@ int dd_factor(dd_handle* h) {
   constexpr size_t kMaxTimed = 8192;
   size_t nev = 0;
   std::vector<int> cls_of(h->time_kernels ? kMaxTimed : 0);
-  auto mark = [&](int cls, bool begin) -> cudaError_t {
+  auto mark_on = [&](int cls, bool begin, cudaStream_t on) -> cudaError_t {
     if (!h->time_kernels || nev >= 2 * kMaxTimed) return cudaSuccess;
     if (begin) cls_of[nev / 2] = cls;
     while (h->kev.size() <= nev) {
@@ -835,8 +851,9 @@ int dd_factor(dd_handle* h) {
       if (err != cudaSuccess) return err;
       h->kev.push_back(e);
     }
-    return cudaEventRecord(h->kev[nev++], s);
+    return cudaEventRecord(h->kev[nev++], on);
   };
+  auto mark = [&](int cls, bool begin) { return mark_on(cls, begin, s); };
   for (int c = 0; c < DD_K_NCLASS; ++c) {
     h->stats.kernel_ms[c] = 0.0;
     h->stats.kernel_launches[c] = 0;
@@ -868,30 +885,69 @@ int dd_factor(dd_handle* h) {
       count(DD_K_ASSEMBLE, n);
     }
     const int diag64 = (l > 0) ? 1 : 0;  // mixed form: FP64 pivot blocks of the auxiliary matrix
-    for (const StepRange& R : L.steps) {
-      DD_CUDA(mark(DD_K_DIAG, true));
+    // one-step look-ahead on levels with few fronts: the main stream updates
+    // only the next panel column and factors that panel, while the second
+    // stream applies the rest of the trailing update of the current step
+    const bool ahead = L.ids.size() <= 32 && L.steps.size() > 1;
+    const int reserve = ahead ? 16 : 0;   // SMs left free for the panel chain
+    auto panel = [&](const StepRange& R) -> cudaError_t {
+      unsigned char* ws = h->use_tc ? h->d_ws + (size_t)(R.k & 1) * h->ws_bytes : nullptr;
+      cudaError_t e = mark(DD_K_DIAG, true);
+      if (e != cudaSuccess) return e;
       if (p == 0)
         ddk::launch_diag(p, 0, h->pool, h->d_fronts, h->d_diag_ids + R.diag_off, R.n_diag, R.k, h->d_status, s);
       else
         ddk::launch_diag_mx(diag64, h->pool, h->d_fronts, h->d_diag_ids + R.diag_off, R.n_diag, R.k, h->d_status,
                             h->d_linv, s);
-      DD_CUDA(mark(DD_K_DIAG, false));
-      DD_CUDA(mark(DD_K_TRSM, true));
+      if ((e = mark(DD_K_DIAG, false)) != cudaSuccess) return e;
+      if ((e = mark(DD_K_TRSM, true)) != cudaSuccess) return e;
       if (p == 0)
         ddk::launch_trsm(p, h->pool, h->d_fronts, h->d_trsm + R.trsm_off, R.n_trsm, R.k, h->d_status, s, nullptr);
       else
-        ddk::launch_trsm_mx(h->pool, h->d_fronts, h->d_trsm + R.trsm_off, R.n_trsm, R.k, h->d_status, h->d_linv,
-                            h->use_tc ? h->d_ws : nullptr, s);
-      DD_CUDA(mark(DD_K_TRSM, false));
-      DD_CUDA(mark(DD_K_UPDATE, true));
-      if (h->use_tc)
-        ddk::launch_update_tc(h->pool, h->d_fronts, h->d_tc + R.tc_off, R.n_tc, R.k, h->d_ws, h->d_status, s);
-      else
-        ddk::launch_update(p, h->pool, h->d_fronts, h->d_updt + R.upd_off, R.n_upd, R.k, s);
-      DD_CUDA(mark(DD_K_UPDATE, false));
+        ddk::launch_trsm_mx(h->pool, h->d_fronts, h->d_trsm + R.trsm_off, R.n_trsm, R.k, h->d_status, h->d_linv, ws,
+                            s);
       count(DD_K_DIAG, R.n_diag);
       count(DD_K_TRSM, R.n_trsm);
-      count(DD_K_UPDATE, h->use_tc ? R.n_tc : R.n_upd);
+      return mark(DD_K_TRSM, false);
+    };
+    // trailing update of step R.k, tasks [first, first + n) of its lists, on stream `on`
+    auto update = [&](const StepRange& R, bool next_part, cudaStream_t on, int cap) -> cudaError_t {
+      const unsigned char* ws = h->use_tc ? h->d_ws + (size_t)(R.k & 1) * h->ws_bytes : nullptr;
+      const int n = h->use_tc ? (next_part ? R.n_tc_next : R.n_tc - R.n_tc_next)
+                              : (next_part ? R.n_upd_next : R.n_upd - R.n_upd_next);
+      const int64_t first = h->use_tc ? R.tc_off + (next_part ? 0 : R.n_tc_next)
+                                      : R.upd_off + (next_part ? 0 : R.n_upd_next);
+      cudaError_t e = mark_on(DD_K_UPDATE, true, on);
+      if (e != cudaSuccess) return e;
+      if (h->use_tc)
+        ddk::launch_update_tc(h->pool, h->d_fronts, h->d_tc + first, n, R.k, ws, h->d_status, on, cap);
+      else
+        ddk::launch_update(p, h->pool, h->d_fronts, h->d_updt + first, n, R.k, on);
+      count(DD_K_UPDATE, n);
+      return mark_on(DD_K_UPDATE, false, on);
+    };
+    const size_t ns = L.steps.size();
+    if (!ahead) {
+      for (const StepRange& R : L.steps) {
+        DD_CUDA(panel(R));
+        DD_CUDA(update(R, true, s, 0));
+        DD_CUDA(update(R, false, s, 0));
+      }
+    } else {
+      DD_CUDA(panel(L.steps[0]));
+      DD_CUDA(cudaEventRecord(h->ev_panel, s));
+      for (size_t q = 0; q < ns; ++q) {
+        const StepRange& R = L.steps[q];
+        DD_CUDA(cudaStreamWaitEvent(h->s2, h->ev_panel, 0));
+        DD_CUDA(update(R, false, h->s2, reserve));            // columns >= k + 2
+        DD_CUDA(cudaEventRecord(h->ev_rest, h->s2));
+        DD_CUDA(update(R, true, s, 0));                       // column k + 1
+        if (q + 1 < ns) {
+          DD_CUDA(panel(L.steps[q + 1]));
+          DD_CUDA(cudaEventRecord(h->ev_panel, s));
+        }
+        DD_CUDA(cudaStreamWaitEvent(s, h->ev_rest, 0));
+      }
     }
   }
   DD_CUDA(cudaGetLastError());

@@ -99,7 +99,7 @@ void launch_trsm_mx(void* pool, const FrontDev* fronts, const Task* tasks, int n
 // tensor-core trailing update (mixed form): task (front, first row tile i0 of a
 // 128-row block, column tile j, store mask in .pad: bit 0 rows of i0, bit 1 rows of i0+1)
 void launch_update_tc(void* pool, const FrontDev* fronts, const Task* tasks, int n, int k,
-                      const unsigned char* ws, DevStatus* st, cudaStream_t s);
+                      const unsigned char* ws, DevStatus* st, cudaStream_t s, int reserve_sms = 0);
 void launch_update(int prec, void* pool, const FrontDev* fronts, const Task* tasks, int n, int k,
                    cudaStream_t s);
 void launch_extend_add(int prec, void* pool, const FrontDev* fronts, const int32_t* node_ids, int n,

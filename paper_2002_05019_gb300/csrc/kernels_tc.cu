@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
 }  // namespace
 
 void launch_update_tc(void* pool, const FrontDev* fronts, const Task* tasks, int n, int k, const unsigned char* ws,
-                      DevStatus* st, cudaStream_t s) {
+                      DevStatus* st, cudaStream_t s, int reserve_sms) {
   if (n <= 0) return;
   static int sms = 0;
   if (!sms) {
@@ -246,7 +246,8 @@ void launch_update_tc(void* pool, const FrontDev* fronts, const Task* tasks, int
     if (sms <= 0) sms = 1;
     cudaFuncSetAttribute(k_update_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemP);
   }
-  const int grid = n < sms ? n : sms;
+  const int avail = sms - reserve_sms > 1 ? sms - reserve_sms : 1;
+  const int grid = n < avail ? n : avail;
   k_update_tc<<<grid, 192, kSmemP, s>>>((float2*)pool, fronts, tasks, n, k, ws, st);
 }
 
