@@ -125,7 +125,7 @@ struct dd_handle {
   Task *d_fwd = nullptr, *d_bwd = nullptr;
   Task* d_tc = nullptr;            // tensor-core update tasks (mixed form)
   unsigned char* d_ws = nullptr;   // panel operand images (mixed form)
-  float2* d_linv = nullptr;        // mixed form: L_kk^{-1} of the current diagonal tile, per front
+  float2* d_linv = nullptr;        // mixed form: L_kk^{-1} of every diagonal tile (index tile_off + k)
   cudaStream_t s2 = nullptr;       // look-ahead: bulk trailing updates run here
   cudaEvent_t ev_panel = nullptr, ev_rest = nullptr;
   size_t ws_bytes = 0;
@@ -332,13 +332,13 @@ void direct_solve(dd_handle* h, int nrhs, const double2* f, int64_t ldf, const d
       h->launches += 3;
     }
     ddk::launch_forward(p, h->pool, h->rpool, h->d_fronts, h->d_fwd + L.fwd_off, L.n_fwd, nrhs, h->d_flag_f, ep,
-                        h->d_solve_status, s);
+                        h->d_solve_status, s, h->d_linv);
     h->launches += 1;
   }
   for (size_t l = h->levels.size(); l-- > 0;) {
     const Level& L = h->levels[l];
     ddk::launch_backward(p, h->pool, h->rpool, h->d_fronts, h->d_bwd + L.bwd_off, L.n_bwd, nrhs, h->d_upd, h->d_sep,
-                         h->lam_work, h->n_dual, h->d_flag_b, ep, h->d_solve_status, s);
+                         h->lam_work, h->n_dual, h->d_flag_b, ep, h->d_solve_status, s, h->d_linv);
     h->launches += 1;
   }
   ddk::launch_leaf_out(p, h->rpool, h->d_fronts, h->d_leaves, h->n_sub, h->d_perm, u, h->n_loc, nrhs, 0, s);
@@ -786,7 +786,8 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
   DD_CUDA(cudaStreamCreateWithFlags(&h->s2, cudaStreamNonBlocking));
   DD_CUDA(cudaEventCreateWithFlags(&h->ev_panel, cudaEventDisableTiming));
   DD_CUDA(cudaEventCreateWithFlags(&h->ev_rest, cudaEventDisableTiming));
-  if (h->prec == DD_PREC_MIXED) DD_CUDA(A.alloc(&h->d_linv, (size_t)n_front * T * T));
+  // mixed form: L^{-1} of every diagonal tile (panel products and the substitution)
+  if (h->prec == DD_PREC_MIXED) DD_CUDA(A.alloc(&h->d_linv, (size_t)std::max<int64_t>(h->n_tiles, 1) * T * T));
   DD_CUDA(A.upload(&h->d_bwd, h_bwd, s));
   DD_CUDA(A.alloc(&h->d_flag_f, (size_t)std::max<int64_t>(h->n_tiles, 1)));
   DD_CUDA(A.alloc(&h->d_flag_b, (size_t)std::max<int64_t>(h->n_tiles, 1)));
@@ -1021,10 +1022,20 @@ int dd_solve(dd_handle* h, int32_t nrhs, const dd_c128* f, int64_t ldf, dd_c128*
     double sdu = 0, su = 0;
     for (int q = 0; q < nb1; ++q) sdu += part[q];
     for (int q = 0; q < nb2; ++q) su += part[512 + q];
+    const double prev = ratio;
     ratio = su > 0 ? std::sqrt(sdu / su) : 0.0;
     iters = it + 1;
     if (!std::isfinite(ratio)) break;
     if (ratio <= h->refine_tol) break;
+    // linear convergence: the error left after this update is about
+    // |du_k| * (|du_k| / |du_{k-1}|); stop once that estimate is within tolerance
+    if (it > 0 && prev > 0 && ratio < prev) {
+      const double est = ratio * (ratio / prev);
+      if (est <= h->refine_tol) {
+        ratio = est;
+        break;
+      }
+    }
   }
   if (h->prec == DD_PREC_MIXED && h->max_refine > 0 && !(ratio <= h->refine_tol)) status = DD_ERR_NOT_CONVERGED;
   DD_CUDA(cudaMemcpy2DAsync(u, (size_t)ldu * 16, h->d_u, row_b, row_b, nrhs,

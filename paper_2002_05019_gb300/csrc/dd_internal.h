@@ -114,11 +114,14 @@ void launch_rhs_extend_add(int prec, void* rpool, const FrontDev* fronts, const 
                            int slot, const int32_t* maps, int nrhs, cudaStream_t s);
 // tile-parallel substitution: one CTA per (front, tile) task of a level; a
 // CTA waits (bounded) on the ready flags of the tiles it depends on
+// linv (mixed form, optional): FP32 inverses of the unit-lower diagonal tiles,
+// index tile_off + tile; when given, the in-tile triangular solves are products
 void launch_forward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const Task* tasks, int n,
-                    int nrhs, int32_t* flags, int epoch, DevStatus* st, cudaStream_t s);
+                    int nrhs, int32_t* flags, int epoch, DevStatus* st, cudaStream_t s,
+                    const void* linv = nullptr);
 void launch_backward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const Task* tasks, int n,
                      int nrhs, const int32_t* upd, const int32_t* sep, void* lam_work, int64_t ld_lam,
-                     int32_t* flags, int epoch, DevStatus* st, cudaStream_t s);
+                     int32_t* flags, int epoch, DevStatus* st, cudaStream_t s, const void* linv = nullptr);
 void launch_leaf_out(int prec, const void* rpool, const FrontDev* fronts, const LeafDev* leaves,
                      int n_leaves, const int32_t* perm, double2* u, int64_t ldu, int nrhs, int accumulate,
                      cudaStream_t s);

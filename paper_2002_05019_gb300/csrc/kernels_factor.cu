@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(256) k_diag_mx(float2* pool, const FrontDev* f
       __syncwarp();
     }
     __syncthreads();
-    float2* out = linv + (int64_t)f * T * T;
+    float2* out = linv + ((int64_t)F.tile_off + k) * T * T;
     for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
       const int i = idx / T, c = idx % T;
       out[idx] = c <= i ? li[tri(i, c)] : make_float2(0.f, 0.f);
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(256) k_trsm_mx(float2* pool, const FrontDev* f
   const FrontDev F = fr[t.f];
   const int64_t ld = F.ld;
   float2* Aik = pool + F.off + (int64_t)(t.i * T) * ld + k * T;
-  const float2* Li = linv + (int64_t)t.f * T * T;
+  const float2* Li = linv + ((int64_t)F.tile_off + k) * T * T;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   if (threadIdx.x < T)
     rinv[threadIdx.x] = cdiv(make_float2(1.f, 0.f), pool[F.off + (int64_t)(k * T + threadIdx.x) * (ld + 1)]);

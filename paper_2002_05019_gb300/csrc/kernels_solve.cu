@@ -123,7 +123,7 @@ __device__ __forceinline__ float2 ldcg<float2>(const float2* p) { return __ldcg(
 template <typename S>
 __global__ void __launch_bounds__(SOLVE_THREADS) k_forward(const S* pool, S* rpool, const FrontDev* fr,
                                                            const Task* tasks, int nrhs, int32_t* flags, int epoch,
-                                                           DevStatus* st) {
+                                                           DevStatus* st, const S* linv) {
   __shared__ S Lt[T * (T + 1) / 2];
   __shared__ S zi[T];
   const Task t = tasks[blockIdx.x];
@@ -137,7 +137,8 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_forward(const S* pool, S* rpo
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   int32_t* flg = flags + F.tile_off;
   constexpr int RW = T / (SOLVE_THREADS / 32);  // rows per warp
-  if (i < nte) {
+  const S* Li = (linv != nullptr && i < nte) ? linv + ((int64_t)F.tile_off + i) * T * T : nullptr;
+  if (i < nte && Li == nullptr) {
     for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
       const int rr = idx / T, c = idx % T;
       if (c <= rr) Lt[tri(rr, c)] = L[(r0 + rr) * ld + r0 + c];
@@ -164,7 +165,23 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_forward(const S* pool, S* rpo
       if (lane == 0) zi[warp * RW + q] = csub(ldcg(z + (int64_t)(r0 + warp * RW + q) * nrhs + j), v);
     }
     __syncthreads();
-    if (i < nte) {
+    if (i < nte && Li != nullptr) {
+      // z_i = L_ii^{-1} z_i: 4 lanes per row, 16 terms each
+      const int row = threadIdx.x >> 2, part = threadIdx.x & 3;
+      S acc = czero<S>();
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int c = part * 16 + q;
+        if (c <= row) acc = cfma(Li[row * T + c], zi[c], acc);
+      }
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
+      __syncthreads();
+      if (part == 0) zi[row] = acc;
+      __syncthreads();
+    } else if (i < nte) {
       if (warp == 0) {
         S v0 = zi[lane], v1 = zi[lane + 32];
         for (int c = 0; c < T; ++c) {
@@ -198,7 +215,7 @@ template <typename S>
 __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rpool, const FrontDev* fr,
                                                             const Task* tasks, int nrhs, const int32_t* upd,
                                                             const int32_t* sep, S* lam, int64_t ld_lam,
-                                                            int32_t* flags, int epoch, DevStatus* st) {
+                                                            int32_t* flags, int epoch, DevStatus* st, const S* linv) {
   __shared__ S Lt[T * (T + 1) / 2];
   __shared__ S part[SOLVE_THREADS];
   __shared__ S yj[T];
@@ -213,9 +230,14 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rp
   const int col = threadIdx.x % T, grp = threadIdx.x / T;  // 64 columns x 4 row groups
   constexpr int NG = SOLVE_THREADS / T;
   int32_t* flg = flags + F.tile_off;
-  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
-    const int rr = idx / T, c = idx % T;
-    if (c <= rr) Lt[tri(rr, c)] = L[(c0 + rr) * ld + c0 + c];
+  const S* Li = linv != nullptr ? linv + ((int64_t)F.tile_off + j) * T * T : nullptr;
+  if (Li == nullptr) {
+    for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+      const int rr = idx / T, c = idx % T;
+      if (c <= rr) Lt[tri(rr, c)] = L[(c0 + rr) * ld + c0 + c];
+    }
+  } else if (threadIdx.x < T) {
+    Lt[tri(threadIdx.x, threadIdx.x)] = L[(c0 + threadIdx.x) * (ld + 1)];   // the pivots d
   }
   for (int jj = 0; jj < nrhs; ++jj) {
     S acc = czero<S>();
@@ -239,7 +261,22 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rp
       yj[threadIdx.x] = csub(cdiv(ldcg(z + (int64_t)(c0 + threadIdx.x) * nrhs + jj), d), sum);
     }
     __syncthreads();
-    if (warp == 0) {
+    if (Li != nullptr) {
+      // x_j = L_jj^{-T} y_j: x[c] = sum_{r >= c} Linv[r][c] y[r], 4 lanes per column
+      const int col2 = threadIdx.x >> 2, part = threadIdx.x & 3;
+      S acc = czero<S>();
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const int r = part * 16 + q;
+        if (r >= col2) acc = cfma(Li[r * T + col2], yj[r], acc);
+      }
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
+      __syncthreads();
+      if (part == 0) yj[col2] = acc;
+    } else if (warp == 0) {
       S v0 = yj[lane], v1 = yj[lane + 32];
       for (int c = T - 1; c >= 0; --c) {
         const S src = (c < 32) ? v0 : v1;
@@ -370,26 +407,26 @@ void launch_rhs_extend_add(int prec, void* rpool, const FrontDev* fronts, const 
 }
 
 void launch_forward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const Task* tasks, int n,
-                    int nrhs, int32_t* flags, int epoch, DevStatus* st, cudaStream_t s) {
+                    int nrhs, int32_t* flags, int epoch, DevStatus* st, cudaStream_t s, const void* linv) {
   if (n <= 0) return;
   if (prec == 0)
     k_forward<double2><<<n, SOLVE_THREADS, 0, s>>>((const double2*)pool, (double2*)rpool, fronts, tasks, nrhs, flags,
-                                                   epoch, st);
+                                                   epoch, st, nullptr);
   else
     k_forward<float2><<<n, SOLVE_THREADS, 0, s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs, flags,
-                                                  epoch, st);
+                                                  epoch, st, (const float2*)linv);
 }
 
 void launch_backward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const Task* tasks, int n,
                      int nrhs, const int32_t* upd, const int32_t* sep, void* lam_work, int64_t ld_lam,
-                     int32_t* flags, int epoch, DevStatus* st, cudaStream_t s) {
+                     int32_t* flags, int epoch, DevStatus* st, cudaStream_t s, const void* linv) {
   if (n <= 0) return;
   if (prec == 0)
     k_backward<double2><<<n, SOLVE_THREADS, 0, s>>>((const double2*)pool, (double2*)rpool, fronts, tasks, nrhs, upd,
-                                                    sep, (double2*)lam_work, ld_lam, flags, epoch, st);
+                                                    sep, (double2*)lam_work, ld_lam, flags, epoch, st, nullptr);
   else
     k_backward<float2><<<n, SOLVE_THREADS, 0, s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs, upd, sep,
-                                                   (float2*)lam_work, ld_lam, flags, epoch, st);
+                                                   (float2*)lam_work, ld_lam, flags, epoch, st, (const float2*)linv);
 }
 
 void launch_leaf_out(int prec, const void* rpool, const FrontDev* fronts, const LeafDev* leaves, int n_leaves,
