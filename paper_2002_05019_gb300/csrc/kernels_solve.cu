@@ -201,9 +201,11 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_forward(const S* pool, S* rpo
     __syncthreads();
   }
   if (i < nte) {
-    __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) st_release(flg + i, epoch);
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release(flg + i, epoch);
+    }
   }
 }
 
@@ -297,9 +299,11 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rp
     }
     __syncthreads();
   }
-  __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) st_release(flg + j, epoch);
+  if (threadIdx.x == 0) {
+    __threadfence();
+    st_release(flg + j, epoch);
+  }
 }
 
 template <typename S>

@@ -205,16 +205,15 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
         tmem_ld32(ta + 64, vi);
         asm volatile("tcgen05.wait::ld.sync.aligned;");
         if (store) {
-          float4* c4 = reinterpret_cast<float4*>(crow + h * 32);
+          // C -= acc as vector reductions performed in L2: no load of C on
+          // the SM; each element receives exactly one addition per launch
+          float* c4 = reinterpret_cast<float*>(crow + h * 32);
 #pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            float4 v = c4[c];
-            v.x -= __uint_as_float(vr[2 * c]);
-            v.y -= __uint_as_float(vi[2 * c]);
-            v.z -= __uint_as_float(vr[2 * c + 1]);
-            v.w -= __uint_as_float(vi[2 * c + 1]);
-            c4[c] = v;
-          }
+          for (int c = 0; c < 16; ++c)
+            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(c4 + 4 * c),
+                         "f"(-__uint_as_float(vr[2 * c])), "f"(-__uint_as_float(vi[2 * c])),
+                         "f"(-__uint_as_float(vr[2 * c + 1])), "f"(-__uint_as_float(vi[2 * c + 1]))
+                         : "memory");
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
