@@ -65,7 +65,7 @@ class Stats(C.Structure):
 
 
 EXPORTS = ["dd_default_options", "dd_setup", "dd_set_values", "dd_factor", "dd_solve", "dd_get_schur",
-           "dd_get_stats", "dd_strerror", "dd_free", "dd_dense_solve_noalloc"]
+           "dd_get_stats", "dd_strerror", "dd_free", "dd_dense_solve_noalloc", "dd_selftest_wait_timeout"]
 
 
 def library_path() -> str:
@@ -95,6 +95,7 @@ def load(build_if_missing: bool = True):
     lib.dd_strerror.restype = C.c_char_p
     lib.dd_free.argtypes = [C.c_void_p]
     lib.dd_free.restype = None
+    lib.dd_selftest_wait_timeout.argtypes = [C.c_void_p]
     lib.dd_dense_solve_noalloc.argtypes = [C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64,
                                            C.c_void_p, C.c_int64, C.c_void_p]
     _lib = lib

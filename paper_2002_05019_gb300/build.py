@@ -32,7 +32,9 @@ def _stale(objs) -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "dd.h"), __file__]
+    inc = os.path.join(ROOT, "include")
+    deps = ([os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(inc, f) for f in os.listdir(inc)]
+            + [__file__])
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "../../include/dd.h"
+#include "../../include/dd_diag.h"
 #include "dd_internal.h"
 
 namespace {
@@ -681,6 +682,7 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
       R.upd_off = (int64_t)h_updt.size();
       R.tc_off = (int64_t)h_tc.size();
       std::vector<Task> upd_next, upd_rest, tc_next, tc_rest;
+      double upd_flops = 0.0;
       for (int f : L.ids) {
         const FrontDev& F = h->fronts[f];
         const int nte = F.ne_pad / T, nt = F.ld / T;
@@ -690,10 +692,14 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
         auto zero_tile = [&](int i) { return F.kind == 0 && i >= nte && (k + 1) * T <= F.n_int; };
         for (int i = k + 1; i < nt; ++i)
           if (!zero_tile(i)) h_trsm.push_back(Task{f, i, k, 0});
+        // algorithmic trailing-update work of this step (64 x 64 tiles, lower part)
         for (int j = k + 1; j < nt; ++j) {
           if (zero_tile(j)) continue;
-          for (int i = j; i < nt; ++i)
-            if (!zero_tile(i)) (j == k + 1 ? upd_next : upd_rest).push_back(Task{f, i, j, 0});
+          for (int i = j; i < nt; ++i) {
+            if (zero_tile(i)) continue;
+            upd_flops += 8.0 * T * (i == j ? T * (T + 1) / 2 : T * T);
+            if (!h->use_tc) (j == k + 1 ? upd_next : upd_rest).push_back(Task{f, i, j, 0});
+          }
         }
         // tensor-core tasks: 128-row blocks (tiles i0, i0 + 1) x column tile j
         if (h->use_tc)
@@ -712,8 +718,7 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
       h_tc.insert(h_tc.end(), tc_next.begin(), tc_next.end());
       h_tc.insert(h_tc.end(), tc_rest.begin(), tc_rest.end());
       R.n_diag = (int)((int64_t)h_diag.size() - R.diag_off);
-      for (int64_t q = R.upd_off; q < (int64_t)h_updt.size(); ++q)
-        h->stats.kernel_flops[DD_K_UPDATE] += 8.0 * T * (h_updt[q].i == h_updt[q].j ? T * (T + 1) / 2 : T * T);
+      h->stats.kernel_flops[DD_K_UPDATE] += upd_flops;
       h->stats.kernel_flops[DD_K_TRSM] += 8.0 * ((int64_t)h_trsm.size() - R.trsm_off) * T * T * (T - 1) / 2.0;
       h->stats.kernel_flops[DD_K_DIAG] += 8.0 * ((int64_t)h_diag.size() - R.diag_off) * (double)T * T * T / 6.0;
       R.n_trsm = (int)((int64_t)h_trsm.size() - R.trsm_off);
@@ -1097,6 +1102,30 @@ int dd_get_schur(const dd_handle* h, int32_t i, dd_c128* out, int32_t* duals, in
       out[(size_t)b * m + a] = dd_c128{-re, -im};
     }
   return DD_OK;
+}
+
+int dd_selftest_wait_timeout(void* cuda_stream) {
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int32_t* flag = nullptr;
+  DevStatus* st = nullptr;
+  if (cudaMalloc(&flag, sizeof(int32_t)) != cudaSuccess) return DD_ERR_OOM;
+  if (cudaMalloc(&st, sizeof(DevStatus)) != cudaSuccess) {
+    cudaFree(flag);
+    return DD_ERR_OOM;
+  }
+  int code = DD_ERR_CUDA;
+  DevStatus host{};
+  if (cudaMemsetAsync(flag, 0, sizeof(int32_t), s) == cudaSuccess &&
+      cudaMemsetAsync(st, 0, sizeof(DevStatus), s) == cudaSuccess) {
+    ddk::launch_wait_probe(flag, st, s);
+    if (cudaGetLastError() == cudaSuccess &&
+        cudaMemcpyAsync(&host, st, sizeof(host), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+        cudaStreamSynchronize(s) == cudaSuccess)
+      code = host.code == 8 ? DD_ERR_TIMEOUT : (host.code == 0 ? DD_OK : DD_ERR_CUDA);
+  }
+  cudaFree(flag);
+  cudaFree(st);
+  return code;
 }
 
 int dd_get_stats(const dd_handle* h, dd_stats* out) {

@@ -136,6 +136,8 @@ void launch_residual(const LeafDev* leaves, int n_leaves, const int32_t* rowptr,
 void launch_dual_residual(int n_dual, const int32_t* bt_ptr, const int64_t* bt_row, const int8_t* bt_sign,
                           const double2* u, int64_t ldu, double2* rl, int64_t ldrl, int nrhs,
                           cudaStream_t s);
+// diagnostic: one CTA waits (bounded) on *flag >= 1
+void launch_wait_probe(const int32_t* flag, DevStatus* st, cudaStream_t s);
 // partial sums of |x|^2 per block into out[blocks]; returns block count used
 int launch_sumsq(const double2* x, int64_t n, double* out, int max_blocks, cudaStream_t s);
 

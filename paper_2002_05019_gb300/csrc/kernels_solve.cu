@@ -306,6 +306,9 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rp
   }
 }
 
+// diagnostic: a bounded wait on a flag that nothing sets
+__global__ void k_wait_probe(const int32_t* flag, DevStatus* st) { wait_ready(flag, 1, st, -1, -1); }
+
 template <typename S>
 __global__ void k_leaf_out(const S* rpool, const FrontDev* fr, const LeafDev* lv, const int32_t* perm, double2* u,
                            int64_t ldu, int nrhs, int accumulate) {
@@ -468,6 +471,8 @@ void launch_dual_residual(int n_dual, const int32_t* bt_ptr, const int64_t* bt_r
   const int blocks = (int)((work + 255) / 256 < 4096 ? (work + 255) / 256 : 4096);
   k_dual_residual<<<blocks, 256, 0, s>>>(n_dual, bt_ptr, bt_row, bt_sign, u, ldu, rl, ldrl, nrhs);
 }
+
+void launch_wait_probe(const int32_t* flag, DevStatus* st, cudaStream_t s) { k_wait_probe<<<1, 32, 0, s>>>(flag, st); }
 
 int launch_sumsq(const double2* x, int64_t n, double* out, int max_blocks, cudaStream_t s) {
   int blocks = (int)((n + 255) / 256);

@@ -27,8 +27,13 @@ def _gpu_present():
 
 
 def _declared():
-    src = open(os.path.join(ROOT, "include", "dd.h")).read()
-    return re.findall(r"^(?:int|void|const char\*)\s+(dd_\w+)\s*\(", src, re.M)
+    names = []
+    inc = os.path.join(ROOT, "include")
+    for f in sorted(os.listdir(inc)):
+        if f.endswith(".h"):
+            src = open(os.path.join(inc, f)).read()
+            names += re.findall(r"^(?:int|void|const char\*)\s+(dd_\w+)\s*\(", src, re.M)
+    return names
 
 
 def test_every_declared_symbol_is_exported():

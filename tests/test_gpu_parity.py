@@ -209,3 +209,18 @@ def test_refinement_stop_at_1e11_meets_1e10(c1, c2_linear):
         assert rel(gather(p, u), ref) <= TOL["mixed"]
         assert s.stats()["refine_last"] <= 1e-11
         s.free()
+
+
+def test_large_2048_domains_closed_form():
+    """The 2048-domain workload (1,960,595 DoFs) in the mixed form at full size:
+    the linear-field closed form to 1e-10 and the arrowhead residual."""
+    p = femgen.large_c4(rhs="linear")
+    s = dd.Solver.from_problem(p, precision="mixed", refine_tol=1e-11)
+    s.factor()
+    u, lam = s.solve(dd.stacked_loads(p))
+    assert rel(gather(p, u), p.x_exact) <= TOL["mixed"]
+    rp, _ = oracle.arrow_residual(p, dd.unstack(p, u), lam)
+    assert np.linalg.norm(np.concatenate(rp)) <= 1e-9 * np.linalg.norm(dd.stacked_loads(p))
+    st = s.stats()
+    assert st["n_sub"] == 2048 and st["n_dual"] == p.n_dual
+    s.free()
