@@ -66,17 +66,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t ta, uint32_t (&r)[32]) {
       : "r"(ta));
 }
 
-// Persistent, warp-specialised form: grid = one CTA per SM, tasks taken
-// round-robin.  Warp 0 lane 0 loads operand stages (one K-atom of A and B per
-// stage, two stages in shared memory), warp 1 lane 0 issues the MMAs into one
-// of two TMEM accumulators, warps 2-5 drain the other accumulator into C.
-constexpr int kStageA = 4 * DD_TC_ATOM;          // 4 planes x 1 atom = 64 KB
-constexpr int kStageB = 2 * 3 * DD_TC_HALF;      // 2 splits x [-Wi][Wr][Wi] = 48 KB
-constexpr int kStage = kStageA + kStageB;        // 112 KB
-constexpr int kSmemP = 2 * kStage + 1024;
+// Persistent, warp-specialised form: grid <= one CTA per SM, each CTA takes a
+// contiguous chunk of the task list, so consecutive tasks share their 128-row
+// A block.  Warp 0 lane 0 loads the A block (128 KB, resident while it is
+// reused) and streams the B tiles through a two-stage ring (one K-atom of B,
+// 48 KB, per stage); warp 1 lane 0 issues the MMAs into one of two TMEM
+// accumulators; warps 2-5 drain the other accumulator into C.
+constexpr int kStageB = 2 * 3 * DD_TC_HALF;      // 2 splits x [-Wi][Wr][Wi] of one atom = 48 KB
+constexpr int kSmemP = kA + 2 * kStageB + 1024;  // 128 KB + 96 KB + alignment
 
 struct PipeBars {
-  uint64_t full[2], empty[2], acc_full[2], acc_empty[2];
+  uint64_t a_full, a_empty, b_full[2], b_empty[2], acc_full[2], acc_empty[2];
 };
 
 __device__ __forceinline__ void mbar_init(uint32_t b, int count) {
@@ -85,19 +85,34 @@ __device__ __forceinline__ void mbar_init(uint32_t b, int count) {
 __device__ __forceinline__ void mbar_arrive(uint32_t b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b) : "memory");
 }
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, int bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
 
 __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontDev* fr, const Task* tasks, int n_tasks,
                                                       int k, const unsigned char* ws, DevStatus* st) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  unsigned char* sA = smem;               // resident A block (planes x atoms, 16 KB each)
+  unsigned char* sB = smem + kA;          // B ring: stage s at sB + s * kStageB
   __shared__ __align__(8) PipeBars bars;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const uint32_t b_full0 = smem_u32(&bars.full[0]), b_empty0 = smem_u32(&bars.empty[0]);
+  const uint32_t b_afull = smem_u32(&bars.a_full), b_aempty = smem_u32(&bars.a_empty);
+  const uint32_t b_full0 = smem_u32(&bars.b_full[0]), b_empty0 = smem_u32(&bars.b_empty[0]);
   const uint32_t b_accf0 = smem_u32(&bars.acc_full[0]), b_acce0 = smem_u32(&bars.acc_empty[0]);
+  const int q0 = (int)(((int64_t)blockIdx.x * n_tasks) / gridDim.x);
+  const int q1 = (int)(((int64_t)(blockIdx.x + 1) * n_tasks) / gridDim.x);
   if (tid == 0) {
     fail = 0;
+    mbar_init(b_afull, 1);
+    mbar_init(b_aempty, 1);
     for (int i = 0; i < 2; ++i) {
       mbar_init(b_full0 + 8 * i, 1);
       mbar_init(b_empty0 + 8 * i, 1);
@@ -118,39 +133,46 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
 
   if (warp == 0 && lane == 0) {
     // ---------------- producer ----------------
-    int u = 0;
-    for (int q = blockIdx.x; q < n_tasks && !fail; q += gridDim.x) {
+    int m = 0, u = 0, pf = -1, pi = -1;
+    for (int q = q0; q < q1 && !fail; ++q) {
       const Task t = tasks[q];
       const FrontDev F = fr[t.f];
-      const unsigned char* gA = ws + F.ws_off + (int64_t)((t.i - k - 1) >> 1) * kA;
+      if (t.f != pf || t.i != pi) {   // new A block
+        if (m > 0 && !mbar_wait(b_aempty, (m - 1) & 1)) { fail = 1; break; }
+        const unsigned char* gA = ws + F.ws_off + (int64_t)((t.i - k - 1) >> 1) * kA;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b_afull), "r"(kA) : "memory");
+        for (int c = 0; c < kA / DD_TC_ATOM; ++c)
+          bulk_g2s(smem_u32(sA + c * DD_TC_ATOM), gA + c * DD_TC_ATOM, DD_TC_ATOM, b_afull);
+        ++m;
+        pf = t.f;
+        pi = t.i;
+      }
       const unsigned char* gB = ws + F.ws_boff + (int64_t)(t.j - k - 1) * kB;
       for (int a = 0; a < 2; ++a, ++u) {
         const int sidx = u & 1;
-        const uint32_t par = ((u >> 1) & 1) ^ 1;
-        if (!mbar_wait(b_empty0 + 8 * sidx, par)) { fail = 1; break; }
-        unsigned char* sA = smem + sidx * kStage;
-        unsigned char* sB = sA + kStageA;
+        if (!mbar_wait(b_empty0 + 8 * sidx, ((u >> 1) & 1) ^ 1)) { fail = 1; break; }
         const uint32_t fb = b_full0 + 8 * sidx;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(kStage) : "memory");
-        for (int pl = 0; pl < 4; ++pl)
-          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                           smem_u32(sA + pl * DD_TC_ATOM)),
-                       "l"(gA + (pl * 2 + a) * DD_TC_ATOM), "r"(DD_TC_ATOM), "r"(fb)
-                       : "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(kStageB) : "memory");
         for (int sp = 0; sp < 2; ++sp)
-          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                           smem_u32(sB + sp * 3 * DD_TC_HALF)),
-                       "l"(gB + (sp * 2 + a) * 3 * DD_TC_HALF), "r"(3 * DD_TC_HALF), "r"(fb)
-                       : "memory");
+          bulk_g2s(smem_u32(sB + sidx * kStageB + sp * 3 * DD_TC_HALF), gB + (sp * 2 + a) * 3 * DD_TC_HALF,
+                   3 * DD_TC_HALF, fb);
       }
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
-    int u = 0, tl = 0;
+    int m = 0, u = 0, tl = 0, pf = -1, pi = -1;
     const int pl[6] = {0, 0, 1, 2, 2, 3};
     const int bs[6] = {0, 1, 0, 0, 1, 0};
     const int bv[6] = {1, 1, 1, 0, 0, 0};
-    for (int q = blockIdx.x; q < n_tasks && !fail; q += gridDim.x, ++tl) {
+    const uint32_t a0 = smem_u32(sA), bring = smem_u32(sB);
+    for (int q = q0; q < q1 && !fail; ++q, ++tl) {
+      const Task t = tasks[q];
+      if (t.f != pf || t.i != pi) {
+        if (!mbar_wait(b_afull, m & 1)) { fail = 1; break; }
+        ++m;
+        pf = t.f;
+        pi = t.i;
+      }
       const int ab = tl & 1;
       if (!mbar_wait(b_acce0 + 8 * ab, ((tl >> 1) & 1) ^ 1)) { fail = 1; break; }
       asm volatile("tcgen05.fence::after_thread_sync;");
@@ -160,11 +182,11 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
         const int sidx = u & 1;
         if (!mbar_wait(b_full0 + 8 * sidx, (u >> 1) & 1)) { fail = 1; break; }
         asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t a0 = smem_u32(smem + sidx * kStage), b0 = a0 + kStageA;
+        const uint32_t b0 = bring + sidx * kStageB;
         for (int s4 = 0; s4 < 4; ++s4)
 #pragma unroll
           for (int qq = 0; qq < 6; ++qq) {
-            const uint64_t ad = desc_sw128(a0 + pl[qq] * DD_TC_ATOM + s4 * 32);
+            const uint64_t ad = desc_sw128(a0 + (pl[qq] * 2 + a) * DD_TC_ATOM + s4 * 32);
             const uint64_t bd = desc_sw128(b0 + (bs[qq] * 3 + bv[qq]) * DD_TC_HALF + s4 * 32);
             asm volatile(
                 "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -172,21 +194,20 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
                 "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
             acc = 1;
           }
-        // the stage is free once these MMAs have read it
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         b_empty0 + 8 * sidx)
-                     : "memory");
+        mma_commit(b_empty0 + 8 * sidx);   // the B stage is free once these MMAs have read it
       }
       if (fail) break;
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(b_accf0 + 8 * ab)
-                   : "memory");
+      mma_commit(b_accf0 + 8 * ab);
+      // the A block is free once the last task that uses it has been issued
+      const bool last_use = (q + 1 >= q1) || tasks[q + 1].f != t.f || tasks[q + 1].i != t.i;
+      if (last_use) mma_commit(b_aempty);
     }
   } else if (warp >= 2) {
-    // ---------------- epilogue: TMEM -> C -= acc ----------------
+    // ---------------- epilogue: C -= acc ----------------
     const int sub = warp & 3;                 // TMEM sub-partition of this warp
     const int row = sub * 32 + lane;
     int tl = 0;
-    for (int q = blockIdx.x; q < n_tasks; q += gridDim.x, ++tl) {
+    for (int q = q0; q < q1; ++q, ++tl) {
       const Task t = tasks[q];
       const FrontDev F = fr[t.f];
       const int ab = tl & 1;
