@@ -894,7 +894,7 @@ int dd_factor(dd_handle* h) {
     // one-step look-ahead on levels with few fronts: the main stream updates
     // only the next panel column and factors that panel, while the second
     // stream applies the rest of the trailing update of the current step
-    const bool ahead = L.ids.size() <= 32 && L.steps.size() > 1;
+    const bool ahead = h->use_tc && L.ids.size() <= 32 && L.steps.size() > 1;
     const int reserve = ahead ? 16 : 0;   // SMs left free for the panel chain
     auto panel = [&](const StepRange& R) -> cudaError_t {
       unsigned char* ws = h->use_tc ? h->d_ws + (size_t)(R.k & 1) * h->ws_bytes : nullptr;
