@@ -118,6 +118,33 @@ def sine_field():
     return E, curlE
 
 
+def plane_wave(p_vec: np.ndarray, k_hat: np.ndarray, k0: float):
+    """Incident plane wave E = p exp(-j k0 k.r) (p perpendicular to k) and its curl -j k0 (k x p) exp(...)."""
+    def E(x):
+        ph = np.exp(-1j * k0 * (x @ k_hat))
+        return ph[..., None] * p_vec
+    kxp = np.cross(k_hat, p_vec)
+
+    def curlE(x):
+        ph = np.exp(-1j * k0 * (x @ k_hat))
+        return (-1j * k0) * ph[..., None] * kxp
+    return E, curlE
+
+
+def seeded_plane_waves(count: int, seed: int):
+    """Directions uniform on the sphere and unit polarisations perpendicular to them."""
+    r = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        k = r.normal(size=3)
+        k /= np.linalg.norm(k)
+        t = r.normal(size=3)
+        t -= (t @ k) * k
+        t /= np.linalg.norm(t)
+        out.append((t.astype(complex), k))
+    return out
+
+
 def _abc_data(E, curlE, k0):
     """U = n x curl E + j k0 n x (n x E) for the absorbing boundary condition."""
     def U(x, nrm):
@@ -139,7 +166,7 @@ def _csr(rows, cols, vals, n):
 def build_problem(name: str, n: int, levels: int, *, jitter=0.15, mesh_seed=0,
                   split_range=None, split_seed=1, size_range=None,
                   eps="uniform", eps_seed=2, rhs="edge", rhs_seed=3, n_rhs_edges=1,
-                  field_seed=5, k0=K0) -> Problem:
+                  n_waves=0, wave_seed=4, field_seed=5, k0=K0) -> Problem:
     mesh = box_mesh(n, jitter=jitter, seed=mesh_seed)
     rng_split = np.random.default_rng(split_seed)
     rcb = rcb_cells(n, levels, split_range=split_range, rng=rng_split, size_range=size_range)
@@ -171,6 +198,14 @@ def build_problem(name: str, n: int, levels: int, *, jitter=0.15, mesh_seed=0,
     x_exact = None
     rhs_edges = None
     elem_load = face_ld = None
+    wave_loads = []
+    if rhs == "edges+waves":
+        # plane-wave sources enter through the absorbing boundary: b -= int U . N dS
+        for p_vec, k_hat in seeded_plane_waves(n_waves, wave_seed):
+            E, curlE = plane_wave(p_vec, k_hat, k0)
+            fl, _ = face_load(mesh, _abc_data(E, curlE, k0), s=3)
+            wave_loads.append(-fl)
+        rhs = "edges"
     if rhs in ("edge", "edges"):
         interior = ~boundary_edge_mask(mesh)
         free = interior & (tr.edge_mult == 1)
@@ -181,8 +216,10 @@ def build_problem(name: str, n: int, levels: int, *, jitter=0.15, mesh_seed=0,
             rhs_edges = np.array([cand[np.argmin(d)]])      # argmin returns the lowest index on ties
         else:
             rhs_edges = np.random.default_rng(rhs_seed).choice(cand, size=n_rhs_edges, replace=False)
-        b = np.zeros((nE, rhs_edges.size), dtype=np.complex128)
+        b = np.zeros((nE, rhs_edges.size + len(wave_loads)), dtype=np.complex128)
         b[rhs_edges, np.arange(rhs_edges.size)] = 1.0
+        for c, fl in enumerate(wave_loads):
+            b[:, rhs_edges.size + c] = _assemble_load(te[:0], np.zeros((0, 6)), feid, fl, nE)
     elif rhs == "linear":
         r = np.random.default_rng(field_seed)
         a = r.normal(size=3) + 1j * r.normal(size=3)
@@ -225,6 +262,8 @@ def build_problem(name: str, n: int, levels: int, *, jitter=0.15, mesh_seed=0,
                     k = np.searchsorted(g, e)
                     if k < g.size and g[k] == e and s == _lowest_owner(tr, e, s):
                         f[k, c] = 1.0
+            for c, fl in enumerate(wave_loads):
+                f[:, rhs_edges.size + c] = _assemble_load(lt[:0], np.zeros((0, 6)), lf, fl[fmask], g.size)
         subs.append(Subdomain(l2g=g, indptr=ip, indices=ix, data=dv, f=f,
                               b_dual=tr.b_dual[s], b_local=tr.b_local[s], b_sign=tr.b_sign[s]))
     return Problem(name=name, mesh=mesh, k0=k0, eps_tet=eps_tet, tet_sub=tet_sub, rcb=rcb,
@@ -271,8 +310,12 @@ def large_c4(rhs="edge", **kw) -> Problem:
                          eps="random", rhs=rhs, **kw)
 
 
-def multi_rhs_c5(n_edges=56, **kw) -> Problem:
-    """C1 mesh with several unit edge currents at seeded random interior edges."""
+def multi_rhs_c5(n_edges=56, n_waves=8, **kw) -> Problem:
+    """8-domain mesh with many excitations: unit edge currents at seeded random
+    interior edges (seed 3) followed by plane-wave sources through the
+    absorbing boundary (seed 4); 56 + 8 = 64 right-hand sides by default."""
+    if n_waves:
+        return build_problem("multirhs-n8-s8", 8, 3, rhs="edges+waves", n_rhs_edges=n_edges, n_waves=n_waves, **kw)
     return build_problem("multirhs-n8-s8", 8, 3, rhs="edges", n_rhs_edges=n_edges, **kw)
 
 

@@ -28,6 +28,8 @@
 namespace {
 
 constexpr int T = DD_TILE;
+constexpr int kSolveBlock = 64;   // right-hand sides per direct-solve pass
+constexpr int kNormBlocks = 16;   // reduction blocks per column for the refinement norms
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
@@ -801,7 +803,7 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
   DD_CUDA(A.alloc(&h->d_solve_status, 1));
   DD_CUDA(cudaMemsetAsync(h->d_solve_status, 0, sizeof(DevStatus), s));
   DD_CUDA(A.alloc(&h->d_status, 1));
-  DD_CUDA(A.alloc(&h->d_partials, 1024));
+  DD_CUDA(A.alloc(&h->d_partials, 2 * kSolveBlock * kNormBlocks));
   DD_CUDA(cudaEventCreate(&h->ev0));
   DD_CUDA(cudaEventCreate(&h->ev1));
   DD_CUDA(cudaStreamSynchronize(s));
@@ -981,6 +983,9 @@ int dd_factor(dd_handle* h) {
   return DD_OK;
 }
 
+static int solve_block(dd_handle* h, int32_t nrhs, const dd_c128* f, int64_t ldf, dd_c128* u, int64_t ldu,
+                       dd_c128* lambda, int64_t ldl);
+
 int dd_solve(dd_handle* h, int32_t nrhs, const dd_c128* f, int64_t ldf, dd_c128* u, int64_t ldu, dd_c128* lambda,
              int64_t ldl) {
   if (!h || nrhs < 0) return DD_ERR_INVALID_ARG;
@@ -988,6 +993,30 @@ int dd_solve(dd_handle* h, int32_t nrhs, const dd_c128* f, int64_t ldf, dd_c128*
   if (!f || !u || ldf < h->n_loc || ldu < h->n_loc) return DD_ERR_INVALID_ARG;
   if (lambda && ldl < h->n_dual) return DD_ERR_INVALID_ARG;
   if (!h->factored) return DD_ERR_NOT_FACTORED;
+  // blocks of up to 64 right-hand sides
+  int status = DD_OK;
+  double t_ms = 0.0, worst = 0.0;
+  int iters = 0, launches = 0;
+  for (int32_t c0 = 0; c0 < nrhs; c0 += kSolveBlock) {
+    const int32_t nb = std::min<int32_t>(kSolveBlock, nrhs - c0);
+    const int st = solve_block(h, nb, f + (size_t)c0 * ldf, ldf, u + (size_t)c0 * ldu, ldu,
+                               lambda ? lambda + (size_t)c0 * ldl : nullptr, ldl);
+    if (st != DD_OK && st != DD_ERR_NOT_CONVERGED) return st;
+    if (st == DD_ERR_NOT_CONVERGED) status = st;
+    t_ms += h->stats.t_solve_ms;
+    worst = std::max(worst, h->stats.refine_last);
+    iters = std::max(iters, h->stats.refine_iters);
+    launches += h->stats.launches_solve;
+  }
+  h->stats.t_solve_ms = t_ms;
+  h->stats.refine_last = worst;
+  h->stats.refine_iters = iters;
+  h->stats.launches_solve = launches;
+  return status;
+}
+
+static int solve_block(dd_handle* h, int32_t nrhs, const dd_c128* f, int64_t ldf, dd_c128* u, int64_t ldu,
+                       dd_c128* lambda, int64_t ldl) {
   int cur = 0;
   cudaGetDevice(&cur);
   cudaSetDevice(h->device);
@@ -1004,6 +1033,7 @@ int dd_solve(dd_handle* h, int32_t nrhs, const dd_c128* f, int64_t ldf, dd_c128*
   int iters = 0;
   double ratio = 0.0;
   int status = DD_OK;
+  double prev_col[kSolveBlock] = {};
   const int64_t nu_el = h->n_loc * (int64_t)nrhs;
   const int64_t nl_el = (int64_t)h->n_dual * nrhs;
   for (int it = 0; it < h->max_refine; ++it) {
@@ -1013,34 +1043,38 @@ int dd_solve(dd_handle* h, int32_t nrhs, const dd_c128* f, int64_t ldf, dd_c128*
     ddk::launch_dual_residual(h->n_dual, h->d_btptr, h->d_btrow, h->d_btsign, h->d_u, h->n_loc, h->d_g, h->n_dual,
                               nrhs, s);
     direct_solve(h, nrhs, h->d_r, h->n_loc, h->d_g, h->d_du, h->d_dlam);
-    const int nb1 = ddk::launch_sumsq(h->d_du, nu_el, h->d_partials, 512, s);
-    const int nb2 = ddk::launch_sumsq(h->d_u, nu_el, h->d_partials + 512, 512, s);
+    ddk::launch_sumsq_cols(h->d_du, h->n_loc, nrhs, kNormBlocks, h->d_partials, s);
+    ddk::launch_sumsq_cols(h->d_u, h->n_loc, nrhs, kNormBlocks, h->d_partials + kSolveBlock * kNormBlocks, s);
     k_axpy<<<1024, 256, 0, s>>>(h->d_u, h->d_du, nu_el);
     if (nl_el) k_axpy<<<256, 256, 0, s>>>(h->d_lam, h->d_dlam, nl_el);
     h->launches += 6;
-    double part[1024];
+    double part[2 * kSolveBlock * kNormBlocks];
     DevStatus sst{};
     DD_CUDA(cudaMemcpyAsync(part, h->d_partials, sizeof(part), cudaMemcpyDeviceToHost, s));
     DD_CUDA(cudaMemcpyAsync(&sst, h->d_solve_status, sizeof(sst), cudaMemcpyDeviceToHost, s));
     DD_CUDA(cudaStreamSynchronize(s));
     if (sst.code != 0) break;  // reported after the loop
-    double sdu = 0, su = 0;
-    for (int q = 0; q < nb1; ++q) sdu += part[q];
-    for (int q = 0; q < nb2; ++q) su += part[512 + q];
-    const double prev = ratio;
-    ratio = su > 0 ? std::sqrt(sdu / su) : 0.0;
+    // per right-hand side: |du_j| / |u_j| and, with linear convergence, the
+    // error left after this update ~ |du_j| (|du_j| / |du_j previous|)
     iters = it + 1;
-    if (!std::isfinite(ratio)) break;
-    if (ratio <= h->refine_tol) break;
-    // linear convergence: the error left after this update is about
-    // |du_k| * (|du_k| / |du_{k-1}|); stop once that estimate is within tolerance
-    if (it > 0 && prev > 0 && ratio < prev) {
-      const double est = ratio * (ratio / prev);
-      if (est <= h->refine_tol) {
-        ratio = est;
-        break;
+    bool all_done = true, finite = true;
+    double worst = 0.0;
+    for (int j = 0; j < nrhs; ++j) {
+      double sdu = 0, su = 0;
+      for (int q = 0; q < kNormBlocks; ++q) {
+        sdu += part[j * kNormBlocks + q];
+        su += part[kSolveBlock * kNormBlocks + j * kNormBlocks + q];
       }
+      const double r = su > 0 ? std::sqrt(sdu / su) : 0.0;
+      if (!std::isfinite(r)) finite = false;
+      double err = r;
+      if (it > 0 && prev_col[j] > 0 && r < prev_col[j]) err = std::min(err, r * (r / prev_col[j]));
+      prev_col[j] = r;
+      worst = std::max(worst, err);
+      if (!(err <= h->refine_tol)) all_done = false;
     }
+    ratio = worst;
+    if (!finite || all_done) break;
   }
   if (h->prec == DD_PREC_MIXED && h->max_refine > 0 && !(ratio <= h->refine_tol)) status = DD_ERR_NOT_CONVERGED;
   DD_CUDA(cudaMemcpy2DAsync(u, (size_t)ldu * 16, h->d_u, row_b, row_b, nrhs,

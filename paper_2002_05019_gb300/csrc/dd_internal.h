@@ -138,6 +138,8 @@ void launch_dual_residual(int n_dual, const int32_t* bt_ptr, const int64_t* bt_r
                           cudaStream_t s);
 // diagnostic: one CTA waits (bounded) on *flag >= 1
 void launch_wait_probe(const int32_t* flag, DevStatus* st, cudaStream_t s);
+// per-column partial sums of |x|^2: out[col * blocks + b]
+void launch_sumsq_cols(const double2* x, int64_t n, int ncols, int blocks, double* out, cudaStream_t s);
 // partial sums of |x|^2 per block into out[blocks]; returns block count used
 int launch_sumsq(const double2* x, int64_t n, double* out, int max_blocks, cudaStream_t s);
 

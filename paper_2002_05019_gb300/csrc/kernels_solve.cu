@@ -306,6 +306,210 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rp
   }
 }
 
+// ---------------------------------------------------------------------------
+// Many right-hand sides (mixed form, up to 64 columns per pass): the same
+// tile-parallel substitution, but every tile of L read from memory is applied
+// to all columns at once as a 64 x 64 x nrhs product (4 x 4 register blocks),
+// and the in-tile solves are products with the stored tile inverses.
+// ---------------------------------------------------------------------------
+constexpr int MR_KC = 32;
+
+struct MrSmem {
+  float2 As[MR_KC][T + 1];   // A chunk, k-major
+  float2 Bs[MR_KC][T + 1];   // B chunk, k-major (columns = right-hand sides)
+  float2 X[T][T + 1];        // tile block of right-hand sides
+};
+
+__device__ __forceinline__ void mr_fma(const MrSmem& sm, float2 (&acc)[4][4], int tx, int ty) {
+#pragma unroll 4
+  for (int kk = 0; kk < MR_KC; ++kk) {
+    float2 a[4], b[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) a[r] = sm.As[kk][ty + 16 * r];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) b[c] = sm.Bs[kk][tx + 16 * c];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[r][c] = cfma(a[r], b[c], acc[r][c]);
+  }
+}
+
+// forward: Z_i = L_ii^{-1} (B_i - sum_k L_ik Z_k) for eliminated tiles; update tiles only subtract
+__global__ void __launch_bounds__(256) k_forward_mr(const float2* pool, float2* rpool, const FrontDev* fr,
+                                                    const Task* tasks, int nrhs, int32_t* flags, int epoch,
+                                                    DevStatus* st, const float2* linv) {
+  extern __shared__ __align__(16) unsigned char mr_raw[];
+  MrSmem& sm = *reinterpret_cast<MrSmem*>(mr_raw);
+  const Task t = tasks[blockIdx.x];
+  const FrontDev F = fr[t.f];
+  const float2* L = pool + F.off;
+  float2* z = rpool + F.roff * nrhs;
+  const int64_t ld = F.ld;
+  const int nte = F.ne_pad / T;
+  const int i = t.i, r0 = i * T;
+  const int kmax = i < nte ? i : nte;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  int32_t* flg = flags + F.tile_off;
+  float2 acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(0.f, 0.f);
+  for (int k = 0; k < kmax; ++k) {
+    if (!wait_ready(flg + k, epoch, st, t.f, k)) return;
+    for (int kc = 0; kc < T; kc += MR_KC) {
+      for (int idx = threadIdx.x; idx < T * MR_KC; idx += blockDim.x) {
+        const int rr = idx / MR_KC, kk = idx % MR_KC;
+        sm.As[kk][rr] = L[(r0 + rr) * ld + k * T + kc + kk];
+        const int col = rr;   // reuse the index: Bs[kk][col] = Z_k[kc + kk][col]
+        sm.Bs[kk][col] = col < nrhs ? ldcg(z + (int64_t)(k * T + kc + kk) * nrhs + col) : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+      mr_fma(sm, acc, tx, ty);
+      __syncthreads();
+    }
+  }
+  // X = B_i - acc
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int rr = ty + 16 * r, col = tx + 16 * c;
+      const float2 b = col < nrhs ? ldcg(z + (int64_t)(r0 + rr) * nrhs + col) : make_float2(0.f, 0.f);
+      sm.X[rr][col] = csub(b, acc[r][c]);
+    }
+  __syncthreads();
+  if (i < nte) {
+    // Z_i = Linv_ii X
+    const float2* Li = linv + ((int64_t)F.tile_off + i) * T * T;
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(0.f, 0.f);
+    for (int kc = 0; kc < T; kc += MR_KC) {
+      for (int idx = threadIdx.x; idx < T * MR_KC; idx += blockDim.x) {
+        const int rr = idx / MR_KC, kk = idx % MR_KC;
+        sm.As[kk][rr] = Li[rr * T + kc + kk];
+        sm.Bs[kk][rr] = sm.X[kc + kk][rr];
+      }
+      __syncthreads();
+      mr_fma(sm, acc, tx, ty);
+      __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) sm.X[ty + 16 * r][tx + 16 * c] = acc[r][c];
+    __syncthreads();
+  }
+  for (int idx = threadIdx.x; idx < T * nrhs; idx += blockDim.x) {
+    const int rr = idx / nrhs, col = idx % nrhs;
+    z[(int64_t)(r0 + rr) * nrhs + col] = sm.X[rr][col];
+  }
+  if (i < nte) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release(flg + i, epoch);
+    }
+  }
+}
+
+// backward: X_j = L_jj^{-T} (D_j^{-1} Z_j - L_uj^T X_u - sum_{i>j} L_ij^T X_i)
+__global__ void __launch_bounds__(256) k_backward_mr(const float2* pool, float2* rpool, const FrontDev* fr,
+                                                     const Task* tasks, int nrhs, const int32_t* upd,
+                                                     const int32_t* sep, float2* lam, int64_t ld_lam, int32_t* flags,
+                                                     int epoch, DevStatus* st, const float2* linv) {
+  extern __shared__ __align__(16) unsigned char mr_raw[];
+  MrSmem& sm = *reinterpret_cast<MrSmem*>(mr_raw);
+  __shared__ float2 dinv[T];
+  const Task t = tasks[blockIdx.x];
+  const FrontDev F = fr[t.f];
+  const float2* L = pool + F.off;
+  float2* z = rpool + F.roff * nrhs;
+  const int64_t ld = F.ld;
+  const int nte = F.ne_pad / T;
+  const int j = t.i, c0 = j * T;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  int32_t* flg = flags + F.tile_off;
+  if (threadIdx.x < T) dinv[threadIdx.x] = cdiv(make_float2(1.f, 0.f), L[(c0 + threadIdx.x) * (ld + 1)]);
+  float2 acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(0.f, 0.f);
+  // update rows: acc += L_uj^T X_u with X_u the known ancestor duals
+  for (int u0 = 0; u0 < F.nu; u0 += MR_KC) {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < T * MR_KC; idx += blockDim.x) {
+      const int kk = idx / T, cc = idx % T;   // row kk of the chunk, column cc
+      const int u = u0 + kk;
+      sm.As[kk][cc] = u < F.nu ? L[(F.ne_pad + u) * ld + c0 + cc] : make_float2(0.f, 0.f);
+      sm.Bs[kk][cc] = (u < F.nu && cc < nrhs) ? ldcg(lam + upd[F.upd_off + u] + cc * ld_lam) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    mr_fma(sm, acc, tx, ty);
+  }
+  for (int i = nte - 1; i > j; --i) {
+    if (!wait_ready(flg + i, epoch, st, t.f, i)) return;
+    for (int kc = 0; kc < T; kc += MR_KC) {
+      for (int idx = threadIdx.x; idx < T * MR_KC; idx += blockDim.x) {
+        const int kk = idx / T, cc = idx % T;
+        const int r = i * T + kc + kk;
+        sm.As[kk][cc] = L[r * ld + c0 + cc];
+        sm.Bs[kk][cc] = cc < nrhs ? ldcg(z + (int64_t)r * nrhs + cc) : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+      mr_fma(sm, acc, tx, ty);
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  // Y = D^{-1} Z_j - acc  (rows = columns c of the tile)
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int cc = ty + 16 * r, col = tx + 16 * c;
+      const float2 zb = col < nrhs ? ldcg(z + (int64_t)(c0 + cc) * nrhs + col) : make_float2(0.f, 0.f);
+      sm.X[cc][col] = csub(cmul(zb, dinv[cc]), acc[r][c]);
+    }
+  __syncthreads();
+  // X_j = Linv^T Y: acc[c][col] = sum_r Linv[r][c] Y[r][col]
+  const float2* Li = linv + ((int64_t)F.tile_off + j) * T * T;
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(0.f, 0.f);
+  for (int kc = 0; kc < T; kc += MR_KC) {
+    for (int idx = threadIdx.x; idx < T * MR_KC; idx += blockDim.x) {
+      const int kk = idx / T, cc = idx % T;
+      sm.As[kk][cc] = Li[(kc + kk) * T + cc];
+      sm.Bs[kk][cc] = sm.X[kc + kk][cc];
+    }
+    __syncthreads();
+    mr_fma(sm, acc, tx, ty);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) sm.X[ty + 16 * r][tx + 16 * c] = acc[r][c];
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < T * nrhs; idx += blockDim.x) {
+    const int cc = idx / nrhs, col = idx % nrhs;
+    const float2 v = sm.X[cc][col];
+    z[(int64_t)(c0 + cc) * nrhs + col] = v;
+    if (F.kind == 1 && c0 + cc < F.ne) lam[sep[F.sep_off + c0 + cc] + col * ld_lam] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    st_release(flg + j, epoch);
+  }
+}
+
 // diagnostic: a bounded wait on a flag that nothing sets
 __global__ void k_wait_probe(const int32_t* flag, DevStatus* st) { wait_ready(flag, 1, st, -1, -1); }
 
@@ -376,6 +580,22 @@ __global__ void k_dual_residual(int n_dual, const int32_t* bt_ptr, const int64_t
   }
 }
 
+// per-column sums of |x|^2: column j of x (n rows, ld n) reduced by gridDim.x blocks into out[j * gridDim.x + b]
+__global__ void k_sumsq_cols(const double2* x, int64_t n, double* out) {
+  __shared__ double sh[256];
+  const double2* xc = x + (int64_t)blockIdx.y * n;
+  double s = 0.0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    s += xc[e].x * xc[e].x + xc[e].y * xc[e].y;
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.y * gridDim.x + blockIdx.x] = sh[0];
+}
+
 __global__ void k_sumsq(const double2* x, int64_t n, double* out) {
   __shared__ double sh[256];
   double s = 0.0;
@@ -416,6 +636,16 @@ void launch_rhs_extend_add(int prec, void* rpool, const FrontDev* fronts, const 
 void launch_forward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const Task* tasks, int n,
                     int nrhs, int32_t* flags, int epoch, DevStatus* st, cudaStream_t s, const void* linv) {
   if (n <= 0) return;
+  if (prec == 1 && linv != nullptr && nrhs >= 4 && nrhs <= T) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_forward_mr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MrSmem));
+      attr = true;
+    }
+    k_forward_mr<<<n, 256, sizeof(MrSmem), s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs, flags, epoch, st,
+                                   (const float2*)linv);
+    return;
+  }
   if (prec == 0)
     k_forward<double2><<<n, SOLVE_THREADS, 0, s>>>((const double2*)pool, (double2*)rpool, fronts, tasks, nrhs, flags,
                                                    epoch, st, nullptr);
@@ -428,6 +658,16 @@ void launch_backward(int prec, const void* pool, void* rpool, const FrontDev* fr
                      int nrhs, const int32_t* upd, const int32_t* sep, void* lam_work, int64_t ld_lam,
                      int32_t* flags, int epoch, DevStatus* st, cudaStream_t s, const void* linv) {
   if (n <= 0) return;
+  if (prec == 1 && linv != nullptr && nrhs >= 4 && nrhs <= T) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_backward_mr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(MrSmem));
+      attr = true;
+    }
+    k_backward_mr<<<n, 256, sizeof(MrSmem), s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs, upd, sep,
+                                    (float2*)lam_work, ld_lam, flags, epoch, st, (const float2*)linv);
+    return;
+  }
   if (prec == 0)
     k_backward<double2><<<n, SOLVE_THREADS, 0, s>>>((const double2*)pool, (double2*)rpool, fronts, tasks, nrhs, upd,
                                                     sep, (double2*)lam_work, ld_lam, flags, epoch, st, nullptr);
@@ -473,6 +713,11 @@ void launch_dual_residual(int n_dual, const int32_t* bt_ptr, const int64_t* bt_r
 }
 
 void launch_wait_probe(const int32_t* flag, DevStatus* st, cudaStream_t s) { k_wait_probe<<<1, 32, 0, s>>>(flag, st); }
+
+void launch_sumsq_cols(const double2* x, int64_t n, int ncols, int blocks, double* out, cudaStream_t s) {
+  if (ncols <= 0) return;
+  k_sumsq_cols<<<dim3(blocks, ncols), 256, 0, s>>>(x, n, out);
+}
 
 int launch_sumsq(const double2* x, int64_t n, double* out, int max_blocks, cudaStream_t s) {
   int blocks = (int)((n + 255) / 256);

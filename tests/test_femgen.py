@@ -169,3 +169,29 @@ def test_convergence_rate_sine_field():
     errs = np.array(errs)
     rates = np.log2(errs[:-1] / errs[1:])
     assert np.all(rates >= 0.9), rates
+
+
+def test_plane_wave_curl_and_boundary_load():
+    """curl of the incident plane wave matches central differences, and the
+    64-excitation set splits exactly into domain loads (sum R_i^T f_i = b)."""
+    from femgen.problems import plane_wave, seeded_plane_waves
+    (p_vec, k_hat), = seeded_plane_waves(1, 4)
+    assert abs(p_vec @ k_hat) < 1e-14
+    E, curlE = plane_wave(p_vec, k_hat, 2 * np.pi)
+    x = np.random.default_rng(0).uniform(size=(5, 3))
+    h = 1e-6
+    num = np.zeros((5, 3), dtype=complex)
+    d = lambda i: np.eye(3)[i] * h
+    dE = [(E(x + d(i)) - E(x - d(i))) / (2 * h) for i in range(3)]   # dE/dx_i
+    num[:, 0] = dE[1][:, 2] - dE[2][:, 1]
+    num[:, 1] = dE[2][:, 0] - dE[0][:, 2]
+    num[:, 2] = dE[0][:, 1] - dE[1][:, 0]
+    assert np.abs(num - curlE(x)).max() < 1e-6
+    p = femgen.multi_rhs_c5()
+    assert p.b.shape == (p.n, 64)
+    n_tot = sum(s.n for s in p.subs)
+    R = sp.csr_matrix((np.ones(n_tot), (np.arange(n_tot), np.concatenate([s.l2g for s in p.subs]))),
+                      shape=(n_tot, p.n))
+    f = np.concatenate([s.f for s in p.subs])
+    assert np.abs(R.T @ f - p.b).max() <= 1e-15 * np.abs(p.b).max()
+    assert np.all(np.abs(p.b[:, 56:]).max(axis=0) > 0.1)

@@ -224,3 +224,27 @@ def test_large_2048_domains_closed_form():
     st = s.stats()
     assert st["n_sub"] == 2048 and st["n_dual"] == p.n_dual
     s.free()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_many_excitations_64_and_chunked(precision):
+    """64 right-hand sides (56 edge currents + 8 plane waves) on the 8-domain
+    mesh, factor once: every column against the oracle; 70 columns exercise the
+    split into blocks of 64."""
+    p = femgen.multi_rhs_c5()
+    o = oracle.DDOracle(p)
+    uo, lo = o.solve([s.f for s in p.subs])
+    xo, _ = o.gather(uo)
+    s = dd.Solver.from_problem(p, precision=precision)
+    s.factor()
+    f = dd.stacked_loads(p)
+    u, lam = s.solve(f)
+    x = gather(p, u)
+    for c in range(f.shape[1]):
+        assert rel(x[:, c], xo[:, c]) <= TOL[precision], c
+    assert rel(lam, lo) <= TOL[precision] * 10
+    f70 = np.concatenate([f, f[:, :6] * (1 + 1j)], axis=1)
+    u70, _ = s.solve(f70)
+    assert rel(u70[:, :64], u) <= TOL[precision]
+    assert rel(u70[:, 64:], u[:, :6] * (1 + 1j)) <= TOL[precision]
+    s.free()
