@@ -38,6 +38,8 @@ struct StepRange {
   int64_t diag_off, trsm_off, upd_off, tc_off;
   int n_diag, n_trsm, n_upd, n_tc;
   int n_upd_next, n_tc_next;   // the first tasks of each list update only the next panel column (j = k + 1)
+  int64_t grp_off;             // tensor-core task groups: next-column groups then the rest
+  int n_grp_next, n_grp_rest;
 };
 
 struct Level {
@@ -127,6 +129,7 @@ struct dd_handle {
   Task *d_trsm = nullptr, *d_updt = nullptr;
   Task *d_fwd = nullptr, *d_bwd = nullptr;
   Task* d_tc = nullptr;            // tensor-core update tasks (mixed form)
+  int2* d_grp = nullptr;           // their groups (first task, count) sharing one A block
   unsigned char* d_ws = nullptr;   // panel operand images (mixed form)
   float2* d_linv = nullptr;        // mixed form: L_kk^{-1} of every diagonal tile (index tile_off + k)
   cudaStream_t s2 = nullptr;       // look-ahead: bulk trailing updates run here
@@ -665,6 +668,19 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
   }
   std::vector<int32_t> h_level_ids, h_diag;
   std::vector<Task> h_trsm, h_updt, h_tc;
+  std::vector<int2> h_grp;
+  // runs of consecutive tasks with the same (front, row block)
+  auto add_groups = [&](int64_t first, int64_t count) -> int {
+    int ng = 0;
+    for (int64_t q = first; q < first + count;) {
+      int64_t e = q + 1;
+      while (e < first + count && h_tc[e].f == h_tc[q].f && h_tc[e].i == h_tc[q].i) ++e;
+      h_grp.push_back(make_int2((int)q, (int)(e - q)));
+      ++ng;
+      q = e;
+    }
+    return ng;
+  };
   for (auto& L : h->levels) {
     L.ids_off = (int64_t)h_level_ids.size();
     h_level_ids.insert(h_level_ids.end(), L.ids.begin(), L.ids.end());
@@ -726,6 +742,9 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
       R.n_trsm = (int)((int64_t)h_trsm.size() - R.trsm_off);
       R.n_upd = (int)((int64_t)h_updt.size() - R.upd_off);
       R.n_tc = (int)((int64_t)h_tc.size() - R.tc_off);
+      R.grp_off = (int64_t)h_grp.size();
+      R.n_grp_next = add_groups(R.tc_off, R.n_tc_next);
+      R.n_grp_rest = add_groups(R.tc_off + R.n_tc_next, R.n_tc - R.n_tc_next);
       L.steps.push_back(R);
     }
   }
@@ -789,6 +808,7 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
   DD_CUDA(A.upload(&h->d_updt, h_updt, s));
   DD_CUDA(A.upload(&h->d_fwd, h_fwd, s));
   DD_CUDA(A.upload(&h->d_tc, h_tc, s));
+  DD_CUDA(A.upload(&h->d_grp, h_grp, s));
   if (h->use_tc) DD_CUDA(A.alloc(&h->d_ws, 2 * h->ws_bytes));   // two step parities (look-ahead)
   DD_CUDA(cudaStreamCreateWithFlags(&h->s2, cudaStreamNonBlocking));
   DD_CUDA(cudaEventCreateWithFlags(&h->ev_panel, cudaEventDisableTiming));
@@ -928,7 +948,8 @@ int dd_factor(dd_handle* h) {
       cudaError_t e = mark_on(DD_K_UPDATE, true, on);
       if (e != cudaSuccess) return e;
       if (h->use_tc)
-        ddk::launch_update_tc(h->pool, h->d_fronts, h->d_tc + first, n, R.k, ws, h->d_status, on, cap);
+        ddk::launch_update_tc(h->pool, h->d_fronts, h->d_tc, h->d_grp + R.grp_off + (next_part ? 0 : R.n_grp_next),
+                              next_part ? R.n_grp_next : R.n_grp_rest, R.k, ws, h->d_status, on, cap);
       else
         ddk::launch_update(p, h->pool, h->d_fronts, h->d_updt + first, n, R.k, on);
       count(DD_K_UPDATE, n);

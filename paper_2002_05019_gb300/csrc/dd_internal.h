@@ -98,7 +98,8 @@ void launch_trsm_mx(void* pool, const FrontDev* fronts, const Task* tasks, int n
                     const void* linv, unsigned char* ws, cudaStream_t s);
 // tensor-core trailing update (mixed form): task (front, first row tile i0 of a
 // 128-row block, column tile j, store mask in .pad: bit 0 rows of i0, bit 1 rows of i0+1)
-void launch_update_tc(void* pool, const FrontDev* fronts, const Task* tasks, int n, int k,
+// groups: (first task, count) of each run of tasks sharing one A block; n = number of groups
+void launch_update_tc(void* pool, const FrontDev* fronts, const Task* tasks, const int2* groups, int n, int k,
                       const unsigned char* ws, DevStatus* st, cudaStream_t s, int reserve_sms = 0);
 void launch_update(int prec, void* pool, const FrontDev* fronts, const Task* tasks, int n, int k,
                    cudaStream_t s);

@@ -94,8 +94,9 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-__global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontDev* fr, const Task* tasks, int n_tasks,
-                                                      int k, const unsigned char* ws, DevStatus* st) {
+__global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontDev* fr, const Task* tasks,
+                                                      const int2* groups, int n_groups, int k,
+                                                      const unsigned char* ws, DevStatus* st) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   unsigned char* sA = smem;               // resident A block (planes x atoms, 16 KB each)
@@ -107,8 +108,9 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
   const uint32_t b_afull = smem_u32(&bars.a_full), b_aempty = smem_u32(&bars.a_empty);
   const uint32_t b_full0 = smem_u32(&bars.b_full[0]), b_empty0 = smem_u32(&bars.b_empty[0]);
   const uint32_t b_accf0 = smem_u32(&bars.acc_full[0]), b_acce0 = smem_u32(&bars.acc_empty[0]);
-  const int q0 = (int)(((int64_t)blockIdx.x * n_tasks) / gridDim.x);
-  const int q1 = (int)(((int64_t)(blockIdx.x + 1) * n_tasks) / gridDim.x);
+  // groups (runs of tasks that share one A block) are dealt round-robin, so the
+  // groups in flight at any time are consecutive ones of a few fronts and their
+  // B tiles are shared through L2
   if (tid == 0) {
     fail = 0;
     mbar_init(b_afull, 1);
@@ -134,10 +136,11 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
   if (warp == 0 && lane == 0) {
     // ---------------- producer ----------------
     int m = 0, u = 0, pf = -1, pi = -1;
-    for (int q = q0; q < q1 && !fail; ++q) {
+    for (int g = blockIdx.x; g < n_groups && !fail; g += gridDim.x)
+    for (int q = groups[g].x; q < groups[g].x + groups[g].y && !fail; ++q) {
       const Task t = tasks[q];
       const FrontDev F = fr[t.f];
-      if (t.f != pf || t.i != pi) {   // new A block
+      if (q == groups[g].x) {   // new A block
         if (m > 0 && !mbar_wait(b_aempty, (m - 1) & 1)) { fail = 1; break; }
         const unsigned char* gA = ws + F.ws_off + (int64_t)((t.i - k - 1) >> 1) * kA;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b_afull), "r"(kA) : "memory");
@@ -165,9 +168,10 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
     const int bs[6] = {0, 1, 0, 0, 1, 0};
     const int bv[6] = {1, 1, 1, 0, 0, 0};
     const uint32_t a0 = smem_u32(sA), bring = smem_u32(sB);
-    for (int q = q0; q < q1 && !fail; ++q, ++tl) {
+    for (int g = blockIdx.x; g < n_groups && !fail; g += gridDim.x)
+    for (int q = groups[g].x; q < groups[g].x + groups[g].y && !fail; ++q, ++tl) {
       const Task t = tasks[q];
-      if (t.f != pf || t.i != pi) {
+      if (q == groups[g].x) {
         if (!mbar_wait(b_afull, m & 1)) { fail = 1; break; }
         ++m;
         pf = t.f;
@@ -199,22 +203,23 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
       if (fail) break;
       mma_commit(b_accf0 + 8 * ab);
       // the A block is free once the last task that uses it has been issued
-      const bool last_use = (q + 1 >= q1) || tasks[q + 1].f != t.f || tasks[q + 1].i != t.i;
-      if (last_use) mma_commit(b_aempty);
+      if (q + 1 == groups[g].x + groups[g].y) mma_commit(b_aempty);   // last task of the group
     }
   } else if (warp >= 2) {
     // ---------------- epilogue: C -= acc ----------------
     const int sub = warp & 3;                 // TMEM sub-partition of this warp
     const int row = sub * 32 + lane;
     int tl = 0;
-    for (int q = q0; q < q1; ++q, ++tl) {
+    bool stop = false;
+    for (int g = blockIdx.x; g < n_groups && !stop; g += gridDim.x)
+    for (int q = groups[g].x; q < groups[g].x + groups[g].y; ++q, ++tl) {
       const Task t = tasks[q];
       const FrontDev F = fr[t.f];
       const int ab = tl & 1;
       bool ok = !fail;
       if (ok && lane == 0) ok = mbar_wait(b_accf0 + 8 * ab, (tl >> 1) & 1);
       ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-      if (!ok) { fail = 1; break; }
+      if (!ok) { fail = 1; stop = true; break; }
       asm volatile("tcgen05.fence::after_thread_sync;");
       const bool store = (row < T) ? (t.pad & 1) : (t.pad & 2);
       float2* crow = pool + F.off + (int64_t)(t.i * T + row) * F.ld + t.j * T;
@@ -255,8 +260,8 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
 
 }  // namespace
 
-void launch_update_tc(void* pool, const FrontDev* fronts, const Task* tasks, int n, int k, const unsigned char* ws,
-                      DevStatus* st, cudaStream_t s, int reserve_sms) {
+void launch_update_tc(void* pool, const FrontDev* fronts, const Task* tasks, const int2* groups, int n, int k,
+                      const unsigned char* ws, DevStatus* st, cudaStream_t s, int reserve_sms) {
   if (n <= 0) return;
   static int sms = 0;
   if (!sms) {
@@ -268,7 +273,7 @@ void launch_update_tc(void* pool, const FrontDev* fronts, const Task* tasks, int
   }
   const int avail = sms - reserve_sms > 1 ? sms - reserve_sms : 1;
   const int grid = n < avail ? n : avail;
-  k_update_tc<<<grid, 192, kSmemP, s>>>((float2*)pool, fronts, tasks, n, k, ws, st);
+  k_update_tc<<<grid, 192, kSmemP, s>>>((float2*)pool, fronts, tasks, groups, n, k, ws, st);
 }
 
 }  // namespace ddk
