@@ -669,12 +669,14 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
   std::vector<int32_t> h_level_ids, h_diag;
   std::vector<Task> h_trsm, h_updt, h_tc;
   std::vector<int2> h_grp;
-  // runs of consecutive tasks with the same (front, row block)
+  // runs of consecutive tasks with the same (front, row block), at most
+  // kGroupCap long so that the round-robin deal stays balanced
+  constexpr int kGroupCap = 8;
   auto add_groups = [&](int64_t first, int64_t count) -> int {
     int ng = 0;
     for (int64_t q = first; q < first + count;) {
       int64_t e = q + 1;
-      while (e < first + count && h_tc[e].f == h_tc[q].f && h_tc[e].i == h_tc[q].i) ++e;
+      while (e < first + count && e - q < kGroupCap && h_tc[e].f == h_tc[q].f && h_tc[e].i == h_tc[q].i) ++e;
       h_grp.push_back(make_int2((int)q, (int)(e - q)));
       ++ng;
       q = e;
