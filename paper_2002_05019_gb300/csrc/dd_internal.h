@@ -45,11 +45,11 @@ struct FrontDev {
 // A image of a 128-row block: planes (Re hi, Re lo, Im hi, Im lo) x 2 K-atoms of
 // 32 tf32 each, 16 KB per (plane, atom), 128B-swizzled K-major; the two 64-row
 // tiles of the block fill its first and second 8 KB half.  B image of a 64-row
-// column tile: split (hi, lo) x 2 K-atoms x [-Im W][Re W][Im W], 8 KB each.
+// column tile: split (hi, lo) x 2 K-atoms x [Re W][Im W], 8 KB each.
 #define DD_TC_ATOM 16384
 #define DD_TC_HALF 8192
 #define DD_TC_ABLOCK (4 * 2 * DD_TC_ATOM)
-#define DD_TC_BTILE (2 * 2 * 3 * DD_TC_HALF)
+#define DD_TC_BTILE (2 * 2 * 2 * DD_TC_HALF)
 
 struct LeafDev {
   int64_t csr_off;   // offset of the domain's nonzeros in the concatenated CSR arrays

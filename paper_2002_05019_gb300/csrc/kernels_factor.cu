@@ -55,12 +55,12 @@ __device__ __forceinline__ void write_images<float2>(unsigned char* ws, const Fr
   split_tf32(L.y, h, l);
   put_img(Ab + (2 * 2 + a) * DD_TC_ATOM, r, kk, h);
   put_img(Ab + (3 * 2 + a) * DD_TC_ATOM, r, kk, l);
-  const float parts[3] = {-W.y, W.x, W.y};
+  const float parts[2] = {W.x, W.y};
 #pragma unroll
-  for (int v = 0; v < 3; ++v) {
+  for (int v = 0; v < 2; ++v) {
     split_tf32(parts[v], h, l);
-    put_img(Bb + ((0 * 2 + a) * 3 + v) * DD_TC_HALF, r, kk, h);
-    put_img(Bb + ((1 * 2 + a) * 3 + v) * DD_TC_HALF, r, kk, l);
+    put_img(Bb + ((0 * 2 + a) * 2 + v) * DD_TC_HALF, r, kk, h);
+    put_img(Bb + ((1 * 2 + a) * 2 + v) * DD_TC_HALF, r, kk, l);
   }
 }
 

@@ -4,9 +4,9 @@
 //
 // A task is a 128 x 64 complex block of  C -= L_ik D_k L_jk^T  (rows of the
 // tiles i0 and i0+1, column tile j), computed with tcgen05.mma kind::tf32:
-//   * complex product as one real GEMM with a [Re | Im] accumulator:
-//       acc[:, 0:64]   = Lr Wr^T - Li Wi^T,   acc[:, 64:128] = Lr Wi^T + Li Wr^T
-//     = Lr [Wr; Wi]^T + Li [-Wi; Wr]^T  (B operands of N = 128 rows);
+//   * complex product as real GEMMs (N = 64) into a [Re | Im] accumulator:
+//       acc[:, 0:64]   = Lr Wr^T - Li Wi^T,   acc[:, 64:128] = Lr Wi^T + Li Wr^T,
+//     the minus sign through the instruction's negate-A bit;
 //   * 3xTF32 split for FP32 accuracy: X Y^T ~ Xh Yh^T + Xh Yl^T + Xl Yh^T;
 //   * operands are the pre-split, 128B-swizzled K-major images written by the
 //     panel kernel, brought into shared memory by bulk asynchronous copies
@@ -39,8 +39,9 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   return d;
 }
 
-// instruction descriptor: D f32, A/B tf32, both K-major, N = 128, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+// instruction descriptor: D f32, A/B tf32, both K-major, N = 64, M = 128; bit 13 negates A
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr uint32_t kIdescNegA = kIdesc | (1u << 13);
 
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
   for (int it = 0; it < kWaitPolls; ++it) {
@@ -69,14 +70,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t ta, uint32_t (&r)[32]) {
 // Persistent, warp-specialised form: grid <= one CTA per SM, each CTA takes a
 // contiguous chunk of the task list, so consecutive tasks share their 128-row
 // A block.  Warp 0 lane 0 loads the A block (128 KB, resident while it is
-// reused) and streams the B tiles through a two-stage ring (one K-atom of B,
-// 48 KB, per stage); warp 1 lane 0 issues the MMAs into one of two TMEM
+// reused) and streams the B tiles through a three-stage ring (one K-atom of B,
+// 32 KB, per stage); warp 1 lane 0 issues the MMAs into one of two TMEM
 // accumulators; warps 2-5 drain the other accumulator into C.
-constexpr int kStageB = 2 * 3 * DD_TC_HALF;      // 2 splits x [-Wi][Wr][Wi] of one atom = 48 KB
-constexpr int kSmemP = kA + 2 * kStageB + 1024;  // 128 KB + 96 KB + alignment
+constexpr int kStageB = 2 * 2 * DD_TC_HALF;      // 2 splits x [Wr][Wi] of one atom = 32 KB
+constexpr int kBStages = 3;
+constexpr int kSmemP = kA + kBStages * kStageB + 1024;  // 128 KB + 96 KB + alignment
 
 struct PipeBars {
-  uint64_t a_full, a_empty, b_full[2], b_empty[2], acc_full[2], acc_empty[2];
+  uint64_t a_full, a_empty, b_full[kBStages], b_empty[kBStages], acc_full[2], acc_empty[2];
 };
 
 __device__ __forceinline__ void mbar_init(uint32_t b, int count) {
@@ -115,9 +117,11 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
     fail = 0;
     mbar_init(b_afull, 1);
     mbar_init(b_aempty, 1);
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < kBStages; ++i) {
       mbar_init(b_full0 + 8 * i, 1);
       mbar_init(b_empty0 + 8 * i, 1);
+    }
+    for (int i = 0; i < 2; ++i) {
       mbar_init(b_accf0 + 8 * i, 1);
       mbar_init(b_acce0 + 8 * i, 4);   // one arrival per epilogue warp
     }
@@ -135,7 +139,7 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
 
   if (warp == 0 && lane == 0) {
     // ---------------- producer ----------------
-    int m = 0, u = 0, pf = -1, pi = -1;
+    int m = 0, u = 0;
     for (int g = blockIdx.x; g < n_groups && !fail; g += gridDim.x)
     for (int q = groups[g].x; q < groups[g].x + groups[g].y && !fail; ++q) {
       const Task t = tasks[q];
@@ -147,26 +151,21 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
         for (int c = 0; c < kA / DD_TC_ATOM; ++c)
           bulk_g2s(smem_u32(sA + c * DD_TC_ATOM), gA + c * DD_TC_ATOM, DD_TC_ATOM, b_afull);
         ++m;
-        pf = t.f;
-        pi = t.i;
       }
       const unsigned char* gB = ws + F.ws_boff + (int64_t)(t.j - k - 1) * kB;
       for (int a = 0; a < 2; ++a, ++u) {
-        const int sidx = u & 1;
-        if (!mbar_wait(b_empty0 + 8 * sidx, ((u >> 1) & 1) ^ 1)) { fail = 1; break; }
+        const int sidx = u % kBStages;
+        if (!mbar_wait(b_empty0 + 8 * sidx, ((u / kBStages) & 1) ^ 1)) { fail = 1; break; }
         const uint32_t fb = b_full0 + 8 * sidx;
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(kStageB) : "memory");
         for (int sp = 0; sp < 2; ++sp)
-          bulk_g2s(smem_u32(sB + sidx * kStageB + sp * 3 * DD_TC_HALF), gB + (sp * 2 + a) * 3 * DD_TC_HALF,
-                   3 * DD_TC_HALF, fb);
+          bulk_g2s(smem_u32(sB + sidx * kStageB + sp * 2 * DD_TC_HALF), gB + (sp * 2 + a) * 2 * DD_TC_HALF,
+                   2 * DD_TC_HALF, fb);
       }
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
-    int m = 0, u = 0, tl = 0, pf = -1, pi = -1;
-    const int pl[6] = {0, 0, 1, 2, 2, 3};
-    const int bs[6] = {0, 1, 0, 0, 1, 0};
-    const int bv[6] = {1, 1, 1, 0, 0, 0};
+    int m = 0, u = 0, tl = 0;
     const uint32_t a0 = smem_u32(sA), bring = smem_u32(sB);
     for (int g = blockIdx.x; g < n_groups && !fail; g += gridDim.x)
     for (int q = groups[g].x; q < groups[g].x + groups[g].y && !fail; ++q, ++tl) {
@@ -174,29 +173,34 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
       if (q == groups[g].x) {
         if (!mbar_wait(b_afull, m & 1)) { fail = 1; break; }
         ++m;
-        pf = t.f;
-        pi = t.i;
       }
       const int ab = tl & 1;
       if (!mbar_wait(b_acce0 + 8 * ab, ((tl >> 1) & 1) ^ 1)) { fail = 1; break; }
       asm volatile("tcgen05.fence::after_thread_sync;");
       const uint32_t dacc = tmem + ab * 128;
-      uint32_t acc = 0;
+      uint32_t init_re = 0, init_im = 0;   // accumulator halves already written for this task
       for (int a = 0; a < 2; ++a, ++u) {
-        const int sidx = u & 1;
-        if (!mbar_wait(b_full0 + 8 * sidx, (u >> 1) & 1)) { fail = 1; break; }
+        const int sidx = u % kBStages;
+        if (!mbar_wait(b_full0 + 8 * sidx, (u / kBStages) & 1)) { fail = 1; break; }
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t b0 = bring + sidx * kStageB;
         for (int s4 = 0; s4 < 4; ++s4)
 #pragma unroll
-          for (int qq = 0; qq < 6; ++qq) {
-            const uint64_t ad = desc_sw128(a0 + (pl[qq] * 2 + a) * DD_TC_ATOM + s4 * 32);
-            const uint64_t bd = desc_sw128(b0 + (bs[qq] * 3 + bv[qq]) * DD_TC_HALF + s4 * 32);
-            asm volatile(
-                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dacc),
-                "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc));
-            acc = 1;
+          for (int sp = 0; sp < 3; ++sp) {     // split pairs (hi, hi), (hi, lo), (lo, hi)
+            const int as = sp == 2 ? 1 : 0, bsp = sp == 1 ? 1 : 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              // (Re L, Re W) -> Re, (Im L, Im W, negated) -> Re, (Re L, Im W) -> Im, (Im L, Re W) -> Im
+              const int ar = q & 1, bw = (q == 1 || q == 2) ? 1 : 0, dh = q >> 1;
+              const uint64_t ad = desc_sw128(a0 + ((ar * 2 + as) * 2 + a) * DD_TC_ATOM + s4 * 32);
+              const uint64_t bd = desc_sw128(b0 + (bsp * 2 + bw) * DD_TC_HALF + s4 * 32);
+              const uint32_t en = dh ? init_im : init_re;
+              asm volatile(
+                  "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                  " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dacc + dh * 64),
+                  "l"(ad), "l"(bd), "r"(q == 1 ? kIdescNegA : kIdesc), "r"(en));
+              if (dh) init_im = 1; else init_re = 1;
+            }
           }
         mma_commit(b_empty0 + 8 * sidx);   // the B stage is free once these MMAs have read it
       }
