@@ -130,6 +130,8 @@ struct dd_handle {
   Task *d_fwd = nullptr, *d_bwd = nullptr;
   Task* d_tc = nullptr;            // tensor-core update tasks (mixed form)
   int2* d_grp = nullptr;           // their groups (first task, count) sharing one A block
+  int* d_counters = nullptr;       // one group counter per tensor-core update launch of a factor
+  int n_counters = 0;
   unsigned char* d_ws = nullptr;   // panel operand images (mixed form)
   float2* d_linv = nullptr;        // mixed form: L_kk^{-1} of every diagonal tile (index tile_off + k)
   cudaStream_t s2 = nullptr;       // look-ahead: bulk trailing updates run here
@@ -811,6 +813,12 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
   DD_CUDA(A.upload(&h->d_fwd, h_fwd, s));
   DD_CUDA(A.upload(&h->d_tc, h_tc, s));
   DD_CUDA(A.upload(&h->d_grp, h_grp, s));
+  {
+    int nl = 0;
+    for (auto& L : h->levels) nl += 2 * (int)L.steps.size();
+    h->n_counters = std::max(nl, 1);
+    DD_CUDA(A.alloc(&h->d_counters, (size_t)h->n_counters));
+  }
   if (h->use_tc) DD_CUDA(A.alloc(&h->d_ws, 2 * h->ws_bytes));   // two step parities (look-ahead)
   DD_CUDA(cudaStreamCreateWithFlags(&h->s2, cudaStreamNonBlocking));
   DD_CUDA(cudaEventCreateWithFlags(&h->ev_panel, cudaEventDisableTiming));
@@ -895,6 +903,8 @@ int dd_factor(dd_handle* h) {
     }
   };
   ddk::launch_zero(h->pool, h->pool_bytes, s);
+  if (h->d_counters) ddk::launch_zero(h->d_counters, sizeof(int) * h->n_counters, s);
+  int next_counter = 0;
   DD_CUDA(mark(DD_K_INIT, true));
   ddk::launch_leaf_init(p, h->pool, h->d_fronts, h->d_leaves, h->n_sub, h->d_rowptr, h->d_colind, h->d_val,
                         h->d_iperm, h->d_brow, h->d_blocal, h->d_bsign, s);
@@ -951,7 +961,8 @@ int dd_factor(dd_handle* h) {
       if (e != cudaSuccess) return e;
       if (h->use_tc)
         ddk::launch_update_tc(h->pool, h->d_fronts, h->d_tc, h->d_grp + R.grp_off + (next_part ? 0 : R.n_grp_next),
-                              next_part ? R.n_grp_next : R.n_grp_rest, R.k, ws, h->d_status, on, cap);
+                              next_part ? R.n_grp_next : R.n_grp_rest, R.k, ws, h->d_status, on, cap,
+                              h->d_counters + (next_counter++ % h->n_counters));
       else
         ddk::launch_update(p, h->pool, h->d_fronts, h->d_updt + first, n, R.k, on);
       count(DD_K_UPDATE, n);

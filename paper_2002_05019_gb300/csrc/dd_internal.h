@@ -98,9 +98,10 @@ void launch_trsm_mx(void* pool, const FrontDev* fronts, const Task* tasks, int n
                     const void* linv, unsigned char* ws, cudaStream_t s);
 // tensor-core trailing update (mixed form): task (front, first row tile i0 of a
 // 128-row block, column tile j, store mask in .pad: bit 0 rows of i0, bit 1 rows of i0+1)
-// groups: (first task, count) of each run of tasks sharing one A block; n = number of groups
+// groups: (first task, count) of each run of tasks sharing one A block; n = number of groups;
+// counter: a zeroed int in device memory used to claim groups dynamically (one per launch)
 void launch_update_tc(void* pool, const FrontDev* fronts, const Task* tasks, const int2* groups, int n, int k,
-                      const unsigned char* ws, DevStatus* st, cudaStream_t s, int reserve_sms = 0);
+                      const unsigned char* ws, DevStatus* st, cudaStream_t s, int reserve_sms, int* counter);
 void launch_update(int prec, void* pool, const FrontDev* fronts, const Task* tasks, int n, int k,
                    cudaStream_t s);
 void launch_extend_add(int prec, void* pool, const FrontDev* fronts, const int32_t* node_ids, int n,

@@ -77,8 +77,11 @@ constexpr int kStageB = 2 * 2 * DD_TC_HALF;      // 2 splits x [Wr][Wi] of one a
 constexpr int kBStages = 3;
 constexpr int kSmemP = kA + kBStages * kStageB + 1024;  // 128 KB + 96 KB + alignment
 
+constexpr int kRing = 8;   // group ids handed from the producer to the MMA and epilogue roles
+
 struct PipeBars {
   uint64_t a_full, a_empty, b_full[kBStages], b_empty[kBStages], acc_full[2], acc_empty[2];
+  uint64_t g_full[kRing], g_empty[kRing];
 };
 
 __device__ __forceinline__ void mbar_init(uint32_t b, int count) {
@@ -98,7 +101,7 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 
 __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontDev* fr, const Task* tasks,
                                                       const int2* groups, int n_groups, int k,
-                                                      const unsigned char* ws, DevStatus* st) {
+                                                      const unsigned char* ws, DevStatus* st, int* counter) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   unsigned char* sA = smem;               // resident A block (planes x atoms, 16 KB each)
@@ -106,13 +109,16 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
   __shared__ __align__(8) PipeBars bars;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int fail;
+  __shared__ int gring[kRing];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t b_afull = smem_u32(&bars.a_full), b_aempty = smem_u32(&bars.a_empty);
   const uint32_t b_full0 = smem_u32(&bars.b_full[0]), b_empty0 = smem_u32(&bars.b_empty[0]);
   const uint32_t b_accf0 = smem_u32(&bars.acc_full[0]), b_acce0 = smem_u32(&bars.acc_empty[0]);
-  // groups (runs of tasks that share one A block) are dealt round-robin, so the
-  // groups in flight at any time are consecutive ones of a few fronts and their
-  // B tiles are shared through L2
+  // groups (runs of <= 8 tasks that share one A block) are claimed dynamically
+  // from a global counter in list order, so the groups in flight at any time are
+  // consecutive ones of a few fronts (their B tiles are shared through L2) and
+  // faster SMs simply take more of them
+  const uint32_t b_gfull0 = smem_u32(&bars.g_full[0]), b_gempty0 = smem_u32(&bars.g_empty[0]);
   if (tid == 0) {
     fail = 0;
     mbar_init(b_afull, 1);
@@ -124,6 +130,10 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
     for (int i = 0; i < 2; ++i) {
       mbar_init(b_accf0 + 8 * i, 1);
       mbar_init(b_acce0 + 8 * i, 4);   // one arrival per epilogue warp
+    }
+    for (int i = 0; i < kRing; ++i) {
+      mbar_init(b_gfull0 + 8 * i, 1);
+      mbar_init(b_gempty0 + 8 * i, 5);  // the MMA issuer and the four epilogue warps
     }
     asm volatile("fence.mbarrier_init.release.cluster;");
     asm volatile("fence.proxy.async.shared::cta;");
@@ -140,7 +150,13 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
   if (warp == 0 && lane == 0) {
     // ---------------- producer ----------------
     int m = 0, u = 0;
-    for (int g = blockIdx.x; g < n_groups && !fail; g += gridDim.x)
+    for (int it = 0; !fail; ++it) {
+      const int slot = it % kRing;
+      if (!mbar_wait(b_gempty0 + 8 * slot, ((it / kRing) & 1) ^ 1)) { fail = 1; break; }
+      const int g = atomicAdd(counter, 1);
+      gring[slot] = g < n_groups ? g : -1;
+      mbar_arrive(b_gfull0 + 8 * slot);
+      if (g >= n_groups) break;
     for (int q = groups[g].x; q < groups[g].x + groups[g].y && !fail; ++q) {
       const Task t = tasks[q];
       const FrontDev F = fr[t.f];
@@ -163,11 +179,17 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
                    2 * DD_TC_HALF, fb);
       }
     }
+    }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer ----------------
     int m = 0, u = 0, tl = 0;
     const uint32_t a0 = smem_u32(sA), bring = smem_u32(sB);
-    for (int g = blockIdx.x; g < n_groups && !fail; g += gridDim.x)
+    for (int it = 0; !fail; ++it) {
+      const int slot = it % kRing;
+      if (!mbar_wait(b_gfull0 + 8 * slot, (it / kRing) & 1)) { fail = 1; break; }
+      const int g = gring[slot];
+      mbar_arrive(b_gempty0 + 8 * slot);
+      if (g < 0) break;
     for (int q = groups[g].x; q < groups[g].x + groups[g].y && !fail; ++q, ++tl) {
       const Task t = tasks[q];
       if (q == groups[g].x) {
@@ -209,13 +231,26 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
       // the A block is free once the last task that uses it has been issued
       if (q + 1 == groups[g].x + groups[g].y) mma_commit(b_aempty);   // last task of the group
     }
+    }
   } else if (warp >= 2) {
     // ---------------- epilogue: C -= acc ----------------
     const int sub = warp & 3;                 // TMEM sub-partition of this warp
     const int row = sub * 32 + lane;
     int tl = 0;
     bool stop = false;
-    for (int g = blockIdx.x; g < n_groups && !stop; g += gridDim.x)
+    for (int it = 0; !stop; ++it) {
+      const int slot = it % kRing;
+      int g = -1;
+      bool okg = true;
+      if (lane == 0) {
+        okg = mbar_wait(b_gfull0 + 8 * slot, (it / kRing) & 1);
+        if (okg) g = gring[slot];
+      }
+      okg = __shfl_sync(0xffffffffu, okg ? 1 : 0, 0) != 0;
+      g = __shfl_sync(0xffffffffu, g, 0);
+      if (lane == 0 && okg) mbar_arrive(b_gempty0 + 8 * slot);
+      if (!okg) { fail = 1; break; }
+      if (g < 0) break;
     for (int q = groups[g].x; q < groups[g].x + groups[g].y; ++q, ++tl) {
       const Task t = tasks[q];
       const FrontDev F = fr[t.f];
@@ -250,6 +285,7 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
       __syncwarp();
       if (lane == 0) mbar_arrive(b_acce0 + 8 * ab);
     }
+    }
   }
   __syncthreads();
   if (fail && tid == 0) {
@@ -265,7 +301,7 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
 }  // namespace
 
 void launch_update_tc(void* pool, const FrontDev* fronts, const Task* tasks, const int2* groups, int n, int k,
-                      const unsigned char* ws, DevStatus* st, cudaStream_t s, int reserve_sms) {
+                      const unsigned char* ws, DevStatus* st, cudaStream_t s, int reserve_sms, int* counter) {
   if (n <= 0) return;
   static int sms = 0;
   if (!sms) {
@@ -277,7 +313,7 @@ void launch_update_tc(void* pool, const FrontDev* fronts, const Task* tasks, con
   }
   const int avail = sms - reserve_sms > 1 ? sms - reserve_sms : 1;
   const int grid = n < avail ? n : avail;
-  k_update_tc<<<grid, 192, kSmemP, s>>>((float2*)pool, fronts, tasks, groups, n, k, ws, st);
+  k_update_tc<<<grid, 192, kSmemP, s>>>((float2*)pool, fronts, tasks, groups, n, k, ws, st, counter);
 }
 
 }  // namespace ddk
