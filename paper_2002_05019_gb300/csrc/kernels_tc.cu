@@ -74,8 +74,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t ta, uint32_t (&r)[32]) {
 // 32 KB, per stage); warp 1 lane 0 issues the MMAs into one of two TMEM
 // accumulators; warps 2-5 drain the other accumulator into C.
 constexpr int kStageB = 2 * 2 * DD_TC_HALF;      // 2 splits x [Wr][Wi] of one atom = 32 KB
-constexpr int kBStages = 3;
-constexpr int kSmemP = kA + kBStages * kStageB + 1024;  // 128 KB + 96 KB + alignment
+constexpr int kBStages = 2;
+constexpr int kStg = 32 * 33;                            // per epilogue warp: 32 x 32 complex, padded rows
+constexpr int kSmemP = kA + kBStages * kStageB + 4 * kStg * 8 + 1024;  // 128 + 64 + 33 KB + alignment
 
 constexpr int kRing = 8;   // group ids handed from the producer to the MMA and epilogue roles
 
@@ -106,6 +107,7 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   unsigned char* sA = smem;               // resident A block (planes x atoms, 16 KB each)
   unsigned char* sB = smem + kA;          // B ring: stage s at sB + s * kStageB
+  float2* stage_c = reinterpret_cast<float2*>(smem + kA + kBStages * kStageB);   // epilogue transposes
   __shared__ __align__(8) PipeBars bars;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int fail;
@@ -260,8 +262,10 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
       ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
       if (!ok) { fail = 1; stop = true; break; }
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const bool store = (row < T) ? (t.pad & 1) : (t.pad & 2);
-      float2* crow = pool + F.off + (int64_t)(t.i * T + row) * F.ld + t.j * T;
+      // rows sub*32 .. sub*32+31 all lie in one 64-row tile: one store flag per warp
+      const bool store = (sub < 2) ? (t.pad & 1) : (t.pad & 2);
+      float2* stg = stage_c + (warp - 2) * kStg;
+      float2* cblk = pool + F.off + (int64_t)(t.i * T + sub * 32) * F.ld + t.j * T;
 #pragma unroll 1
       for (int h = 0; h < 2; ++h) {
         uint32_t vr[32], vi[32];
@@ -270,15 +274,22 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
         tmem_ld32(ta + 64, vi);
         asm volatile("tcgen05.wait::ld.sync.aligned;");
         if (store) {
-          // C -= acc as vector reductions performed in L2: no load of C on
-          // the SM; each element receives exactly one addition per launch
-          float* c4 = reinterpret_cast<float*>(crow + h * 32);
+          // thread = row -> shared memory -> two rows x 32 columns per warp access, so the
+          // reductions into C are row-contiguous (256 B per row)
 #pragma unroll
-          for (int c = 0; c < 16; ++c)
-            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(c4 + 4 * c),
-                         "f"(-__uint_as_float(vr[2 * c])), "f"(-__uint_as_float(vi[2 * c])),
-                         "f"(-__uint_as_float(vr[2 * c + 1])), "f"(-__uint_as_float(vi[2 * c + 1]))
+          for (int c = 0; c < 32; ++c) stg[lane * 33 + c] = make_float2(-__uint_as_float(vr[c]), -__uint_as_float(vi[c]));
+          __syncwarp();
+          const int rsub = lane >> 4, cpair = (lane & 15) * 2;
+#pragma unroll 4
+          for (int rr = 0; rr < 16; ++rr) {
+            const int r = 2 * rr + rsub;
+            const float2 v0 = stg[r * 33 + cpair], v1 = stg[r * 33 + cpair + 1];
+            float* dst = reinterpret_cast<float*>(cblk + (int64_t)r * F.ld + h * 32 + cpair);
+            asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(v0.x), "f"(v0.y), "f"(v1.x),
+                         "f"(v1.y)
                          : "memory");
+          }
+          __syncwarp();
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;");
