@@ -210,7 +210,8 @@ def backward_error(p, u):
 def time_form(p, precision, args, torch, stream):
     import paper_2002_05019_gb300 as dd
     s = dd.Solver.from_problem(p, precision=precision, stream=stream.cuda_stream, device=torch.cuda.current_device(),
-                               time_kernels=True, refine_tol=args.refine_tol)
+                               time_kernels=not args.no_kernel_timing, refine_tol=args.refine_tol,
+                               pivoting=args.pivoting)
     f_host = dd.stacked_loads(p)
     f_dev = torch.from_numpy(f_host).cuda()
     for _ in range(args.warmup):
@@ -330,7 +331,7 @@ def ours_arm(args):
         "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "c64+f64" if args.precision == "mixed" else "c128", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload][1], "form": args.precision, "n_dofs": p.n,
-                   "n_domains": p.n_sub, "n_duals": p.n_dual, "nrhs": p.nrhs,
+                   "n_domains": p.n_sub, "n_duals": p.n_dual, "nrhs": p.nrhs, "pivoting": args.pivoting,
                    "l2": "working set (front pool) far larger than the 129 MB L2",
                    "parallelism": f"replicas x{ws}"},
         "tflops": flops_step / t_step / 1e12,
@@ -374,6 +375,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--pivoting", type=int, default=0, choices=[0, 1, 2],
+                    help="restricted Bunch-Kaufman: 0 none, 1 auxiliary fronts, 2 every front")
+    ap.add_argument("--no-kernel-timing", action="store_true",
+                    help="no per-launch CUDA events (no kernel breakdown or roofline)")
     ap.add_argument("--refine-tol", type=float, default=1e-11,
                     help="mixed form: stop refinement at this relative correction (1e-11 keeps the error <= 1e-10)")
     args = ap.parse_args()

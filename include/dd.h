@@ -85,7 +85,13 @@ typedef struct {
   double refine_tol;        /* MIXED: stop when |du|/|u| <= refine_tol (default 1e-13) */
   int32_t max_refine;       /* MIXED: refinement iteration cap (default 10); FP64: extra
                                FP64 refinement steps after the direct solve (default 0) */
-  int32_t pivoting;         /* 0: unpivoted LDL^T (exists for lossy domains) - only value accepted */
+  int32_t pivoting;         /* 0: unpivoted LDL^T everywhere (it exists for lossy domains).
+                               1: restricted Bunch-Kaufman pivoting (Section II) in the diagonal
+                                  blocks of the auxiliary-matrix fronts: 64 x 64 tiles (FP64 form)
+                                  or 32 x 32 FP64 pivot blocks (mixed form); the domains unpivoted.
+                               2: the same in the domain fronts too.
+                               Pivots never leave their diagonal block, so the symbolic structure
+                               is unchanged; other values: DD_ERR_INVALID_ARG. */
   const int32_t* tree_parent; /* optional, 2*n_sub-1 entries: binary domain tree, leaves
                                  0..n_sub-1 are the domains, internal nodes n_sub.. with every
                                  parent id larger than its children's, root parent = -1.
@@ -122,6 +128,8 @@ typedef struct {
   double kernel_ms[DD_K_NCLASS];        /* time_kernels: summed device time per class, last dd_factor */
   int32_t kernel_launches[DD_K_NCLASS]; /* launches per class in one dd_factor */
   double kernel_flops[DD_K_NCLASS];     /* algorithmic real flops per class in one dd_factor */
+  int64_t interchanges;      /* pivoting: symmetric interchanges in the last dd_factor */
+  int64_t pivots_2x2;        /* pivoting: 2 x 2 pivot blocks in the last dd_factor */
 } dd_stats;
 
 /* Fill `opt` with defaults (FP64, no tree, default stream, device 0). */

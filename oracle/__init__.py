@@ -11,15 +11,20 @@ Routes to the same solution x = A^{-1} b of the assembled FEM system:
   * dd.DDOracle             - the paper's decomposition route (Section II):
                               per-domain LDL^T, F = sum B_i A_i^{-1} B_i^T,
                               F lambda = d, primal recovery;
+  * dd.arrow_solve          - the arrowhead system solved undecomposed by LU with
+                              partial pivoting (inputs whose LDL^T needs pivoting);
+  * dense.ldlt_bk_restricted - LDL^T with Bunch-Kaufman pivoting restricted to
+                              diagonal blocks (the pivoting rule of Section II);
   * refine.residual_dd      - double-double residuals for iterative refinement.
 
 Parity status: pinned by closed forms and library special cases (see the
 tests); the paper prints no numerical values, so no value of the paper pins it.
 """
-from .dense import lu_solve, ldlt, ldlt_solve
+from .dense import lu_solve, ldlt, ldlt_solve, ldlt_bk_restricted, ldlt_bk_solve
 from .skyline import BandLDLT, rcm
-from .dd import DDOracle, subdomain_schur, arrow_residual, local_B
+from .dd import DDOracle, subdomain_schur, arrow_residual, local_B, arrow_dense, arrow_solve
 from .refine import residual_dd, refine, backward_error
 
-__all__ = ["lu_solve", "ldlt", "ldlt_solve", "BandLDLT", "rcm", "DDOracle", "subdomain_schur",
-           "arrow_residual", "local_B", "residual_dd", "refine", "backward_error"]
+__all__ = ["lu_solve", "ldlt", "ldlt_solve", "ldlt_bk_restricted", "ldlt_bk_solve", "BandLDLT", "rcm",
+           "DDOracle", "subdomain_schur", "arrow_residual", "local_B", "arrow_dense", "arrow_solve",
+           "residual_dd", "refine", "backward_error"]

@@ -21,7 +21,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .dense import ldlt, ldlt_solve
+from .dense import ldlt, ldlt_solve, lu_solve
 
 
 def local_B(sub) -> np.ndarray:
@@ -119,3 +119,34 @@ def arrow_residual(problem, u_list, lam, g=None):
     if g is not None:
         ru -= g
     return rp, ru
+
+
+def _csr_dense(sub) -> np.ndarray:
+    A = np.zeros((sub.n, sub.n), dtype=np.complex128)
+    rows = np.repeat(np.arange(sub.n), np.diff(sub.indptr))
+    A[rows, sub.indices] = sub.data
+    return A
+
+
+def arrow_dense(subs, n_dual: int) -> np.ndarray:
+    """Step 1 written out: the dense arrowhead matrix [blkdiag(A_i) B^T; B 0]."""
+    n_loc = sum(s.n for s in subs)
+    K = np.zeros((n_loc + n_dual, n_loc + n_dual), dtype=np.complex128)
+    off = 0
+    for s in subs:
+        K[off:off + s.n, off:off + s.n] = _csr_dense(s)
+        K[n_loc + s.b_dual, off + s.b_local] = s.b_sign
+        K[off + s.b_local, n_loc + s.b_dual] = s.b_sign
+        off += s.n
+    return K
+
+
+def arrow_solve(subs, n_dual: int, f: np.ndarray):
+    """The arrowhead system solved as one undecomposed system by LU with partial
+    pivoting (no LDL^T, so no pivoting assumption): (stacked u, lambda) for the
+    stacked loads f (n_loc, k) and g = 0."""
+    n_loc = sum(s.n for s in subs)
+    rhs = np.zeros((n_loc + n_dual, f.shape[1]), dtype=np.complex128)
+    rhs[:n_loc] = f
+    x = lu_solve(arrow_dense(subs, n_dual), rhs)
+    return x[:n_loc], x[n_loc:]

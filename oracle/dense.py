@@ -8,6 +8,13 @@
   symmetric LDL^T (Section II); existence without pivoting follows from the
   lossy domains: Im(x^H A x) > 0 for every x != 0, so every leading principal
   submatrix is nonsingular.
+* ldlt_bk_restricted / ldlt_bk_solve: complex-symmetric LDL^T with the
+  Bunch-Kaufman pivot choice (Bunch & Kaufman 1977, partial pivoting with
+  1x1 and 2x2 pivots, alpha = (1 + sqrt 17) / 8) whose search is restricted to
+  the diagonal block holding the current column, the "restricted
+  Bunch-Kaufman" of the block LDL^T of the auxiliary matrix (Section II).
+  Right-looking, one column (or column pair) at a time, with the interchanges
+  applied to the whole matrix.
 """
 from __future__ import annotations
 
@@ -78,3 +85,80 @@ def ldlt_solve(L: np.ndarray, d: np.ndarray, b: np.ndarray) -> np.ndarray:
     z = forward_unit(L, b)
     z = z / (d[:, None] if z.ndim == 2 else d)
     return backward_unit_t(L, z)
+
+
+BK_ALPHA = (1.0 + np.sqrt(17.0)) / 8.0
+
+
+def ldlt_bk_restricted(A: np.ndarray, nb: int):
+    """A[perm][:, perm] = L D L^T with restricted Bunch-Kaufman pivoting.
+
+    The diagonal blocks are [b, b + nb) for b = 0, nb, 2 nb, ...; at column j
+    (block end e) with S the trailing matrix:
+      lambda = max_{j < i < e} |S_ij| (first maximiser r); if lambda = 0 or
+      |S_jj| >= alpha lambda: 1x1 pivot at j; else with
+      sigma = max_{j <= i < e, i != r} |S_ir|: 1x1 at j if |S_jj| sigma >=
+      alpha lambda^2, else 1x1 at j after interchanging j and r if
+      |S_rr| >= alpha sigma, else a 2x2 pivot on (j, j+1) after
+      interchanging j+1 and r.
+    Returns (perm, L unit lower, D block diagonal, interchanges, 2x2 pivots).
+    """
+    S = np.array(A, dtype=np.complex128, copy=True)
+    n = S.shape[0]
+    perm = np.arange(n)
+    L = np.eye(n, dtype=np.complex128)
+    D = np.zeros((n, n), dtype=np.complex128)
+    n_swap = n_2x2 = 0
+    j = 0
+    while j < n:
+        e = min((j // nb + 1) * nb, n)
+        step, q = 1, -1
+        col = np.abs(S[j + 1:e, j])
+        if col.size and col.max() > 0:
+            lam = col.max()
+            r = j + 1 + int(np.argmax(col))
+            ajj = abs(S[j, j])
+            if ajj < BK_ALPHA * lam:
+                sig = max(abs(S[i, r]) for i in range(j, e) if i != r)
+                if ajj * sig >= BK_ALPHA * lam * lam:
+                    pass
+                elif abs(S[r, r]) >= BK_ALPHA * sig:
+                    q = r
+                else:
+                    step = 2
+                    q = r if r != j + 1 else -1
+        if q >= 0:
+            p = j + step - 1
+            S[[p, q], :] = S[[q, p], :]
+            S[:, [p, q]] = S[:, [q, p]]
+            L[[p, q], :j] = L[[q, p], :j]
+            perm[[p, q]] = perm[[q, p]]
+            n_swap += 1
+        if step == 1:
+            D[j, j] = S[j, j]
+            if S[j, j] == 0:
+                raise np.linalg.LinAlgError(f"zero pivot at {j}")
+            w = S[j + 1:, j].copy()                   # d_j l_ij
+            L[j + 1:, j] = w / S[j, j]
+            S[j + 1:, j + 1:] -= np.outer(L[j + 1:, j], w)
+        else:
+            Db = S[j:j + 2, j:j + 2].copy()
+            D[j:j + 2, j:j + 2] = Db
+            W = S[j + 2:, j:j + 2].copy()               # L_b D_b
+            Lb = np.linalg.solve(Db.T, W.T).T          # W D_b^{-1}
+            L[j + 2:, j:j + 2] = Lb
+            S[j + 2:, j + 2:] -= Lb @ W.T
+            n_2x2 += 1
+        j += step
+    return perm, L, D, n_swap, n_2x2
+
+
+def ldlt_bk_solve(perm, L, D, b: np.ndarray) -> np.ndarray:
+    """x = A^{-1} b from A[perm][:, perm] = L D L^T."""
+    b = np.asarray(b, dtype=np.complex128)
+    z = forward_unit(L, b[perm])
+    z = np.linalg.solve(D, z)
+    y = backward_unit_t(L, z)
+    x = np.empty_like(y)
+    x[perm] = y
+    return x

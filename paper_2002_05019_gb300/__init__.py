@@ -61,7 +61,8 @@ class Stats(C.Structure):
                 ("t_setup_ms", C.c_double), ("t_factor_ms", C.c_double), ("t_solve_ms", C.c_double),
                 ("growth", C.c_double), ("min_pivot", C.c_double), ("refine_iters", C.c_int32),
                 ("refine_last", C.c_double), ("launches_factor", C.c_int32), ("launches_solve", C.c_int32),
-                ("kernel_ms", C.c_double * 5), ("kernel_launches", C.c_int32 * 5), ("kernel_flops", C.c_double * 5)]
+                ("kernel_ms", C.c_double * 5), ("kernel_launches", C.c_int32 * 5), ("kernel_flops", C.c_double * 5),
+                ("interchanges", C.c_int64), ("pivots_2x2", C.c_int64)]
 
 
 EXPORTS = ["dd_default_options", "dd_setup", "dd_set_values", "dd_factor", "dd_solve", "dd_get_schur",
@@ -121,7 +122,7 @@ class Solver:
 
     def __init__(self, subdomains, n_dual: int, precision: str = "fp64", refine_tol: float = 1e-13,
                  max_refine: int | None = None, tree_parent=None, centroids=None, stream=None, device: int = 0,
-                 time_kernels: bool = False, simt_update: bool = False):
+                 time_kernels: bool = False, simt_update: bool = False, pivoting: int | None = None):
         lib = load()
         self._keep = []
         subs = (Subdomain * len(subdomains))()
@@ -159,6 +160,8 @@ class Solver:
         opt.device = device
         opt.time_kernels = 1 if time_kernels else 0
         opt.simt_update = 1 if simt_update else 0
+        if pivoting is not None:
+            opt.pivoting = int(pivoting)   # 0 none, 1 auxiliary fronts, 2 every front (restricted Bunch-Kaufman)
         self.precision = precision
         h = C.c_void_p()
         _check(lib.dd_setup(C.byref(h), len(subdomains), subs, self.n_dual, C.byref(opt)), "dd_setup")

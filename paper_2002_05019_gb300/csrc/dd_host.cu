@@ -134,6 +134,8 @@ struct dd_handle {
   int n_counters = 0;
   unsigned char* d_ws = nullptr;   // panel operand images (mixed form)
   float2* d_linv = nullptr;        // mixed form: L_kk^{-1} of every diagonal tile (index tile_off + k)
+  uint8_t* d_piv = nullptr;        // restricted Bunch-Kaufman: permutation of every diagonal tile (64 bytes each)
+  int pivoting = 0;
   cudaStream_t s2 = nullptr;       // look-ahead: bulk trailing updates run here
   cudaEvent_t ev_panel = nullptr, ev_rest = nullptr;
   size_t ws_bytes = 0;
@@ -340,13 +342,13 @@ void direct_solve(dd_handle* h, int nrhs, const double2* f, int64_t ldf, const d
       h->launches += 3;
     }
     ddk::launch_forward(p, h->pool, h->rpool, h->d_fronts, h->d_fwd + L.fwd_off, L.n_fwd, nrhs, h->d_flag_f, ep,
-                        h->d_solve_status, s, h->d_linv);
+                        h->d_solve_status, s, h->d_linv, h->d_piv);
     h->launches += 1;
   }
   for (size_t l = h->levels.size(); l-- > 0;) {
     const Level& L = h->levels[l];
     ddk::launch_backward(p, h->pool, h->rpool, h->d_fronts, h->d_bwd + L.bwd_off, L.n_bwd, nrhs, h->d_upd, h->d_sep,
-                         h->lam_work, h->n_dual, h->d_flag_b, ep, h->d_solve_status, s, h->d_linv);
+                         h->lam_work, h->n_dual, h->d_flag_b, ep, h->d_solve_status, s, h->d_linv, h->d_piv);
     h->launches += 1;
   }
   ddk::launch_leaf_out(p, h->rpool, h->d_fronts, h->d_leaves, h->n_sub, h->d_perm, u, h->n_loc, nrhs, 0, s);
@@ -411,7 +413,8 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
   dd_default_options(&opt);
   if (opt_in) opt = *opt_in;
   if (opt.precision != DD_PREC_FP64 && opt.precision != DD_PREC_MIXED) return DD_ERR_INVALID_ARG;
-  if (opt.pivoting != 0 || opt.max_refine < 0 || !(opt.refine_tol >= 0)) return DD_ERR_INVALID_ARG;
+  if (opt.pivoting < 0 || opt.pivoting > 2 || opt.max_refine < 0 || !(opt.refine_tol >= 0))
+    return DD_ERR_INVALID_ARG;
   if (opt.device < 0) return DD_ERR_INVALID_ARG;
 
   double amax = 0.0;
@@ -433,6 +436,7 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
   h->elem = opt.precision == DD_PREC_FP64 ? 16 : 8;
   h->time_kernels = opt.time_kernels ? 1 : 0;
   h->use_tc = (opt.precision == DD_PREC_MIXED && !opt.simt_update) ? 1 : 0;
+  h->pivoting = opt.pivoting;
   h->max_abs_a = std::max(amax, 1.0);
   cudaStream_t s = h->stream;
 
@@ -514,6 +518,7 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
     h->leaf_vec_off[i] = vec_off;
 
     FrontDev& F = h->fronts[i];
+    F.piv = h->pivoting == 2 ? 1 : 0;   // domain fronts pivot in mode 2 only
     F.kind = 0;
     F.sub = i;
     F.ne = sd.n;
@@ -588,6 +593,7 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
   for (int v = n_sub; v < n_front; ++v) {
     FrontDev& F = h->fronts[v];
     F.kind = 1;
+    F.piv = h->pivoting >= 1 ? 1 : 0;   // auxiliary fronts pivot in modes 1 and 2
     F.sub = -1;
     std::vector<int32_t> all;
     for (int c : children[v]) all.insert(all.end(), upd[c].begin(), upd[c].end());
@@ -825,6 +831,7 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
   DD_CUDA(cudaEventCreateWithFlags(&h->ev_rest, cudaEventDisableTiming));
   // mixed form: L^{-1} of every diagonal tile (panel products and the substitution)
   if (h->prec == DD_PREC_MIXED) DD_CUDA(A.alloc(&h->d_linv, (size_t)std::max<int64_t>(h->n_tiles, 1) * T * T));
+  if (h->pivoting) DD_CUDA(A.alloc(&h->d_piv, (size_t)std::max<int64_t>(h->n_tiles, 1) * T));
   DD_CUDA(A.upload(&h->d_bwd, h_bwd, s));
   DD_CUDA(A.alloc(&h->d_flag_f, (size_t)std::max<int64_t>(h->n_tiles, 1)));
   DD_CUDA(A.alloc(&h->d_flag_b, (size_t)std::max<int64_t>(h->n_tiles, 1)));
@@ -935,17 +942,19 @@ int dd_factor(dd_handle* h) {
       cudaError_t e = mark(DD_K_DIAG, true);
       if (e != cudaSuccess) return e;
       if (p == 0)
-        ddk::launch_diag(p, 0, h->pool, h->d_fronts, h->d_diag_ids + R.diag_off, R.n_diag, R.k, h->d_status, s);
+        ddk::launch_diag(p, 0, h->pool, h->d_fronts, h->d_diag_ids + R.diag_off, R.n_diag, R.k, h->d_status, s,
+                         h->d_piv);
       else
         ddk::launch_diag_mx(diag64, h->pool, h->d_fronts, h->d_diag_ids + R.diag_off, R.n_diag, R.k, h->d_status,
-                            h->d_linv, s);
+                            h->d_linv, s, h->d_piv);
       if ((e = mark(DD_K_DIAG, false)) != cudaSuccess) return e;
       if ((e = mark(DD_K_TRSM, true)) != cudaSuccess) return e;
       if (p == 0)
-        ddk::launch_trsm(p, h->pool, h->d_fronts, h->d_trsm + R.trsm_off, R.n_trsm, R.k, h->d_status, s, nullptr);
+        ddk::launch_trsm(p, h->pool, h->d_fronts, h->d_trsm + R.trsm_off, R.n_trsm, R.k, h->d_status, s, nullptr,
+                         h->d_piv);
       else
         ddk::launch_trsm_mx(h->pool, h->d_fronts, h->d_trsm + R.trsm_off, R.n_trsm, R.k, h->d_status, h->d_linv, ws,
-                            s);
+                            s, h->d_piv);
       count(DD_K_DIAG, R.n_diag);
       count(DD_K_TRSM, R.n_trsm);
       return mark(DD_K_TRSM, false);
@@ -1011,6 +1020,8 @@ int dd_factor(dd_handle* h) {
   std::memcpy(&maxl, &st.max_abs_l, 8);
   h->stats.growth = std::max(maxd, maxl) / h->max_abs_a;
   h->stats.min_pivot = mind;
+  h->stats.interchanges = (int64_t)st.n_swap;
+  h->stats.pivots_2x2 = (int64_t)st.n_2x2;
   if (st.code == 8) return DD_ERR_TIMEOUT;
   if (st.code != 0) return DD_ERR_SINGULAR_PIVOT;
   h->factored = true;

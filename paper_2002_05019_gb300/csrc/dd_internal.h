@@ -36,7 +36,7 @@ struct FrontDev {
   int32_t child[2];  // node: child fronts (-1 if absent)
   int32_t map_off[2];// node: offsets of the extend-add maps (child update row -> row here)
   int32_t tile_off;  // offset of this front's per-tile ready flags (ld / DD_TILE of them)
-  int32_t pad_;
+  int32_t piv;       // 1: its diagonal tiles use restricted Bunch-Kaufman pivoting
   int64_t ws_off;    // mixed form: byte offset of this front's A operand images in the panel workspace
   int64_t ws_boff;   // mixed form: byte offset of its B operand images
 };
@@ -74,6 +74,8 @@ struct DevStatus {
   unsigned long long max_abs_d;   // bit pattern of a non-negative double: max |d|
   unsigned long long min_abs_d;   // min |d| over real (unpadded) pivots
   unsigned long long max_abs_l;   // max |l * d| entry written by the panel kernels
+  unsigned long long n_swap;      // restricted Bunch-Kaufman: symmetric interchanges
+  unsigned long long n_2x2;       // restricted Bunch-Kaufman: 2 x 2 pivots
 };
 
 namespace ddk {
@@ -86,16 +88,19 @@ void launch_leaf_init(int prec, void* pool, const FrontDev* fronts, const LeafDe
                       const int8_t* b_sign, cudaStream_t s);
 void launch_node_init(int prec, void* pool, const FrontDev* fronts, const int32_t* node_ids, int n,
                       cudaStream_t s);
+// piv (optional): one byte per pivot position of every diagonal tile (index
+// (tile_off + tile) * 64 + c), the permutation of the restricted Bunch-Kaufman
+// pivoting of the fronts with FrontDev::piv set; nullptr: no front pivots
 void launch_diag(int prec, int diag_fp64, void* pool, const FrontDev* fronts, const int32_t* fids, int n,
-                 int k, DevStatus* st, cudaStream_t s);
+                 int k, DevStatus* st, cudaStream_t s, uint8_t* piv = nullptr);
 void launch_trsm(int prec, void* pool, const FrontDev* fronts, const Task* tasks, int n, int k,
-                 DevStatus* st, cudaStream_t s, unsigned char* ws = nullptr);
+                 DevStatus* st, cudaStream_t s, unsigned char* ws = nullptr, const uint8_t* piv = nullptr);
 // mixed form: 64 x 64 diagonal tile with 32 x 32 pivot blocks (FP64 if
 // diag_fp64) and L_kk^{-1} (FP32, 64 x 64 per front id) for the panel product
 void launch_diag_mx(int diag_fp64, void* pool, const FrontDev* fronts, const int32_t* fids, int n, int k,
-                    DevStatus* st, void* linv, cudaStream_t s);
+                    DevStatus* st, void* linv, cudaStream_t s, uint8_t* piv = nullptr);
 void launch_trsm_mx(void* pool, const FrontDev* fronts, const Task* tasks, int n, int k, DevStatus* st,
-                    const void* linv, unsigned char* ws, cudaStream_t s);
+                    const void* linv, unsigned char* ws, cudaStream_t s, const uint8_t* piv = nullptr);
 // tensor-core trailing update (mixed form): task (front, first row tile i0 of a
 // 128-row block, column tile j, store mask in .pad: bit 0 rows of i0, bit 1 rows of i0+1)
 // groups: (first task, count) of each run of tasks sharing one A block; n = number of groups;
@@ -120,10 +125,11 @@ void launch_rhs_extend_add(int prec, void* rpool, const FrontDev* fronts, const 
 // index tile_off + tile; when given, the in-tile triangular solves are products
 void launch_forward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const Task* tasks, int n,
                     int nrhs, int32_t* flags, int epoch, DevStatus* st, cudaStream_t s,
-                    const void* linv = nullptr);
+                    const void* linv = nullptr, const uint8_t* piv = nullptr);
 void launch_backward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const Task* tasks, int n,
                      int nrhs, const int32_t* upd, const int32_t* sep, void* lam_work, int64_t ld_lam,
-                     int32_t* flags, int epoch, DevStatus* st, cudaStream_t s, const void* linv = nullptr);
+                     int32_t* flags, int epoch, DevStatus* st, cudaStream_t s, const void* linv = nullptr,
+                     const uint8_t* piv = nullptr);
 void launch_leaf_out(int prec, const void* rpool, const FrontDev* fronts, const LeafDev* leaves,
                      int n_leaves, const int32_t* perm, double2* u, int64_t ldu, int nrhs, int accumulate,
                      cudaStream_t s);

@@ -11,6 +11,7 @@
 // float2 (mixed form).
 #include "dd_complex.cuh"
 #include "dd_internal.h"
+#include "dd_pivot.cuh"
 
 namespace ddk {
 
@@ -121,54 +122,98 @@ __global__ void k_node_init(S* pool, const FrontDev* fr, const int32_t* ids) {
 // lower triangle), computed in precision C (FP64 for the auxiliary pivot
 // blocks of the mixed form)
 // ---------------------------------------------------------------------------
+// writes the pivot data of a factored tile that pivoted: the 2x2 off-diagonals
+// of D above the diagonal (0 elsewhere on the superdiagonal) and the permutation
+template <typename S, typename C>
+__device__ void store_pivots(S* base, int64_t ld, const int* perm, const C* dsup, uint8_t* piv_tile) {
+  if (threadIdx.x < T - 1) base[(int64_t)threadIdx.x * ld + threadIdx.x + 1] = cconv<S>(dsup[threadIdx.x]);
+  if (threadIdx.x < T) piv_tile[threadIdx.x] = (uint8_t)perm[threadIdx.x];
+}
+
+// pivot statistics of column c of a factored tile: |d| (1x1) or sqrt|det| (2x2)
+template <typename A, typename C>
+__device__ void pivot_stats(const A* a, const C* dsup, bool pv, int c, int f, int row, DevStatus* st) {
+  double m2 = cabs2d(a[tri(c, c)]);
+  if (pv) {
+    const int p0 = (c + 1 < T && (dsup[c].x != 0 || dsup[c].y != 0)) ? c
+                   : (c > 0 && (dsup[c - 1].x != 0 || dsup[c - 1].y != 0)) ? c - 1 : -1;
+    if (p0 >= 0) {
+      const double2 d0 = cconv<double2>(a[tri(p0, p0)]), d1 = cconv<double2>(a[tri(p0 + 1, p0 + 1)]);
+      const double2 b = cconv<double2>(dsup[p0]);
+      m2 = sqrt(cabs2d(csub(cmul(d0, d1), cmul(b, b))));
+    }
+  }
+  if (!(m2 > 0.0) || !isfinite(m2)) status_pivot(st, f, row);
+  const double m = sqrt(m2);
+  if (isfinite(m)) {
+    atomic_max_pos(&st->max_abs_d, m);
+    atomic_min_pos(&st->min_abs_d, m);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// diagonal tile: LDL^T of a 64 x 64 block in shared memory (packed lower
+// triangle), computed in precision C (FP64 for the auxiliary pivot blocks of
+// the mixed form); unpivoted, or with restricted Bunch-Kaufman pivoting for
+// the fronts that pivot
+// ---------------------------------------------------------------------------
 template <typename S, typename C>
 __global__ void __launch_bounds__(256) k_diag(S* pool, const FrontDev* fr, const int32_t* fids, int k,
-                                              DevStatus* st) {
+                                              DevStatus* st, uint8_t* piv) {
   __shared__ C a[T * (T + 1) / 2];
   __shared__ C w[T];        // column j before scaling: w_c = d_j * l_cj
+  __shared__ C w1[T];       // second column of a 2x2 pivot
+  __shared__ C dsup[T];
+  __shared__ int perm[T];
+  __shared__ int cnt[2];
   __shared__ C rinv;        // 1 / d_j
   const int f = fids[blockIdx.x];
   const FrontDev F = fr[f];
+  const bool pv = piv != nullptr && F.piv != 0;
   S* base = pool + F.off + (int64_t)(k * T) * F.ld + k * T;
   for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
     const int i = idx / T, c = idx % T;
     if (c <= i) a[tri(i, c)] = cconv<C>(base[(int64_t)i * F.ld + c]);
   }
+  if (threadIdx.x < 2) cnt[threadIdx.x] = 0;
   __syncthreads();
-  if (threadIdx.x == 0) rinv = cdiv(cmake<C>(1, 0), a[0]);
-  __syncthreads();
-  const int row = threadIdx.x >> 2, sub = threadIdx.x & 3;   // 4 threads per row
-  for (int j = 0; j < T; ++j) {
-    // l_ij = a_ij / d_j, keeping the unscaled value for the update
-    if (sub == 0 && row > j) {
-      const C v = a[tri(row, j)];
-      w[row] = v;
-      a[tri(row, j)] = cmul(v, rinv);
-    }
+  if (pv) {
+    ldlt_bk<C>(a, T, perm, dsup, w, w1, &cnt[0], &cnt[1]);
+  } else {
+    if (threadIdx.x == 0) rinv = cdiv(cmake<C>(1, 0), a[0]);
     __syncthreads();
-    // a_ic -= l_ij * (d_j l_cj) for j < c <= i
-    if (row > j) {
-      const C l = a[tri(row, j)];
-      for (int c = j + 1 + sub; c <= row; c += 4) a[tri(row, c)] = cfms(l, w[c], a[tri(row, c)]);
-      if (row == j + 1 && sub == 0) rinv = cdiv(cmake<C>(1, 0), a[tri(j + 1, j + 1)]);
+    const int row = threadIdx.x >> 2, sub = threadIdx.x & 3;   // 4 threads per row
+    for (int j = 0; j < T; ++j) {
+      // l_ij = a_ij / d_j, keeping the unscaled value for the update
+      if (sub == 0 && row > j) {
+        const C v = a[tri(row, j)];
+        w[row] = v;
+        a[tri(row, j)] = cmul(v, rinv);
+      }
+      __syncthreads();
+      // a_ic -= l_ij * (d_j l_cj) for j < c <= i
+      if (row > j) {
+        const C l = a[tri(row, j)];
+        for (int c = j + 1 + sub; c <= row; c += 4) a[tri(row, c)] = cfms(l, w[c], a[tri(row, c)]);
+        if (row == j + 1 && sub == 0) rinv = cdiv(cmake<C>(1, 0), a[tri(j + 1, j + 1)]);
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
   for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
     const int i = idx / T, c = idx % T;
     if (c <= i) base[(int64_t)i * F.ld + c] = cconv<S>(a[tri(i, c)]);
   }
+  if (pv) {
+    store_pivots<S, C>(base, F.ld, perm, dsup, piv + ((int64_t)F.tile_off + k) * T);
+    if (threadIdx.x == 0 && (cnt[0] | cnt[1])) {
+      atomicAdd(&st->n_swap, (unsigned long long)cnt[0]);
+      atomicAdd(&st->n_2x2, (unsigned long long)cnt[1]);
+    }
+  }
   if (threadIdx.x < T) {
     const int r = k * T + threadIdx.x;
-    if (r < F.ne) {
-      const double m2 = cabs2d(a[tri(threadIdx.x, threadIdx.x)]);
-      if (!(m2 > 0.0) || !isfinite(m2)) status_pivot(st, f, r);
-      const double m = sqrt(m2);
-      if (isfinite(m)) {
-        atomic_max_pos(&st->max_abs_d, m);
-        atomic_min_pos(&st->min_abs_d, m);
-      }
-    }
+    if (r < F.ne) pivot_stats(a, dsup, pv, threadIdx.x, f, r, st);
   }
 }
 
@@ -213,35 +258,82 @@ __device__ void factor_pivot32(float2* a, int jb, C* ap, C* w, C* rinv, int nthr
   __syncthreads();
 }
 
+// the same with restricted Bunch-Kaufman pivoting inside the 32 x 32 block;
+// perm and dsup receive the block-local permutation and 2x2 off-diagonals
+template <typename C>
+__device__ void factor_pivot32_bk(float2* a, int jb, C* ap, C* w, C* w1, int* perm, C* dsup, int* cnt) {
+  for (int idx = threadIdx.x; idx < PB * PB; idx += blockDim.x) {
+    const int i = idx / PB, c = idx % PB;
+    if (c <= i) ap[tri(i, c)] = cconv<C>(a[tri(jb + i, jb + c)]);
+  }
+  __syncthreads();
+  ldlt_bk<C>(ap, PB, perm, dsup, w, w1, &cnt[0], &cnt[1]);
+  for (int idx = threadIdx.x; idx < PB * PB; idx += blockDim.x) {
+    const int i = idx / PB, c = idx % PB;
+    if (c <= i) a[tri(jb + i, jb + c)] = cconv<float2>(ap[tri(i, c)]);
+  }
+  __syncthreads();
+}
+
 template <typename C>
 __global__ void __launch_bounds__(256) k_diag_mx(float2* pool, const FrontDev* fr, const int32_t* fids, int k,
-                                                 DevStatus* st, float2* linv) {
+                                                 DevStatus* st, float2* linv, uint8_t* piv) {
   __shared__ float2 a[T * (T + 1) / 2];
   __shared__ C ap[PB * (PB + 1) / 2];
   __shared__ C w[PB];
   __shared__ C rinv;
-  __shared__ float2 d1inv[PB];
+  __shared__ float2 d1inv[PB];   // D1^{-1}: (D1^{-1} x)_c = d1inv[c] x_c + g1[c] x_{q1[c]}
+  // restricted Bunch-Kaufman (fronts that pivot): 2x2 column, permutation, 2x2 off-diagonals
+  __shared__ C w1[PB];
+  __shared__ float2 g1[PB];
+  __shared__ int q1[PB];
+  __shared__ int perm[T];
+  __shared__ C dsup[T];
+  __shared__ int cnt[2];
   // x21 (unscaled A21 L11^{-T}, 32 x 33) and later L^{-1} (packed lower 64 x 64) share storage
   __shared__ float2 scratch[T * (T + 1) / 2];
   float2 (*x21)[PB + 1] = reinterpret_cast<float2 (*)[PB + 1]>(scratch);
   float2* li = scratch;
   const int f = fids[blockIdx.x];
   const FrontDev F = fr[f];
+  const bool pv = piv != nullptr && F.piv != 0;
   float2* base = pool + F.off + (int64_t)(k * T) * F.ld + k * T;
   for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
     const int i = idx / T, c = idx % T;
     if (c <= i) a[tri(i, c)] = base[(int64_t)i * F.ld + c];
   }
+  if (threadIdx.x < 2) cnt[threadIdx.x] = 0;
   __syncthreads();
-  factor_pivot32<C>(a, 0, ap, w, &rinv, blockDim.x);
+  if (pv) factor_pivot32_bk<C>(a, 0, ap, w, w1, perm, dsup, cnt);
+  else factor_pivot32<C>(a, 0, ap, w, &rinv, blockDim.x);
   // X = A21 L11^{-T}, column by column; then L21 = X D1^{-1}
   {
     const int r = threadIdx.x & (PB - 1), g = threadIdx.x >> 5;   // 8 column groups
     for (int idx = threadIdx.x; idx < PB * PB; idx += blockDim.x) {
       const int rr = idx / PB, c = idx % PB;
-      x21[rr][c] = a[tri(PB + rr, c)];
+      x21[rr][c] = a[tri(PB + rr, pv ? perm[c] : c)];   // A21 P1^T
     }
-    if (threadIdx.x < PB) d1inv[threadIdx.x] = cdiv(make_float2(1.f, 0.f), a[tri(threadIdx.x, threadIdx.x)]);
+    if (threadIdx.x < PB) {
+      const int c = threadIdx.x;
+      const bool first = pv && c + 1 < PB && (dsup[c].x != 0 || dsup[c].y != 0);
+      const bool second = pv && !first && c > 0 && (dsup[c - 1].x != 0 || dsup[c - 1].y != 0);
+      if (!first && !second) {
+        d1inv[c] = pv ? cconv<float2>(cdiv(cmake<C>(1, 0), ap[tri(c, c)]))
+                      : cdiv(make_float2(1.f, 0.f), a[tri(c, c)]);
+        g1[c] = make_float2(0.f, 0.f);
+        q1[c] = c;
+      } else {
+        // block inverse of [d0 b; b d1] from the precision-C factor still in ap
+        const int p0 = first ? c : c - 1;
+        const double2 d0 = cconv<double2>(ap[tri(p0, p0)]), dd = cconv<double2>(ap[tri(p0 + 1, p0 + 1)]);
+        const double2 b = cconv<double2>(dsup[p0]);
+        const double2 idet = cdiv(make_double2(1.0, 0.0), csub(cmul(d0, dd), cmul(b, b)));
+        d1inv[c] = cconv<float2>(cmul(first ? dd : d0, idet));
+        const double2 nb = cmul(b, idet);
+        g1[c] = make_float2((float)-nb.x, (float)-nb.y);
+        q1[c] = first ? c + 1 : c - 1;
+      }
+    }
     __syncthreads();
     for (int j = 0; j < PB - 1; ++j) {
       const float2 xj = x21[r][j];
@@ -250,7 +342,7 @@ __global__ void __launch_bounds__(256) k_diag_mx(float2* pool, const FrontDev* f
     }
     for (int idx = threadIdx.x; idx < PB * PB; idx += blockDim.x) {
       const int rr = idx / PB, c = idx % PB;
-      a[tri(PB + rr, c)] = cmul(x21[rr][c], d1inv[c]);
+      a[tri(PB + rr, c)] = cfma(x21[rr][q1[c]], g1[c], cmul(x21[rr][c], d1inv[c]));
     }
     __syncthreads();
     // A22 -= L21 X^T (lower part)
@@ -264,10 +356,34 @@ __global__ void __launch_bounds__(256) k_diag_mx(float2* pool, const FrontDev* f
     }
     __syncthreads();
   }
-  factor_pivot32<C>(a, PB, ap, w, &rinv, blockDim.x);
+  if (pv) {
+    factor_pivot32_bk<C>(a, PB, ap, w, w1, perm + PB, dsup + PB, cnt);
+    // rows of L21 follow the interchanges of the second pivot block
+    for (int idx = threadIdx.x; idx < PB * PB; idx += blockDim.x) {
+      const int rr = idx / PB, c = idx % PB;
+      x21[rr][c] = a[tri(PB + rr, c)];
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < PB * PB; idx += blockDim.x) {
+      const int rr = idx / PB, c = idx % PB;
+      a[tri(PB + rr, c)] = x21[perm[PB + rr]][c];
+    }
+    __syncthreads();
+    if (threadIdx.x < PB) perm[PB + threadIdx.x] += PB;
+  } else {
+    factor_pivot32<C>(a, PB, ap, w, &rinv, blockDim.x);
+  }
   for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
     const int i = idx / T, c = idx % T;
     if (c <= i) base[(int64_t)i * F.ld + c] = a[tri(i, c)];
+  }
+  if (pv) {
+    __syncthreads();
+    store_pivots<float2, C>(base, F.ld, perm, dsup, piv + ((int64_t)F.tile_off + k) * T);
+    if (threadIdx.x == 0 && (cnt[0] | cnt[1])) {
+      atomicAdd(&st->n_swap, (unsigned long long)cnt[0]);
+      atomicAdd(&st->n_2x2, (unsigned long long)cnt[1]);
+    }
   }
   // L^{-1} of the unit lower tile, column by column: 4 lanes per column share the dot products
   {
@@ -297,34 +413,48 @@ __global__ void __launch_bounds__(256) k_diag_mx(float2* pool, const FrontDev* f
   }
   if (threadIdx.x < T) {
     const int r = k * T + threadIdx.x;
-    if (r < F.ne) {
-      const double m2 = cabs2d(a[tri(threadIdx.x, threadIdx.x)]);
-      if (!(m2 > 0.0) || !isfinite(m2)) status_pivot(st, f, r);
-      const double m = sqrt(m2);
-      if (isfinite(m)) {
-        atomic_max_pos(&st->max_abs_d, m);
-        atomic_min_pos(&st->min_abs_d, m);
-      }
-    }
+    if (r < F.ne) pivot_stats(a, dsup, pv, threadIdx.x, f, r, st);
   }
 }
 
-// mixed form panel: X = A_ik L_kk^{-T} as a product with the stored inverse,
-// L_ik = X D_k^{-1}; 4 x 4 register blocking like the trailing update
+// mixed form panel: X = A_ik P_k^T L_kk^{-T} as a product with the stored
+// inverse, L_ik = X D_k^{-1}; 4 x 4 register blocking like the trailing update
 __global__ void __launch_bounds__(256) k_trsm_mx(float2* pool, const FrontDev* fr, const Task* tasks, int k,
-                                                 DevStatus* st, const float2* linv, unsigned char* ws) {
+                                                 DevStatus* st, const float2* linv, unsigned char* ws,
+                                                 const uint8_t* piv) {
   constexpr int KC = 32;
-  __shared__ float2 As[KC][T + 1];
-  __shared__ float2 Bs[KC][T + 1];
+  // A and B chunks; after the product the same storage holds X (64 x 65) when D has 2x2 blocks
+  __shared__ float2 sraw[2 * KC * (T + 1)];
+  float2 (*As)[T + 1] = reinterpret_cast<float2 (*)[T + 1]>(sraw);
+  float2 (*Bs)[T + 1] = As + KC;
+  float2 (*Xs)[T + 1] = As;
   __shared__ float2 rinv[T];
+  __shared__ float2 g1[T];
+  __shared__ int qc[T];
+  __shared__ int perm[T];
   const Task t = tasks[blockIdx.x];
   const FrontDev F = fr[t.f];
+  const bool pv = piv != nullptr && F.piv != 0;
   const int64_t ld = F.ld;
   float2* Aik = pool + F.off + (int64_t)(t.i * T) * ld + k * T;
+  const float2* Dk = pool + F.off + (int64_t)(k * T) * ld + k * T;
   const float2* Li = linv + ((int64_t)F.tile_off + k) * T * T;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  if (threadIdx.x < T)
-    rinv[threadIdx.x] = cdiv(make_float2(1.f, 0.f), pool[F.off + (int64_t)(k * T + threadIdx.x) * (ld + 1)]);
+  if (threadIdx.x < T) {
+    const int p = threadIdx.x;
+    if (pv) {
+      float2 g0, gg;
+      int q;
+      dinv_col(Dk, ld, p, g0, gg, q);
+      rinv[p] = g0;
+      g1[p] = gg;
+      qc[p] = q;
+      perm[p] = piv[((int64_t)F.tile_off + k) * T + p];
+    } else {
+      rinv[p] = cdiv(make_float2(1.f, 0.f), Dk[(int64_t)p * (ld + 1)]);
+      perm[p] = p;
+    }
+  }
   float2 acc[4][4];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
@@ -334,7 +464,7 @@ __global__ void __launch_bounds__(256) k_trsm_mx(float2* pool, const FrontDev* f
     __syncthreads();
     for (int idx = threadIdx.x; idx < T * KC; idx += blockDim.x) {
       const int r = idx / KC, kk = idx % KC;
-      As[kk][r] = Aik[(int64_t)r * ld + kc + kk];
+      As[kk][r] = Aik[(int64_t)r * ld + perm[kc + kk]];
       Bs[kk][r] = Li[r * T + kc + kk];   // Linv[p][q], p = r
     }
     __syncthreads();
@@ -352,6 +482,13 @@ __global__ void __launch_bounds__(256) k_trsm_mx(float2* pool, const FrontDev* f
     }
   }
   __syncthreads();
+  if (pv) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) Xs[ty + 16 * r][tx + 16 * c] = acc[r][c];
+    __syncthreads();
+  }
   double mx = 0.0;
 #pragma unroll
   for (int r = 0; r < 4; ++r)
@@ -360,7 +497,7 @@ __global__ void __launch_bounds__(256) k_trsm_mx(float2* pool, const FrontDev* f
       const int rr = ty + 16 * r, p = tx + 16 * c;
       const float2 x = acc[r][c];
       mx = fmax(mx, cabs2d(x));
-      const float2 lv = cmul(x, rinv[p]);
+      const float2 lv = pv ? cfma(Xs[rr][qc[p]], g1[p], cmul(x, rinv[p])) : cmul(x, rinv[p]);
       Aik[(int64_t)rr * ld + p] = lv;
       if (ws) write_images<float2>(ws, F, t.i - k - 1, rr * T + p, lv, x);
     }
@@ -374,21 +511,39 @@ __global__ void __launch_bounds__(256) k_trsm_mx(float2* pool, const FrontDev* f
 // ---------------------------------------------------------------------------
 template <typename S>
 __global__ void __launch_bounds__(256) k_trsm(S* pool, const FrontDev* fr, const Task* tasks, int k,
-                                              DevStatus* st, unsigned char* ws) {
+                                              DevStatus* st, unsigned char* ws, const uint8_t* piv) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   S* Lt = reinterpret_cast<S*>(smem_raw);  // Lt[j * T + p] = L_kk[p][j]
   S* X = Lt + T * T;                       // X[p * (T + 1) + r] = row r, column p
-  S* rinv = X + T * (T + 1);               // 1 / d_p
+  S* rinv = X + T * (T + 1);               // 1 / d_p, or the first coefficient of D^{-1} (2x2 blocks)
+  __shared__ S g1[T];                      // D^{-1} with 2x2 blocks: L_p = X_p rinv_p + X_q g1_p
+  __shared__ int qc[T], perm[T];
   const Task t = tasks[blockIdx.x];
   const FrontDev F = fr[t.f];
+  const bool pv = piv != nullptr && F.piv != 0;
   const S* Lkk = pool + F.off + (int64_t)(k * T) * F.ld + k * T;
   S* Aik = pool + F.off + (int64_t)(t.i * T) * F.ld + k * T;
-  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
-    const int p = idx / T, j = idx % T;  // coalesced reads along rows
-    Lt[j * T + p] = (j < p) ? Lkk[(int64_t)p * F.ld + j] : czero<S>();
-    X[j * (T + 1) + p] = Aik[(int64_t)p * F.ld + j];
+  if (threadIdx.x < T) {
+    const int p = threadIdx.x;
+    if (pv) {
+      S g0, gg;
+      int q;
+      dinv_col(Lkk, F.ld, p, g0, gg, q);
+      rinv[p] = g0;
+      g1[p] = gg;
+      qc[p] = q;
+      perm[p] = piv[((int64_t)F.tile_off + k) * T + p];
+    } else {
+      rinv[p] = cdiv(cmake<S>(1, 0), Lkk[(int64_t)p * F.ld + p]);
+      perm[p] = p;
+    }
   }
-  if (threadIdx.x < T) rinv[threadIdx.x] = cdiv(cmake<S>(1, 0), Lkk[(int64_t)threadIdx.x * F.ld + threadIdx.x]);
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+    const int p = idx / T, j = idx % T;  // coalesced reads along rows (A_ik P_k^T: permuted columns)
+    Lt[j * T + p] = (j < p) ? Lkk[(int64_t)p * F.ld + j] : czero<S>();
+    X[j * (T + 1) + p] = Aik[(int64_t)p * F.ld + perm[j]];
+  }
   __syncthreads();
   // X L_kk^T = A_ik, column by column: X[:, p] -= X[:, j] L_kk[p][j] for p > j
   const int r = threadIdx.x & (T - 1), g = threadIdx.x >> 6;  // 4 column groups
@@ -402,7 +557,7 @@ __global__ void __launch_bounds__(256) k_trsm(S* pool, const FrontDev* fr, const
     const int rr = idx / T, p = idx % T;
     const S x = X[p * (T + 1) + rr];
     mx = fmax(mx, cabs2d(x));
-    const S lv = cmul(x, rinv[p]);
+    const S lv = pv ? cfma(X[qc[p] * (T + 1) + rr], g1[p], cmul(x, rinv[p])) : cmul(x, rinv[p]);
     Aik[(int64_t)rr * F.ld + p] = lv;
     if (ws) write_images<S>(ws, F, t.i - k - 1, idx, lv, x);
   }
@@ -526,35 +681,35 @@ void launch_node_init(int prec, void* pool, const FrontDev* fronts, const int32_
 }
 
 void launch_diag(int prec, int diag_fp64, void* pool, const FrontDev* fronts, const int32_t* fids, int n, int k,
-                 DevStatus* st, cudaStream_t s) {
+                 DevStatus* st, cudaStream_t s, uint8_t* piv) {
   if (n <= 0) return;
-  if (prec == 0) k_diag<double2, double2><<<n, 256, 0, s>>>((double2*)pool, fronts, fids, k, st);
-  else if (diag_fp64) k_diag<float2, double2><<<n, 256, 0, s>>>((float2*)pool, fronts, fids, k, st);
-  else k_diag<float2, float2><<<n, 256, 0, s>>>((float2*)pool, fronts, fids, k, st);
+  if (prec == 0) k_diag<double2, double2><<<n, 256, 0, s>>>((double2*)pool, fronts, fids, k, st, piv);
+  else if (diag_fp64) k_diag<float2, double2><<<n, 256, 0, s>>>((float2*)pool, fronts, fids, k, st, piv);
+  else k_diag<float2, float2><<<n, 256, 0, s>>>((float2*)pool, fronts, fids, k, st, piv);
 }
 
 void launch_diag_mx(int diag_fp64, void* pool, const FrontDev* fronts, const int32_t* fids, int n, int k,
-                    DevStatus* st, void* linv, cudaStream_t s) {
+                    DevStatus* st, void* linv, cudaStream_t s, uint8_t* piv) {
   if (n <= 0) return;
-  if (diag_fp64) k_diag_mx<double2><<<n, 256, 0, s>>>((float2*)pool, fronts, fids, k, st, (float2*)linv);
-  else k_diag_mx<float2><<<n, 256, 0, s>>>((float2*)pool, fronts, fids, k, st, (float2*)linv);
+  if (diag_fp64) k_diag_mx<double2><<<n, 256, 0, s>>>((float2*)pool, fronts, fids, k, st, (float2*)linv, piv);
+  else k_diag_mx<float2><<<n, 256, 0, s>>>((float2*)pool, fronts, fids, k, st, (float2*)linv, piv);
 }
 
 void launch_trsm_mx(void* pool, const FrontDev* fronts, const Task* tasks, int n, int k, DevStatus* st,
-                    const void* linv, unsigned char* ws, cudaStream_t s) {
+                    const void* linv, unsigned char* ws, cudaStream_t s, const uint8_t* piv) {
   if (n <= 0) return;
-  k_trsm_mx<<<n, 256, 0, s>>>((float2*)pool, fronts, tasks, k, st, (const float2*)linv, ws);
+  k_trsm_mx<<<n, 256, 0, s>>>((float2*)pool, fronts, tasks, k, st, (const float2*)linv, ws, piv);
 }
 
 void launch_trsm(int prec, void* pool, const FrontDev* fronts, const Task* tasks, int n, int k, DevStatus* st,
-                 cudaStream_t s, unsigned char* ws) {
+                 cudaStream_t s, unsigned char* ws, const uint8_t* piv) {
   if (n <= 0) return;
   if (prec == 0) {
     set_trsm_attr<double2>();
-    k_trsm<double2><<<n, 256, trsm_smem<double2>(), s>>>((double2*)pool, fronts, tasks, k, st, nullptr);
+    k_trsm<double2><<<n, 256, trsm_smem<double2>(), s>>>((double2*)pool, fronts, tasks, k, st, nullptr, piv);
   } else {
     set_trsm_attr<float2>();
-    k_trsm<float2><<<n, 256, trsm_smem<float2>(), s>>>((float2*)pool, fronts, tasks, k, st, ws);
+    k_trsm<float2><<<n, 256, trsm_smem<float2>(), s>>>((float2*)pool, fronts, tasks, k, st, ws, piv);
   }
 }
 

@@ -11,6 +11,7 @@
 // duals, and z <- L^{-T} (z - L_upd^T x_upd) over the eliminated rows.
 #include "dd_complex.cuh"
 #include "dd_internal.h"
+#include "dd_pivot.cuh"
 
 namespace ddk {
 
@@ -123,9 +124,10 @@ __device__ __forceinline__ float2 ldcg<float2>(const float2* p) { return __ldcg(
 template <typename S>
 __global__ void __launch_bounds__(SOLVE_THREADS) k_forward(const S* pool, S* rpool, const FrontDev* fr,
                                                            const Task* tasks, int nrhs, int32_t* flags, int epoch,
-                                                           DevStatus* st, const S* linv) {
+                                                           DevStatus* st, const S* linv, const uint8_t* piv) {
   __shared__ S Lt[T * (T + 1) / 2];
   __shared__ S zi[T];
+  __shared__ int perm[T];
   const Task t = tasks[blockIdx.x];
   const FrontDev F = fr[t.f];
   const S* L = pool + F.off;
@@ -138,6 +140,9 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_forward(const S* pool, S* rpo
   int32_t* flg = flags + F.tile_off;
   constexpr int RW = T / (SOLVE_THREADS / 32);  // rows per warp
   const S* Li = (linv != nullptr && i < nte) ? linv + ((int64_t)F.tile_off + i) * T * T : nullptr;
+  // restricted Bunch-Kaufman: the tile's right-hand side is permuted (P_i) before its solve
+  const bool pv = piv != nullptr && F.piv != 0 && i < nte;
+  if (pv && threadIdx.x < T) perm[threadIdx.x] = piv[((int64_t)F.tile_off + i) * T + threadIdx.x];
   if (i < nte && Li == nullptr) {
     for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
       const int rr = idx / T, c = idx % T;
@@ -165,6 +170,13 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_forward(const S* pool, S* rpo
       if (lane == 0) zi[warp * RW + q] = csub(ldcg(z + (int64_t)(r0 + warp * RW + q) * nrhs + j), v);
     }
     __syncthreads();
+    if (pv) {
+      S v;
+      if (threadIdx.x < T) v = zi[perm[threadIdx.x]];
+      __syncthreads();
+      if (threadIdx.x < T) zi[threadIdx.x] = v;
+      __syncthreads();
+    }
     if (i < nte && Li != nullptr) {
       // z_i = L_ii^{-1} z_i: 4 lanes per row, 16 terms each
       const int row = threadIdx.x >> 2, part = threadIdx.x & 3;
@@ -217,10 +229,13 @@ template <typename S>
 __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rpool, const FrontDev* fr,
                                                             const Task* tasks, int nrhs, const int32_t* upd,
                                                             const int32_t* sep, S* lam, int64_t ld_lam,
-                                                            int32_t* flags, int epoch, DevStatus* st, const S* linv) {
+                                                            int32_t* flags, int epoch, DevStatus* st, const S* linv,
+                                                            const uint8_t* piv) {
   __shared__ S Lt[T * (T + 1) / 2];
   __shared__ S part[SOLVE_THREADS];
   __shared__ S yj[T];
+  __shared__ S g0s[T], g1s[T];   // D_j^{-1} coefficients when the tile pivoted
+  __shared__ int qs[T], perm[T];
   const Task t = tasks[blockIdx.x];
   const FrontDev F = fr[t.f];
   const S* L = pool + F.off;
@@ -241,6 +256,16 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rp
   } else if (threadIdx.x < T) {
     Lt[tri(threadIdx.x, threadIdx.x)] = L[(c0 + threadIdx.x) * (ld + 1)];   // the pivots d
   }
+  const bool pv = piv != nullptr && F.piv != 0;
+  if (pv && threadIdx.x < T) {
+    S g0, g1;
+    int q;
+    dinv_col(L + (int64_t)c0 * ld + c0, ld, threadIdx.x, g0, g1, q);
+    g0s[threadIdx.x] = g0;
+    g1s[threadIdx.x] = g1;
+    qs[threadIdx.x] = q;
+    perm[threadIdx.x] = piv[((int64_t)F.tile_off + j) * T + threadIdx.x];
+  }
   for (int jj = 0; jj < nrhs; ++jj) {
     S acc = czero<S>();
     for (int u = grp; u < F.nu; u += NG)
@@ -259,8 +284,13 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rp
       S sum = part[threadIdx.x];
 #pragma unroll
       for (int g = 1; g < NG; ++g) sum = cadd(sum, part[g * T + threadIdx.x]);
-      const S d = Lt[tri(threadIdx.x, threadIdx.x)];
-      yj[threadIdx.x] = csub(cdiv(ldcg(z + (int64_t)(c0 + threadIdx.x) * nrhs + jj), d), sum);
+      const S zc = ldcg(z + (int64_t)(c0 + threadIdx.x) * nrhs + jj);
+      if (pv) {
+        const S zq = ldcg(z + (int64_t)(c0 + qs[threadIdx.x]) * nrhs + jj);
+        yj[threadIdx.x] = csub(cfma(zq, g1s[threadIdx.x], cmul(zc, g0s[threadIdx.x])), sum);
+      } else {
+        yj[threadIdx.x] = csub(cdiv(zc, Lt[tri(threadIdx.x, threadIdx.x)]), sum);
+      }
     }
     __syncthreads();
     if (Li != nullptr) {
@@ -293,7 +323,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rp
     }
     __syncthreads();
     if (threadIdx.x < T) {
-      const int r = c0 + threadIdx.x;
+      const int r = c0 + (pv ? perm[threadIdx.x] : threadIdx.x);   // x_j = P_j^T (L_jj^{-T} y_j)
       z[(int64_t)r * nrhs + jj] = yj[threadIdx.x];
       if (F.kind == 1 && r < F.ne) lam[sep[F.sep_off + r] + jj * ld_lam] = yj[threadIdx.x];
     }
@@ -338,9 +368,10 @@ __device__ __forceinline__ void mr_fma(const MrSmem& sm, float2 (&acc)[4][4], in
 // forward: Z_i = L_ii^{-1} (B_i - sum_k L_ik Z_k) for eliminated tiles; update tiles only subtract
 __global__ void __launch_bounds__(256) k_forward_mr(const float2* pool, float2* rpool, const FrontDev* fr,
                                                     const Task* tasks, int nrhs, int32_t* flags, int epoch,
-                                                    DevStatus* st, const float2* linv) {
+                                                    DevStatus* st, const float2* linv, const uint8_t* piv) {
   extern __shared__ __align__(16) unsigned char mr_raw[];
   MrSmem& sm = *reinterpret_cast<MrSmem*>(mr_raw);
+  __shared__ int ip[T];   // inverse of the tile's pivot permutation (identity if it did not pivot)
   const Task t = tasks[blockIdx.x];
   const FrontDev F = fr[t.f];
   const float2* L = pool + F.off;
@@ -370,14 +401,20 @@ __global__ void __launch_bounds__(256) k_forward_mr(const float2* pool, float2* 
       __syncthreads();
     }
   }
-  // X = B_i - acc
+  // X = P_i (B_i - acc)
+  if (threadIdx.x < T) {
+    const bool pv = piv != nullptr && F.piv != 0 && i < nte;
+    const int c = threadIdx.x;
+    ip[pv ? piv[((int64_t)F.tile_off + i) * T + c] : c] = c;
+  }
+  __syncthreads();
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const int rr = ty + 16 * r, col = tx + 16 * c;
       const float2 b = col < nrhs ? ldcg(z + (int64_t)(r0 + rr) * nrhs + col) : make_float2(0.f, 0.f);
-      sm.X[rr][col] = csub(b, acc[r][c]);
+      sm.X[ip[rr]][col] = csub(b, acc[r][c]);
     }
   __syncthreads();
   if (i < nte) {
@@ -420,10 +457,13 @@ __global__ void __launch_bounds__(256) k_forward_mr(const float2* pool, float2* 
 __global__ void __launch_bounds__(256) k_backward_mr(const float2* pool, float2* rpool, const FrontDev* fr,
                                                      const Task* tasks, int nrhs, const int32_t* upd,
                                                      const int32_t* sep, float2* lam, int64_t ld_lam, int32_t* flags,
-                                                     int epoch, DevStatus* st, const float2* linv) {
+                                                     int epoch, DevStatus* st, const float2* linv,
+                                                     const uint8_t* piv) {
   extern __shared__ __align__(16) unsigned char mr_raw[];
   MrSmem& sm = *reinterpret_cast<MrSmem*>(mr_raw);
   __shared__ float2 dinv[T];
+  __shared__ float2 g1s[T];   // D_j^{-1} with 2x2 blocks: y_c = dinv_c z_c + g1_c z_q
+  __shared__ int qs[T], perm[T];
   const Task t = tasks[blockIdx.x];
   const FrontDev F = fr[t.f];
   const float2* L = pool + F.off;
@@ -433,7 +473,23 @@ __global__ void __launch_bounds__(256) k_backward_mr(const float2* pool, float2*
   const int j = t.i, c0 = j * T;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   int32_t* flg = flags + F.tile_off;
-  if (threadIdx.x < T) dinv[threadIdx.x] = cdiv(make_float2(1.f, 0.f), L[(c0 + threadIdx.x) * (ld + 1)]);
+  const bool pv = piv != nullptr && F.piv != 0;
+  if (threadIdx.x < T) {
+    if (pv) {
+      float2 g0, g1;
+      int q;
+      dinv_col(L + (int64_t)c0 * ld + c0, ld, threadIdx.x, g0, g1, q);
+      dinv[threadIdx.x] = g0;
+      g1s[threadIdx.x] = g1;
+      qs[threadIdx.x] = q;
+      perm[threadIdx.x] = piv[((int64_t)F.tile_off + j) * T + threadIdx.x];
+    } else {
+      dinv[threadIdx.x] = cdiv(make_float2(1.f, 0.f), L[(c0 + threadIdx.x) * (ld + 1)]);
+      g1s[threadIdx.x] = make_float2(0.f, 0.f);
+      qs[threadIdx.x] = threadIdx.x;
+      perm[threadIdx.x] = threadIdx.x;
+    }
+  }
   float2 acc[4][4];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
@@ -472,8 +528,12 @@ __global__ void __launch_bounds__(256) k_backward_mr(const float2* pool, float2*
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const int cc = ty + 16 * r, col = tx + 16 * c;
-      const float2 zb = col < nrhs ? ldcg(z + (int64_t)(c0 + cc) * nrhs + col) : make_float2(0.f, 0.f);
-      sm.X[cc][col] = csub(cmul(zb, dinv[cc]), acc[r][c]);
+      float2 y = make_float2(0.f, 0.f);
+      if (col < nrhs) {
+        y = cmul(ldcg(z + (int64_t)(c0 + cc) * nrhs + col), dinv[cc]);
+        if (pv) y = cfma(ldcg(z + (int64_t)(c0 + qs[cc]) * nrhs + col), g1s[cc], y);
+      }
+      sm.X[cc][col] = csub(y, acc[r][c]);
     }
   __syncthreads();
   // X_j = Linv^T Y: acc[c][col] = sum_r Linv[r][c] Y[r][col]
@@ -500,8 +560,9 @@ __global__ void __launch_bounds__(256) k_backward_mr(const float2* pool, float2*
   for (int idx = threadIdx.x; idx < T * nrhs; idx += blockDim.x) {
     const int cc = idx / nrhs, col = idx % nrhs;
     const float2 v = sm.X[cc][col];
-    z[(int64_t)(c0 + cc) * nrhs + col] = v;
-    if (F.kind == 1 && c0 + cc < F.ne) lam[sep[F.sep_off + c0 + cc] + col * ld_lam] = v;
+    const int r = c0 + perm[cc];   // X_j = P_j^T (L_jj^{-T} Y)
+    z[(int64_t)r * nrhs + col] = v;
+    if (F.kind == 1 && r < F.ne) lam[sep[F.sep_off + r] + col * ld_lam] = v;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -634,7 +695,8 @@ void launch_rhs_extend_add(int prec, void* rpool, const FrontDev* fronts, const 
 }
 
 void launch_forward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const Task* tasks, int n,
-                    int nrhs, int32_t* flags, int epoch, DevStatus* st, cudaStream_t s, const void* linv) {
+                    int nrhs, int32_t* flags, int epoch, DevStatus* st, cudaStream_t s, const void* linv,
+                    const uint8_t* piv) {
   if (n <= 0) return;
   if (prec == 1 && linv != nullptr && nrhs >= 4 && nrhs <= T) {
     static bool attr = false;
@@ -643,20 +705,21 @@ void launch_forward(int prec, const void* pool, void* rpool, const FrontDev* fro
       attr = true;
     }
     k_forward_mr<<<n, 256, sizeof(MrSmem), s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs, flags, epoch, st,
-                                   (const float2*)linv);
+                                   (const float2*)linv, piv);
     return;
   }
   if (prec == 0)
     k_forward<double2><<<n, SOLVE_THREADS, 0, s>>>((const double2*)pool, (double2*)rpool, fronts, tasks, nrhs, flags,
-                                                   epoch, st, nullptr);
+                                                   epoch, st, nullptr, piv);
   else
     k_forward<float2><<<n, SOLVE_THREADS, 0, s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs, flags,
-                                                  epoch, st, (const float2*)linv);
+                                                  epoch, st, (const float2*)linv, piv);
 }
 
 void launch_backward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const Task* tasks, int n,
                      int nrhs, const int32_t* upd, const int32_t* sep, void* lam_work, int64_t ld_lam,
-                     int32_t* flags, int epoch, DevStatus* st, cudaStream_t s, const void* linv) {
+                     int32_t* flags, int epoch, DevStatus* st, cudaStream_t s, const void* linv,
+                     const uint8_t* piv) {
   if (n <= 0) return;
   if (prec == 1 && linv != nullptr && nrhs >= 4 && nrhs <= T) {
     static bool attr = false;
@@ -665,15 +728,16 @@ void launch_backward(int prec, const void* pool, void* rpool, const FrontDev* fr
       attr = true;
     }
     k_backward_mr<<<n, 256, sizeof(MrSmem), s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs, upd, sep,
-                                    (float2*)lam_work, ld_lam, flags, epoch, st, (const float2*)linv);
+                                    (float2*)lam_work, ld_lam, flags, epoch, st, (const float2*)linv, piv);
     return;
   }
   if (prec == 0)
     k_backward<double2><<<n, SOLVE_THREADS, 0, s>>>((const double2*)pool, (double2*)rpool, fronts, tasks, nrhs, upd,
-                                                    sep, (double2*)lam_work, ld_lam, flags, epoch, st, nullptr);
+                                                    sep, (double2*)lam_work, ld_lam, flags, epoch, st, nullptr, piv);
   else
     k_backward<float2><<<n, SOLVE_THREADS, 0, s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs, upd, sep,
-                                                   (float2*)lam_work, ld_lam, flags, epoch, st, (const float2*)linv);
+                                                   (float2*)lam_work, ld_lam, flags, epoch, st, (const float2*)linv,
+                                                   piv);
 }
 
 void launch_leaf_out(int prec, const void* rpool, const FrontDev* fronts, const LeafDev* leaves, int n_leaves,

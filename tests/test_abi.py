@@ -83,6 +83,7 @@ def test_setup_host_analysis_succeeds_without_device():
     assert _setup_code(_subs(p), p.n_dual, tree_parent=p.rcb.parent) == 9      # NO_DEVICE: analysis passed
     assert _setup_code(_subs(p), p.n_dual, centroids=p.centroids()) == 9
     assert _setup_code(_subs(p), p.n_dual) == 9
+    assert _setup_code(_subs(p), p.n_dual, pivoting=2) == 9                      # every pivoting mode accepted
 
 
 def test_setup_rejects_bad_inputs():
@@ -119,3 +120,5 @@ def test_setup_rejects_bad_inputs():
     assert _setup_code(good, p.n_dual, tree_parent=np.array([2, 0, -1])) == 1
     # unsupported options
     assert _setup_code(good, p.n_dual, precision="fp64", refine_tol=-1.0) == 1
+    assert _setup_code(good, p.n_dual, pivoting=3) == 1
+    assert _setup_code(good, p.n_dual, pivoting=-1) == 1

@@ -191,3 +191,36 @@ def test_planted_mistakes_are_caught(monkeypatch, mistake):
     u, lam = o.solve([s.f for s in p.subs])
     x3, _ = o.gather(u)
     assert np.linalg.norm(x3 - x1) > 1e-6 * np.linalg.norm(x1)
+
+
+# ---------------------------------------------------------------------------
+# the undecomposed arrowhead route (inputs that need pivoting have no
+# unpivoted DD route): pinned against the decomposition route and against the
+# global LU on FEM problems, and by its residual on an indefinite input
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,levels", [(2, 1), (3, 2)])
+def test_arrow_solve_equals_dd_route(n, levels):
+    p = femgen.tiny(n, levels)
+    o = oracle.DDOracle(p)
+    uo, lo = o.solve([s.f for s in p.subs])
+    f = np.concatenate([s.f for s in p.subs], axis=0)
+    u, lam = oracle.arrow_solve(p.subs, p.n_dual, f)
+    assert np.linalg.norm(u - np.concatenate(uo)) <= 1e-12 * np.linalg.norm(u)
+    assert np.linalg.norm(lam - lo) <= 1e-11 * np.linalg.norm(lam)
+    x1 = oracle.lu_solve(p.A_csr().toarray(), p.b)
+    x3, _ = o.gather(np.split(u, np.cumsum([s.n for s in p.subs])[:-1]))
+    assert np.linalg.norm(x3 - x1) <= 1e-12 * np.linalg.norm(x1)
+
+
+def test_arrow_solve_on_indefinite_chain():
+    from femgen.indefinite import indefinite_chain
+    p = indefinite_chain(n_sub=3, m=40, n_if=4, eps=0.0, nrhs=2, seed=5)
+    f = np.concatenate([s.f for s in p.subs], axis=0)
+    u, lam = oracle.arrow_solve(p.subs, p.n_dual, f)
+    offs = np.cumsum([0] + [s.n for s in p.subs])
+    rp, ru = oracle.arrow_residual(p, [u[offs[k]:offs[k + 1]] for k in range(p.n_sub)], lam)
+    assert max(np.abs(r).max() for r in rp) <= 1e-12 * np.abs(f).max()
+    assert np.abs(ru).max() <= 1e-12 * np.abs(u).max()
+    # exactly zero diagonal: the unpivoted LDL^T of a domain breaks down at once
+    with pytest.raises(np.linalg.LinAlgError):
+        oracle.ldlt(odd._csr_dense(p.subs[0]))
