@@ -582,7 +582,25 @@ __global__ void __launch_bounds__(256) k_update(S* pool, const FrontDev* fr, con
   const S* Lj = pool + F.off + (int64_t)(t.j * T) * ld + k * T;
   S* Cij = pool + F.off + (int64_t)(t.i * T) * ld + t.j * T;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  if (threadIdx.x < T) dk[threadIdx.x] = pool[F.off + (int64_t)(k * T + threadIdx.x) * (ld + 1)];
+  // W_jk = L_jk D_k: D_k diagonal, or with 2x2 blocks (c, q) when the front pivots,
+  // whose off-diagonal entry sits above the diagonal of the factored tile
+  __shared__ S db[T];
+  __shared__ int dq[T];
+  if (threadIdx.x < T) {
+    const int c = threadIdx.x;
+    const S* Dk = pool + F.off + (int64_t)(k * T) * ld + k * T;
+    dk[c] = Dk[(int64_t)c * (ld + 1)];
+    int q = c;
+    S b = czero<S>();
+    if (F.piv) {
+      const S up = c + 1 < T ? Dk[(int64_t)c * ld + c + 1] : czero<S>();
+      const S lo = c > 0 ? Dk[(int64_t)(c - 1) * ld + c] : czero<S>();
+      if (up.x != 0 || up.y != 0) { q = c + 1; b = up; }
+      else if (lo.x != 0 || lo.y != 0) { q = c - 1; b = lo; }
+    }
+    dq[c] = q;
+    db[c] = b;
+  }
   S acc[4][4];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
@@ -593,7 +611,8 @@ __global__ void __launch_bounds__(256) k_update(S* pool, const FrontDev* fr, con
     for (int idx = threadIdx.x; idx < T * KC; idx += blockDim.x) {
       const int r = idx / KC, kk = idx % KC;
       As[kk][r] = Li[(int64_t)r * ld + kc + kk];
-      Bs[kk][r] = cmul(Lj[(int64_t)r * ld + kc + kk], dk[kc + kk]);
+      const S w = cmul(Lj[(int64_t)r * ld + kc + kk], dk[kc + kk]);
+      Bs[kk][r] = F.piv ? cfma(Lj[(int64_t)r * ld + dq[kc + kk]], db[kc + kk], w) : w;
     }
     __syncthreads();
 #pragma unroll 4
