@@ -58,7 +58,7 @@ def indefinite_chain(n_sub: int = 4, m: int = 96, n_if: int = 8, eps: float = 0.
         A[0::2, 1::2] = C
         A[1::2, 0::2] = C.T
         A[np.diag_indices(m)] = eps
-        rows, cols = np.nonzero(A != 0) if eps == 0 else np.nonzero(np.ones((m, m), dtype=bool))
+        rows, cols = np.nonzero(np.ones((m, m), dtype=bool))   # dense pattern, zero diagonal stored
         indptr = np.searchsorted(rows, np.arange(m + 1)).astype(np.int32)
         f = rng.normal(size=(m, nrhs)) + 1j * rng.normal(size=(m, nrhs))
         bd, bl, bs = [], [], []
