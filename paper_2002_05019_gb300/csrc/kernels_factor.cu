@@ -220,38 +220,68 @@ __global__ void __launch_bounds__(256) k_diag(S* pool, const FrontDev* fr, const
 // ---------------------------------------------------------------------------
 // mixed form diagonal tile: the 64 x 64 tile is factored as 2 x 2 blocks of
 // 32; the two 32 x 32 pivot blocks in precision C (FP64 for the auxiliary
-// matrix, FP32 for the domains), the off-diagonal block solve and the Schur
-// update of the second pivot block in FP32.  Also writes L_kk^{-1} (FP32) for
-// the panel kernel, which then is a product instead of a substitution.
+// matrix, FP32 for the domains), everything else in FP32 as products with the
+// inverses of the unit-lower pivot blocks:
+//   L11 D1 L11^T = A11            (pivot block 1, precision C)
+//   N11 = L11^{-1}
+//   X21 = A21 N11^T,  L21 = X21 D1^{-1},  A22 -= L21 X21^T
+//   L22 D2 L22^T = A22            (pivot block 2, precision C)
+//   N22 = L22^{-1},   N21 = -N22 (L21 N11)
+// N = [N11 0; N21 N22] = L_kk^{-1} is stored (FP32) for the panel kernel and
+// the substitutions.  GB300's FP64 rate is about 1/64 of its FP32 rate, so
+// the FP64 work is kept to the two pivot blocks and spread evenly over all
+// threads.
 // ---------------------------------------------------------------------------
 constexpr int PB = 32;
 
+// 1 / d: one real division (the pivot magnitudes of these matrices are far
+// from the limits of the exponent range, so |d|^2 cannot overflow in FP64)
+__device__ __forceinline__ double2 crcp(double2 d) {
+  const double s = 1.0 / (d.x * d.x + d.y * d.y);
+  return make_double2(d.x * s, -d.y * s);
+}
+__device__ __forceinline__ float2 crcp(float2 d) { return cdiv(make_float2(1.f, 0.f), d); }
+
+// element e of a column-descending enumeration of the update set of a 32 x 32
+// block: columns c = 31, 30, ..., 1, rows r = c..31 within each, so the
+// elements with c > j are exactly e < (31 - j)(32 - j) / 2
+__device__ __forceinline__ uint16_t pb_elem(int e) {
+  int k = 0;
+  while ((k + 1) * (k + 2) / 2 <= e) ++k;
+  const int c = PB - 1 - k, r = c + (e - k * (k + 1) / 2);
+  return (uint16_t)((r << 8) | c);
+}
+
+// Unpivoted LDL^T of pivot block jb of the tile in precision C.  Per column j:
+// the rows below scale their entry (one barrier), then every thread updates
+// its elements of the trailing triangle, the owner of (j+1, j+1) also forming
+// the next reciprocal pivot (one barrier).
 template <typename C>
-__device__ void factor_pivot32(float2* a, int jb, C* ap, C* w, C* rinv, int nthreads) {
-  // ap: packed lower 32 x 32 in precision C; a: packed lower 64 x 64 tile (FP32)
-  for (int idx = threadIdx.x; idx < PB * PB; idx += nthreads) {
+__device__ void factor_pivot32(float2* a, int jb, C* ap, C* w, C* rinv, const uint16_t* etab) {
+  for (int idx = threadIdx.x; idx < PB * PB; idx += blockDim.x) {
     const int i = idx / PB, c = idx % PB;
     if (c <= i) ap[tri(i, c)] = cconv<C>(a[tri(jb + i, jb + c)]);
   }
   __syncthreads();
-  if (threadIdx.x == 0) *rinv = cdiv(cmake<C>(1, 0), ap[0]);
+  if (threadIdx.x == 0) *rinv = crcp(ap[0]);
   __syncthreads();
-  const int row = threadIdx.x >> 3, sub = threadIdx.x & 7;   // 8 threads per row
-  for (int j = 0; j < PB; ++j) {
-    if (sub == 0 && row > j && row < PB) {
-      const C v = ap[tri(row, j)];
-      w[row] = v;
-      ap[tri(row, j)] = cmul(v, *rinv);
+  for (int j = 0; j < PB - 1; ++j) {
+    if (threadIdx.x > j && threadIdx.x < PB) {
+      const C v = ap[tri(threadIdx.x, j)];
+      w[threadIdx.x] = v;
+      ap[tri(threadIdx.x, j)] = cmul(v, *rinv);
     }
     __syncthreads();
-    if (row > j && row < PB) {
-      const C l = ap[tri(row, j)];
-      for (int c = j + 1 + sub; c <= row; c += 8) ap[tri(row, c)] = cfms(l, w[c], ap[tri(row, c)]);
-      if (row == j + 1 && sub == 0) *rinv = cdiv(cmake<C>(1, 0), ap[tri(j + 1, j + 1)]);
+    const int nj = (PB - 1 - j) * (PB - j) / 2;
+    for (int e = threadIdx.x; e < nj; e += blockDim.x) {
+      const int r = etab[e] >> 8, c = etab[e] & 255;
+      const C v = cfms(ap[tri(r, j)], w[c], ap[tri(r, c)]);
+      ap[tri(r, c)] = v;
+      if (c == j + 1 && r == j + 1) *rinv = crcp(v);
     }
     __syncthreads();
   }
-  for (int idx = threadIdx.x; idx < PB * PB; idx += nthreads) {
+  for (int idx = threadIdx.x; idx < PB * PB; idx += blockDim.x) {
     const int i = idx / PB, c = idx % PB;
     if (c <= i) a[tri(jb + i, jb + c)] = cconv<float2>(ap[tri(i, c)]);
   }
@@ -275,13 +305,41 @@ __device__ void factor_pivot32_bk(float2* a, int jb, C* ap, C* w, C* w1, int* pe
   __syncthreads();
 }
 
+// N = L^{-1} of the unit-lower 32 x 32 block jb of the tile, into the same
+// positions of the packed 64 x 64 li: 8 lanes per column, rows in order
+__device__ void inv_unit_lower32(const float2* a, int jb, float2* li) {
+  const int col = threadIdx.x >> 3, part = threadIdx.x & 7;
+  if (part == 0) li[tri(jb + col, jb + col)] = make_float2(1.f, 0.f);
+  __syncwarp();
+  const int col0 = (threadIdx.x >> 5) * 4;   // first column of this warp: the loop bound is warp-uniform
+  for (int i = col0 + 1; i < PB; ++i) {
+    float2 acc = make_float2(0.f, 0.f);
+    if (i > col)
+      for (int q = col + part; q < i; q += 8) acc = cfma(a[tri(jb + i, jb + q)], li[tri(jb + q, jb + col)], acc);
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+    }
+    if (part == 0 && i > col) li[tri(jb + i, jb + col)] = make_float2(-acc.x, -acc.y);
+    __syncwarp();
+  }
+}
+
 template <typename C>
-__global__ void __launch_bounds__(256) k_diag_mx(float2* pool, const FrontDev* fr, const int32_t* fids, int k,
+__global__ void __launch_bounds__(256, 1) k_diag_mx(float2* pool, const FrontDev* fr, const int32_t* fids, int k,
                                                  DevStatus* st, float2* linv, uint8_t* piv) {
   __shared__ float2 a[T * (T + 1) / 2];
-  __shared__ C ap[PB * (PB + 1) / 2];
+  __shared__ float2 li[T * (T + 1) / 2];   // L_kk^{-1}, packed lower
+  // the precision-C pivot block, and between the two block factorizations the
+  // 32 x 33 FP32 work block X21 (later L21 N11): the same bytes
+  constexpr int kApBytes = sizeof(C) * (PB * (PB + 1) / 2), kX21Bytes = sizeof(float2) * PB * (PB + 1);
+  __shared__ __align__(16) unsigned char ap_raw[kApBytes > kX21Bytes ? kApBytes : kX21Bytes];
+  C* ap = reinterpret_cast<C*>(ap_raw);
+  float2 (*x21)[PB + 1] = reinterpret_cast<float2 (*)[PB + 1]>(ap_raw);
   __shared__ C w[PB];
   __shared__ C rinv;
+  __shared__ uint16_t etab[PB * (PB + 1) / 2];
   __shared__ float2 d1inv[PB];   // D1^{-1}: (D1^{-1} x)_c = d1inv[c] x_c + g1[c] x_{q1[c]}
   // restricted Bunch-Kaufman (fronts that pivot): 2x2 column, permutation, 2x2 off-diagonals
   __shared__ C w1[PB];
@@ -290,10 +348,6 @@ __global__ void __launch_bounds__(256) k_diag_mx(float2* pool, const FrontDev* f
   __shared__ int perm[T];
   __shared__ C dsup[T];
   __shared__ int cnt[2];
-  // x21 (unscaled A21 L11^{-T}, 32 x 33) and later L^{-1} (packed lower 64 x 64) share storage
-  __shared__ float2 scratch[T * (T + 1) / 2];
-  float2 (*x21)[PB + 1] = reinterpret_cast<float2 (*)[PB + 1]>(scratch);
-  float2* li = scratch;
   const int f = fids[blockIdx.x];
   const FrontDev F = fr[f];
   const bool pv = piv != nullptr && F.piv != 0;
@@ -302,60 +356,61 @@ __global__ void __launch_bounds__(256) k_diag_mx(float2* pool, const FrontDev* f
     const int i = idx / T, c = idx % T;
     if (c <= i) a[tri(i, c)] = base[(int64_t)i * F.ld + c];
   }
+  for (int e = threadIdx.x; e < PB * (PB - 1) / 2; e += blockDim.x) etab[e] = pb_elem(e);
   if (threadIdx.x < 2) cnt[threadIdx.x] = 0;
   __syncthreads();
   if (pv) factor_pivot32_bk<C>(a, 0, ap, w, w1, perm, dsup, cnt);
-  else factor_pivot32<C>(a, 0, ap, w, &rinv, blockDim.x);
-  // X = A21 L11^{-T}, column by column; then L21 = X D1^{-1}
-  {
-    const int r = threadIdx.x & (PB - 1), g = threadIdx.x >> 5;   // 8 column groups
-    for (int idx = threadIdx.x; idx < PB * PB; idx += blockDim.x) {
-      const int rr = idx / PB, c = idx % PB;
-      x21[rr][c] = a[tri(PB + rr, pv ? perm[c] : c)];   // A21 P1^T
+  else factor_pivot32<C>(a, 0, ap, w, &rinv, etab);
+  // D1^{-1} (from the precision-C factor while ap still holds it) and N11
+  if (threadIdx.x < PB) {
+    const int c = threadIdx.x;
+    const bool first = pv && c + 1 < PB && (dsup[c].x != 0 || dsup[c].y != 0);
+    const bool second = pv && !first && c > 0 && (dsup[c - 1].x != 0 || dsup[c - 1].y != 0);
+    if (!first && !second) {
+      d1inv[c] = cconv<float2>(crcp(ap[tri(c, c)]));
+      g1[c] = make_float2(0.f, 0.f);
+      q1[c] = c;
+    } else {
+      // block inverse of [d0 b; b d1]
+      const int p0 = first ? c : c - 1;
+      const double2 d0 = cconv<double2>(ap[tri(p0, p0)]), dd = cconv<double2>(ap[tri(p0 + 1, p0 + 1)]);
+      const double2 b = cconv<double2>(dsup[p0]);
+      const double2 idet = cdiv(make_double2(1.0, 0.0), csub(cmul(d0, dd), cmul(b, b)));
+      d1inv[c] = cconv<float2>(cmul(first ? dd : d0, idet));
+      const double2 nb = cmul(b, idet);
+      g1[c] = make_float2((float)-nb.x, (float)-nb.y);
+      q1[c] = first ? c + 1 : c - 1;
     }
-    if (threadIdx.x < PB) {
-      const int c = threadIdx.x;
-      const bool first = pv && c + 1 < PB && (dsup[c].x != 0 || dsup[c].y != 0);
-      const bool second = pv && !first && c > 0 && (dsup[c - 1].x != 0 || dsup[c - 1].y != 0);
-      if (!first && !second) {
-        d1inv[c] = pv ? cconv<float2>(cdiv(cmake<C>(1, 0), ap[tri(c, c)]))
-                      : cdiv(make_float2(1.f, 0.f), a[tri(c, c)]);
-        g1[c] = make_float2(0.f, 0.f);
-        q1[c] = c;
-      } else {
-        // block inverse of [d0 b; b d1] from the precision-C factor still in ap
-        const int p0 = first ? c : c - 1;
-        const double2 d0 = cconv<double2>(ap[tri(p0, p0)]), dd = cconv<double2>(ap[tri(p0 + 1, p0 + 1)]);
-        const double2 b = cconv<double2>(dsup[p0]);
-        const double2 idet = cdiv(make_double2(1.0, 0.0), csub(cmul(d0, dd), cmul(b, b)));
-        d1inv[c] = cconv<float2>(cmul(first ? dd : d0, idet));
-        const double2 nb = cmul(b, idet);
-        g1[c] = make_float2((float)-nb.x, (float)-nb.y);
-        q1[c] = first ? c + 1 : c - 1;
-      }
-    }
-    __syncthreads();
-    for (int j = 0; j < PB - 1; ++j) {
-      const float2 xj = x21[r][j];
-      for (int p = j + 1 + ((g - j - 1) & 7); p < PB; p += 8) x21[r][p] = cfms(xj, a[tri(p, j)], x21[r][p]);
-      __syncthreads();
-    }
-    for (int idx = threadIdx.x; idx < PB * PB; idx += blockDim.x) {
-      const int rr = idx / PB, c = idx % PB;
-      a[tri(PB + rr, c)] = cfma(x21[rr][q1[c]], g1[c], cmul(x21[rr][c], d1inv[c]));
-    }
-    __syncthreads();
-    // A22 -= L21 X^T (lower part)
-    for (int idx = threadIdx.x; idx < PB * PB; idx += blockDim.x) {
-      const int i = idx / PB, c = idx % PB;
-      if (c <= i) {
-        float2 acc = a[tri(PB + i, PB + c)];
-        for (int q = 0; q < PB; ++q) acc = cfms(a[tri(PB + i, q)], x21[c][q], acc);
-        a[tri(PB + i, PB + c)] = acc;
-      }
-    }
-    __syncthreads();
   }
+  inv_unit_lower32(a, 0, li);
+  __syncthreads();   // ap (the precision-C block) is dead from here until pivot block 2
+  {
+    // X21 = A21 P1^T N11^T: x21[r][c] = sum_{q <= c} A21[r][perm q] N11[c][q]
+    const int r = threadIdx.x >> 3, cg = threadIdx.x & 7;
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const int c = cg + 8 * h;
+      float2 acc = make_float2(0.f, 0.f);
+      for (int q = 0; q <= c; ++q) acc = cfma(a[tri(PB + r, pv ? perm[q] : q)], li[tri(c, q)], acc);
+      x21[r][c] = acc;
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < PB * PB; idx += blockDim.x) {
+    const int rr = idx / PB, c = idx % PB;
+    a[tri(PB + rr, c)] = cfma(x21[rr][q1[c]], g1[c], cmul(x21[rr][c], d1inv[c]));   // L21 = X21 D1^{-1}
+  }
+  __syncthreads();
+  // A22 -= L21 X21^T (lower part)
+  for (int idx = threadIdx.x; idx < PB * PB; idx += blockDim.x) {
+    const int i = idx / PB, c = idx % PB;
+    if (c <= i) {
+      float2 acc = a[tri(PB + i, PB + c)];
+      for (int q = 0; q < PB; ++q) acc = cfms(a[tri(PB + i, q)], x21[c][q], acc);
+      a[tri(PB + i, PB + c)] = acc;
+    }
+  }
+  __syncthreads();
   if (pv) {
     factor_pivot32_bk<C>(a, PB, ap, w, w1, perm + PB, dsup + PB, cnt);
     // rows of L21 follow the interchanges of the second pivot block
@@ -371,7 +426,30 @@ __global__ void __launch_bounds__(256) k_diag_mx(float2* pool, const FrontDev* f
     __syncthreads();
     if (threadIdx.x < PB) perm[PB + threadIdx.x] += PB;
   } else {
-    factor_pivot32<C>(a, PB, ap, w, &rinv, blockDim.x);
+    factor_pivot32<C>(a, PB, ap, w, &rinv, etab);
+  }
+  // N22, then N21 = -N22 (L21 N11) through x21 = L21 N11
+  inv_unit_lower32(a, PB, li);
+  {
+    const int r = threadIdx.x >> 3, cg = threadIdx.x & 7;
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const int c = cg + 8 * h;
+      float2 acc = make_float2(0.f, 0.f);
+      for (int q = c; q < PB; ++q) acc = cfma(a[tri(PB + r, q)], li[tri(q, c)], acc);
+      x21[r][c] = acc;
+    }
+  }
+  __syncthreads();
+  {
+    const int r = threadIdx.x >> 3, cg = threadIdx.x & 7;
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const int c = cg + 8 * h;
+      float2 acc = make_float2(0.f, 0.f);
+      for (int q = 0; q <= r; ++q) acc = cfma(li[tri(PB + r, PB + q)], x21[q][c], acc);
+      li[tri(PB + r, c)] = make_float2(-acc.x, -acc.y);
+    }
   }
   for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
     const int i = idx / T, c = idx % T;
@@ -385,31 +463,11 @@ __global__ void __launch_bounds__(256) k_diag_mx(float2* pool, const FrontDev* f
       atomicAdd(&st->n_2x2, (unsigned long long)cnt[1]);
     }
   }
-  // L^{-1} of the unit lower tile, column by column: 4 lanes per column share the dot products
-  {
-    const int col = threadIdx.x >> 2, part = threadIdx.x & 3;
-    __syncthreads();   // x21 is dead from here on
-    if (part == 0) li[tri(col, col)] = make_float2(1.f, 0.f);
-    __syncwarp();
-    // the loop bound is uniform over the warp (its 8 columns start at col0)
-    const int col0 = (threadIdx.x >> 5) * 8;
-    for (int i = col0 + 1; i < T; ++i) {
-      float2 acc = make_float2(0.f, 0.f);
-      if (i > col)
-        for (int q = col + part; q < i; q += 4) acc = cfma(a[tri(i, q)], li[tri(q, col)], acc);
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
-      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
-      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
-      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
-      if (part == 0 && i > col) li[tri(i, col)] = make_float2(-acc.x, -acc.y);
-      __syncwarp();
-    }
-    __syncthreads();
-    float2* out = linv + ((int64_t)F.tile_off + k) * T * T;
-    for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
-      const int i = idx / T, c = idx % T;
-      out[idx] = c <= i ? li[tri(i, c)] : make_float2(0.f, 0.f);
-    }
+  __syncthreads();
+  float2* out = linv + ((int64_t)F.tile_off + k) * T * T;
+  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+    const int i = idx / T, c = idx % T;
+    out[idx] = c <= i ? li[tri(i, c)] : make_float2(0.f, 0.f);
   }
   if (threadIdx.x < T) {
     const int r = k * T + threadIdx.x;
