@@ -42,10 +42,23 @@ struct StepRange {
   int n_grp_next, n_grp_rest;
 };
 
+// mixed form, tensor cores: the trailing update of panels k and k + 1 in one
+// pass (K = 128) over the columns j >= k + 2; "near" tasks are the columns
+// k + 2 and k + 3 (the next pair's panels), "far" tasks the rest
+struct PairRange {
+  int k;
+  int64_t tc2_off;
+  int n_near, n_far;
+  int64_t grp_off;
+  int n_grp_near, n_grp_far;
+};
+
 struct Level {
   std::vector<int32_t> ids;       // fronts in this level
   int64_t ids_off = 0;            // offset into d_level_ids
   std::vector<StepRange> steps;   // factor schedule
+  std::vector<PairRange> pairs;   // two-panel updates of steps (0, 1), (2, 3), ... (tensor-core path)
+  bool ahead = false;             // one-step look-ahead on a second stream
   int max_child_nu = 0;
   int64_t fwd_off = 0, bwd_off = 0;   // solve tasks (forward by row tile, backward by column tile)
   int n_fwd = 0, n_bwd = 0;
@@ -129,10 +142,12 @@ struct dd_handle {
   Task *d_trsm = nullptr, *d_updt = nullptr;
   Task *d_fwd = nullptr, *d_bwd = nullptr;
   Task* d_tc = nullptr;            // tensor-core update tasks (mixed form)
+  Task* d_tc2 = nullptr;           // two-panel tensor-core update tasks
   int2* d_grp = nullptr;           // their groups (first task, count) sharing one A block
   int* d_counters = nullptr;       // one group counter per tensor-core update launch of a factor
   int n_counters = 0;
-  unsigned char* d_ws = nullptr;   // panel operand images (mixed form)
+  unsigned char* d_ws = nullptr;   // panel operand images (mixed form), four slots
+  size_t ws_slot_off[4] = {0, 0, 0, 0};
   float2* d_linv = nullptr;        // mixed form: L_kk^{-1} of every diagonal tile (index tile_off + k)
   uint8_t* d_piv = nullptr;        // restricted Bunch-Kaufman: permutation of every diagonal tile (64 bytes each)
   int pivoting = 0;
@@ -659,7 +674,10 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
     if (h->fronts[x].ld > 0 || x < n_sub) h->levels[height[x]].ids.push_back(x);
   // mixed form: panel image workspace, reused level after level
   if (h->use_tc) {
-    size_t need = 0;
+    // slots 0 and 1 hold the images of even / odd panels of every level; the
+    // look-ahead levels also use slots 2 and 3 (panels k + 2, k + 3 are formed
+    // while the two-panel update of k, k + 1 still reads 0 and 1)
+    size_t need = 0, need_ahead = 0;
     for (auto& L : h->levels) {
       int64_t w = 0;
       for (int f : L.ids) {
@@ -670,21 +688,26 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
         F.ws_boff = w;
         w += ntr * (int64_t)DD_TC_BTILE;
       }
+      L.ahead = L.ids.size() <= 32;
       need = std::max(need, (size_t)w);
+      if (L.ahead) need_ahead = std::max(need_ahead, (size_t)w);
     }
-    h->ws_bytes = need;
+    h->ws_bytes = 2 * need + 2 * need_ahead;
+    h->ws_slot_off[1] = need;
+    h->ws_slot_off[2] = 2 * need;
+    h->ws_slot_off[3] = 2 * need + need_ahead;
   }
   std::vector<int32_t> h_level_ids, h_diag;
-  std::vector<Task> h_trsm, h_updt, h_tc;
+  std::vector<Task> h_trsm, h_updt, h_tc, h_tc2;
   std::vector<int2> h_grp;
   // runs of consecutive tasks with the same (front, row block), at most
   // kGroupCap long so that the round-robin deal stays balanced
   constexpr int kGroupCap = 8;
-  auto add_groups = [&](int64_t first, int64_t count) -> int {
+  auto add_groups = [&](const std::vector<Task>& tl, int64_t first, int64_t count) -> int {
     int ng = 0;
     for (int64_t q = first; q < first + count;) {
       int64_t e = q + 1;
-      while (e < first + count && e - q < kGroupCap && h_tc[e].f == h_tc[q].f && h_tc[e].i == h_tc[q].i) ++e;
+      while (e < first + count && e - q < kGroupCap && tl[e].f == tl[q].f && tl[e].i == tl[q].i) ++e;
       h_grp.push_back(make_int2((int)q, (int)(e - q)));
       ++ng;
       q = e;
@@ -753,10 +776,46 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
       R.n_upd = (int)((int64_t)h_updt.size() - R.upd_off);
       R.n_tc = (int)((int64_t)h_tc.size() - R.tc_off);
       R.grp_off = (int64_t)h_grp.size();
-      R.n_grp_next = add_groups(R.tc_off, R.n_tc_next);
-      R.n_grp_rest = add_groups(R.tc_off + R.n_tc_next, R.n_tc - R.n_tc_next);
+      R.n_grp_next = add_groups(h_tc, R.tc_off, R.n_tc_next);
+      R.n_grp_rest = add_groups(h_tc, R.tc_off + R.n_tc_next, R.n_tc - R.n_tc_next);
       L.steps.push_back(R);
     }
+    // two-panel updates: row blocks never straddle the first update-row tile,
+    // so within a block every row tile has the same structurally zero panels
+    if (h->use_tc)
+      for (int k = 0; k + 1 < max_steps; k += 2) {
+        PairRange P{};
+        P.k = k;
+        P.tc2_off = (int64_t)h_tc2.size();
+        std::vector<Task> near, far;
+        for (int f : L.ids) {
+          const FrontDev& F = h->fronts[f];
+          const int nte = F.ne_pad / T, nt = F.ld / T;
+          if (k >= nte) continue;
+          const int np = (k + 1 < nte) ? 2 : 1;
+          auto zero = [&](int p, int i) { return F.kind == 0 && i >= nte && (p + 1) * T <= F.n_int; };
+          const int seg[3] = {k + 2, std::max(nte, k + 2), nt};
+          for (int sg = 0; sg < 2; ++sg)
+            for (int i0 = seg[sg]; i0 < seg[sg + 1]; i0 += 2) {
+              const int i1 = i0 + 1 < seg[sg + 1] ? i0 + 1 : -1;
+              for (int j = k + 2; j <= std::min(i1 >= 0 ? i1 : i0, nt - 1); ++j) {
+                const int lo = i0 >= j ? 1 : 0, hi = i1 >= 0 ? 2 : 0;
+                int pm = 0;
+                for (int pp = 0; pp < np; ++pp)
+                  if (!zero(k + pp, i0) && !zero(k + pp, j)) pm |= 4 << pp;
+                if ((lo | hi) && pm) (j <= k + 3 ? near : far).push_back(Task{f, i0, j, lo | hi | pm});
+              }
+            }
+        }
+        P.n_near = (int)near.size();
+        P.n_far = (int)far.size();
+        h_tc2.insert(h_tc2.end(), near.begin(), near.end());
+        h_tc2.insert(h_tc2.end(), far.begin(), far.end());
+        P.grp_off = (int64_t)h_grp.size();
+        P.n_grp_near = add_groups(h_tc2, P.tc2_off, P.n_near);
+        P.n_grp_far = add_groups(h_tc2, P.tc2_off + P.n_near, P.n_far);
+        L.pairs.push_back(P);
+      }
   }
   // solve tasks: forward (front, row tile) by increasing tile, backward (front,
   // eliminated tile) by decreasing tile, so that every CTA waits only on CTAs
@@ -818,6 +877,7 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
   DD_CUDA(A.upload(&h->d_updt, h_updt, s));
   DD_CUDA(A.upload(&h->d_fwd, h_fwd, s));
   DD_CUDA(A.upload(&h->d_tc, h_tc, s));
+  DD_CUDA(A.upload(&h->d_tc2, h_tc2, s));
   DD_CUDA(A.upload(&h->d_grp, h_grp, s));
   {
     int nl = 0;
@@ -825,7 +885,7 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
     h->n_counters = std::max(nl, 1);
     DD_CUDA(A.alloc(&h->d_counters, (size_t)h->n_counters));
   }
-  if (h->use_tc) DD_CUDA(A.alloc(&h->d_ws, 2 * h->ws_bytes));   // two step parities (look-ahead)
+  if (h->use_tc) DD_CUDA(A.alloc(&h->d_ws, h->ws_bytes));
   DD_CUDA(cudaStreamCreateWithFlags(&h->s2, cudaStreamNonBlocking));
   DD_CUDA(cudaEventCreateWithFlags(&h->ev_panel, cudaEventDisableTiming));
   DD_CUDA(cudaEventCreateWithFlags(&h->ev_rest, cudaEventDisableTiming));
@@ -933,12 +993,14 @@ int dd_factor(dd_handle* h) {
     }
     const int diag64 = (l > 0) ? 1 : 0;  // mixed form: FP64 pivot blocks of the auxiliary matrix
     // one-step look-ahead on levels with few fronts: the main stream updates
-    // only the next panel column and factors that panel, while the second
-    // stream applies the rest of the trailing update of the current step
-    const bool ahead = h->use_tc && L.ids.size() <= 32 && L.steps.size() > 1;
+    // only the next panel columns and factors those panels, while the second
+    // stream applies the rest of the trailing update
+    const bool ahead = h->use_tc && L.ahead && L.steps.size() > 1;
     const int reserve = ahead ? 16 : 0;   // SMs left free for the panel chain
+    // image slot of panel k: even / odd panels alternate, the look-ahead levels over four slots
+    auto wsp = [&](int k) -> unsigned char* { return h->d_ws + h->ws_slot_off[ahead ? (k & 3) : (k & 1)]; };
     auto panel = [&](const StepRange& R) -> cudaError_t {
-      unsigned char* ws = h->use_tc ? h->d_ws + (size_t)(R.k & 1) * h->ws_bytes : nullptr;
+      unsigned char* ws = h->use_tc ? wsp(R.k) : nullptr;
       cudaError_t e = mark(DD_K_DIAG, true);
       if (e != cudaSuccess) return e;
       if (p == 0)
@@ -961,7 +1023,7 @@ int dd_factor(dd_handle* h) {
     };
     // trailing update of step R.k, tasks [first, first + n) of its lists, on stream `on`
     auto update = [&](const StepRange& R, bool next_part, cudaStream_t on, int cap) -> cudaError_t {
-      const unsigned char* ws = h->use_tc ? h->d_ws + (size_t)(R.k & 1) * h->ws_bytes : nullptr;
+      const unsigned char* ws = h->use_tc ? wsp(R.k) : nullptr;
       const int n = h->use_tc ? (next_part ? R.n_tc_next : R.n_tc - R.n_tc_next)
                               : (next_part ? R.n_upd_next : R.n_upd - R.n_upd_next);
       const int64_t first = h->use_tc ? R.tc_off + (next_part ? 0 : R.n_tc_next)
@@ -977,28 +1039,70 @@ int dd_factor(dd_handle* h) {
       count(DD_K_UPDATE, n);
       return mark_on(DD_K_UPDATE, false, on);
     };
+    // two-panel update of steps P.k, P.k + 1: near (columns k + 2, k + 3) or far (the rest)
+    auto pair_update = [&](const PairRange& P, bool near_part, cudaStream_t on, int cap) -> cudaError_t {
+      cudaError_t e = mark_on(DD_K_UPDATE, true, on);
+      if (e != cudaSuccess) return e;
+      ddk::launch_update_tc2(h->pool, h->d_fronts, h->d_tc2, h->d_grp + P.grp_off + (near_part ? 0 : P.n_grp_near),
+                             near_part ? P.n_grp_near : P.n_grp_far, P.k, wsp(P.k), wsp(P.k + 1), h->d_status, on,
+                             cap, h->d_counters + (next_counter++ % h->n_counters));
+      count(DD_K_UPDATE, near_part ? P.n_near : P.n_far);
+      return mark_on(DD_K_UPDATE, false, on);
+    };
     const size_t ns = L.steps.size();
-    if (!ahead) {
+    if (!h->use_tc) {
       for (const StepRange& R : L.steps) {
         DD_CUDA(panel(R));
         DD_CUDA(update(R, true, s, 0));
         DD_CUDA(update(R, false, s, 0));
       }
-    } else {
-      DD_CUDA(panel(L.steps[0]));
-      DD_CUDA(cudaEventRecord(h->ev_panel, s));
-      for (size_t q = 0; q < ns; ++q) {
+    } else if (!ahead) {
+      // steps in pairs: panel k, column k + 1, panel k + 1, then both panels at once
+      for (size_t q = 0; q < ns;) {
         const StepRange& R = L.steps[q];
-        DD_CUDA(cudaStreamWaitEvent(h->s2, h->ev_panel, 0));
-        DD_CUDA(update(R, false, h->s2, reserve));            // columns >= k + 2
-        DD_CUDA(cudaEventRecord(h->ev_rest, h->s2));
-        DD_CUDA(update(R, true, s, 0));                       // column k + 1
+        DD_CUDA(panel(R));
+        DD_CUDA(update(R, true, s, 0));
         if (q + 1 < ns) {
+          const PairRange& P = L.pairs[q / 2];
           DD_CUDA(panel(L.steps[q + 1]));
-          DD_CUDA(cudaEventRecord(h->ev_panel, s));
+          DD_CUDA(pair_update(P, true, s, 0));
+          DD_CUDA(pair_update(P, false, s, 0));
+          q += 2;
+        } else {
+          DD_CUDA(update(R, false, s, 0));
+          q += 1;
         }
-        DD_CUDA(cudaStreamWaitEvent(s, h->ev_rest, 0));
       }
+    } else {
+      // the far part of each two-panel update runs on the second stream while
+      // the main stream forms the next two panels; before touching columns the
+      // far part also updates, the main stream waits for it
+      DD_CUDA(cudaEventRecord(h->ev_rest, h->s2));
+      DD_CUDA(panel(L.steps[0]));
+      for (size_t q = 0; q < ns;) {
+        const StepRange& R = L.steps[q];
+        DD_CUDA(update(R, true, s, 0));                       // column k + 1 with panel k
+        if (q + 1 < ns) {
+          const PairRange& P = L.pairs[q / 2];
+          DD_CUDA(panel(L.steps[q + 1]));
+          DD_CUDA(cudaStreamWaitEvent(s, h->ev_rest, 0));     // the previous far part is done
+          DD_CUDA(cudaEventRecord(h->ev_panel, s));
+          DD_CUDA(cudaStreamWaitEvent(h->s2, h->ev_panel, 0));
+          DD_CUDA(pair_update(P, false, h->s2, reserve));     // columns >= k + 4
+          DD_CUDA(cudaEventRecord(h->ev_rest, h->s2));
+          DD_CUDA(pair_update(P, true, s, 0));                // columns k + 2, k + 3
+          if (q + 2 < ns) DD_CUDA(panel(L.steps[q + 2]));
+          q += 2;
+        } else {
+          DD_CUDA(cudaStreamWaitEvent(s, h->ev_rest, 0));
+          DD_CUDA(cudaEventRecord(h->ev_panel, s));
+          DD_CUDA(cudaStreamWaitEvent(h->s2, h->ev_panel, 0));
+          DD_CUDA(update(R, false, h->s2, reserve));          // columns >= k + 2
+          DD_CUDA(cudaEventRecord(h->ev_rest, h->s2));
+          q += 1;
+        }
+      }
+      DD_CUDA(cudaStreamWaitEvent(s, h->ev_rest, 0));
     }
   }
   DD_CUDA(cudaGetLastError());

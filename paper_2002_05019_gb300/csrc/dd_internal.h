@@ -107,6 +107,12 @@ void launch_trsm_mx(void* pool, const FrontDev* fronts, const Task* tasks, int n
 // counter: a zeroed int in device memory used to claim groups dynamically (one per launch)
 void launch_update_tc(void* pool, const FrontDev* fronts, const Task* tasks, const int2* groups, int n, int k,
                       const unsigned char* ws, DevStatus* st, cudaStream_t s, int reserve_sms, int* counter);
+// two-panel form: C -= [L_ik L_i,k+1] [W_jk W_j,k+1]^T (K = 128) with the operand
+// images of panel k in ws0 and of panel k + 1 in ws1; task .pad bits 0 / 1 store
+// the rows of tile i0 / i0 + 1, bits 2 / 3 enable panel k / k + 1
+void launch_update_tc2(void* pool, const FrontDev* fronts, const Task* tasks, const int2* groups, int n, int k,
+                       const unsigned char* ws0, const unsigned char* ws1, DevStatus* st, cudaStream_t s,
+                       int reserve_sms, int* counter);
 void launch_update(int prec, void* pool, const FrontDev* fronts, const Task* tasks, int n, int k,
                    cudaStream_t s);
 void launch_extend_add(int prec, void* pool, const FrontDev* fronts, const int32_t* node_ids, int n,
