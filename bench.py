@@ -211,7 +211,7 @@ def time_form(p, precision, args, torch, stream):
     import paper_2002_05019_gb300 as dd
     s = dd.Solver.from_problem(p, precision=precision, stream=stream.cuda_stream, device=torch.cuda.current_device(),
                                time_kernels=not args.no_kernel_timing, refine_tol=args.refine_tol,
-                               pivoting=args.pivoting)
+                               pivoting=args.pivoting, update_panels=args.update_panels)
     f_host = dd.stacked_loads(p)
     f_dev = torch.from_numpy(f_host).cuda()
     for _ in range(args.warmup):
@@ -316,7 +316,10 @@ def ours_arm(args):
         # tcgen05 kind::tf32: dense TF32 peak = measured bf16 peak x nominal TF32/BF16 ratio (1.1 / 2.25);
         # the 3xTF32 split issues 3 tensor passes per algorithmic product
         tf32 = peaks["bf16_tflops"] * (1.1 / 2.25)
-        bound, peak, kernel = "tensor", tf32 / 3.0, "k_update_tc (tcgen05 3xTF32, 128x64 complex blocks)"
+        kernel = ("k_update_tc2 + k_update_tc (tcgen05 3xTF32, 128x64 complex blocks; two-panel K=128 passes, "
+                  "one-panel passes for the next column)" if args.update_panels == 2 else
+                  "k_update_tc (tcgen05 3xTF32, 128x64 complex blocks, one panel per pass)")
+        bound, peak = "tensor", tf32 / 3.0
         src = (f"TF32 dense {tf32:.0f} TFLOP/s = measured bf16 {peaks['bf16_tflops']:.0f} x 1.1/2.25 "
                f"({peaks_src}); effective complex64 peak = TF32 / 3 split passes")
     else:
@@ -332,6 +335,7 @@ def ours_arm(args):
         "vs_baseline": None, "dtype": "c64+f64" if args.precision == "mixed" else "c128", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload][1], "form": args.precision, "n_dofs": p.n,
                    "n_domains": p.n_sub, "n_duals": p.n_dual, "nrhs": p.nrhs, "pivoting": args.pivoting,
+                   "update_panels": args.update_panels,
                    "l2": "working set (front pool) far larger than the 129 MB L2",
                    "parallelism": f"replicas x{ws}"},
         "tflops": flops_step / t_step / 1e12,
@@ -377,6 +381,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--pivoting", type=int, default=0, choices=[0, 1, 2],
                     help="restricted Bunch-Kaufman: 0 none, 1 auxiliary fronts, 2 every front")
+    ap.add_argument("--update-panels", type=int, default=2, choices=[1, 2],
+                    help="mixed form: panels fused per tensor-core trailing-update pass")
     ap.add_argument("--no-kernel-timing", action="store_true",
                     help="no per-launch CUDA events (no kernel breakdown or roofline)")
     ap.add_argument("--refine-tol", type=float, default=1e-11,

@@ -104,6 +104,9 @@ typedef struct {
                                per-kernel-class device time in dd_stats (slower; default 0) */
   int32_t simt_update;      /* MIXED: 1 runs the trailing updates on the FP32 FMA pipes instead of
                                the tensor cores (comparison baseline; default 0) */
+  int32_t update_panels;    /* MIXED, tensor cores: panels fused per trailing-update pass, 1 (C read
+                               and written after every 64-wide panel) or 2 (after every pair of
+                               panels, K = 128; default); other values: DD_ERR_INVALID_ARG */
 } dd_options;
 
 /* Kernel classes of dd_stats.kernel_ms / kernel_launches / kernel_flops. */

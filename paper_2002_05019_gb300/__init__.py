@@ -49,7 +49,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("refine_tol", C.c_double), ("max_refine", C.c_int32),
                 ("pivoting", C.c_int32), ("tree_parent", C.POINTER(C.c_int32)),
                 ("centroids", C.POINTER(C.c_double)), ("cuda_stream", C.c_void_p), ("device", C.c_int32),
-                ("time_kernels", C.c_int32), ("simt_update", C.c_int32)]
+                ("time_kernels", C.c_int32), ("simt_update", C.c_int32), ("update_panels", C.c_int32)]
 
 KERNEL_CLASSES = ["diag", "trsm", "update", "assemble", "init"]
 
@@ -122,7 +122,8 @@ class Solver:
 
     def __init__(self, subdomains, n_dual: int, precision: str = "fp64", refine_tol: float = 1e-13,
                  max_refine: int | None = None, tree_parent=None, centroids=None, stream=None, device: int = 0,
-                 time_kernels: bool = False, simt_update: bool = False, pivoting: int | None = None):
+                 time_kernels: bool = False, simt_update: bool = False, pivoting: int | None = None,
+                 update_panels: int | None = None):
         lib = load()
         self._keep = []
         subs = (Subdomain * len(subdomains))()
@@ -160,6 +161,8 @@ class Solver:
         opt.device = device
         opt.time_kernels = 1 if time_kernels else 0
         opt.simt_update = 1 if simt_update else 0
+        if update_panels is not None:
+            opt.update_panels = int(update_panels)   # tensor-core update: 1 or 2 panels per pass
         if pivoting is not None:
             opt.pivoting = int(pivoting)   # 0 none, 1 auxiliary fronts, 2 every front (restricted Bunch-Kaufman)
         self.precision = precision

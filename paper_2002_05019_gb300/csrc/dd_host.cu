@@ -155,6 +155,7 @@ struct dd_handle {
   cudaEvent_t ev_panel = nullptr, ev_rest = nullptr;
   size_t ws_bytes = 0;
   int use_tc = 0;
+  bool pair_panels = false;        // two-panel trailing updates (K = 128)
   int32_t *d_flag_f = nullptr, *d_flag_b = nullptr;
   int64_t n_tiles = 0;
   int epoch = 0;
@@ -408,6 +409,7 @@ int dd_default_options(dd_options* opt) {
   opt->refine_tol = 1e-13;
   opt->max_refine = 0;
   opt->pivoting = 0;
+  opt->update_panels = 2;
   return DD_OK;
 }
 
@@ -430,6 +432,7 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
   if (opt.precision != DD_PREC_FP64 && opt.precision != DD_PREC_MIXED) return DD_ERR_INVALID_ARG;
   if (opt.pivoting < 0 || opt.pivoting > 2 || opt.max_refine < 0 || !(opt.refine_tol >= 0))
     return DD_ERR_INVALID_ARG;
+  if (opt.update_panels != 1 && opt.update_panels != 2) return DD_ERR_INVALID_ARG;
   if (opt.device < 0) return DD_ERR_INVALID_ARG;
 
   double amax = 0.0;
@@ -451,6 +454,7 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
   h->elem = opt.precision == DD_PREC_FP64 ? 16 : 8;
   h->time_kernels = opt.time_kernels ? 1 : 0;
   h->use_tc = (opt.precision == DD_PREC_MIXED && !opt.simt_update) ? 1 : 0;
+  h->pair_panels = h->use_tc && opt.update_panels == 2;
   h->pivoting = opt.pivoting;
   h->max_abs_a = std::max(amax, 1.0);
   cudaStream_t s = h->stream;
@@ -782,7 +786,7 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
     }
     // two-panel updates: row blocks never straddle the first update-row tile,
     // so within a block every row tile has the same structurally zero panels
-    if (h->use_tc)
+    if (h->pair_panels)
       for (int k = 0; k + 1 < max_steps; k += 2) {
         PairRange P{};
         P.k = k;
@@ -1050,11 +1054,28 @@ int dd_factor(dd_handle* h) {
       return mark_on(DD_K_UPDATE, false, on);
     };
     const size_t ns = L.steps.size();
-    if (!h->use_tc) {
+    if (!h->use_tc || (!h->pair_panels && !ahead)) {
       for (const StepRange& R : L.steps) {
         DD_CUDA(panel(R));
         DD_CUDA(update(R, true, s, 0));
         DD_CUDA(update(R, false, s, 0));
+      }
+    } else if (!h->pair_panels) {
+      // one panel per update pass: the rest of step k on the second stream
+      // while the main stream updates column k + 1 and forms panel k + 1
+      DD_CUDA(panel(L.steps[0]));
+      DD_CUDA(cudaEventRecord(h->ev_panel, s));
+      for (size_t q = 0; q < ns; ++q) {
+        const StepRange& R = L.steps[q];
+        DD_CUDA(cudaStreamWaitEvent(h->s2, h->ev_panel, 0));
+        DD_CUDA(update(R, false, h->s2, reserve));            // columns >= k + 2
+        DD_CUDA(cudaEventRecord(h->ev_rest, h->s2));
+        DD_CUDA(update(R, true, s, 0));                       // column k + 1
+        if (q + 1 < ns) {
+          DD_CUDA(panel(L.steps[q + 1]));
+          DD_CUDA(cudaEventRecord(h->ev_panel, s));
+        }
+        DD_CUDA(cudaStreamWaitEvent(s, h->ev_rest, 0));
       }
     } else if (!ahead) {
       // steps in pairs: panel k, column k + 1, panel k + 1, then both panels at once

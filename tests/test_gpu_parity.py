@@ -16,8 +16,11 @@ pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-12, "mixed": 1e-10}
 # F_i itself is not refined: in the mixed form it carries the complex64 LDL^T
-# error, about cond(A_i) * u32 with cond(A_i) <~ 1e3 and u32 = 6e-8
-TOL_F = {"fp64": 1e-12, "mixed": 1e-4}
+# error, about cond(A_i) * u with cond(A_i) <~ 1e3.  The tensor-core products
+# are 3xTF32: a = hi + lo with lo rounded to tf32, so each product carries
+# about 2^-21 (the dropped lo lo' term and the rounding of lo, each 2^-22
+# relative) instead of FP32's 2^-24: u ~ 5e-7, cond * u ~ 5e-4
+TOL_F = {"fp64": 1e-12, "mixed": 5e-4}
 
 
 def rel(a, b):
@@ -177,22 +180,28 @@ def test_batched_512_domains_full_size(c2_linear, precision):
     s.free()
 
 
-def test_tensor_core_update_matches_simt_update(c1):
-    """The tcgen05 3xTF32 trailing update and the FP32 FMA-pipe update give the
-    same F_i to FP32 accuracy and both refine to the mixed tolerance."""
-    o = oracle.DDOracle(c1)
-    uo, _ = o.solve([s.f for s in c1.subs])
-    xo, _ = o.gather(uo)
+@pytest.mark.parametrize("p_name", ["c1", "medium"])
+def test_tensor_core_update_matches_simt_update(c1, p_name):
+    """The tcgen05 3xTF32 trailing update, one or two panels per pass, and the
+    FP32 FMA-pipe update give the same F_i to the accuracy of 3xTF32 products
+    (cond(A_i) <~ 1e3 times 2^-21) and all refine to the mixed tolerance."""
+    p = c1 if p_name == "c1" else femgen.medium()
+    o = oracle.DDOracle(p) if p_name == "c1" else None
+    xo = o.gather(o.solve([s.f for s in p.subs])[0])[0] if o else None
     res = {}
-    for simt in (False, True):
-        s = dd.Solver.from_problem(c1, precision="mixed", simt_update=simt)
+    for mode in ("tc2", "tc1", "simt"):
+        s = dd.Solver.from_problem(p, precision="mixed", simt_update=(mode == "simt"),
+                                   update_panels=(1 if mode == "tc1" else 2))
         s.factor()
-        u, _ = s.solve(dd.stacked_loads(c1))
-        assert rel(gather(c1, u), xo) <= TOL["mixed"]
-        res[simt] = [s.schur(i)[0] for i in range(c1.n_sub)]
+        u, lam = s.solve(dd.stacked_loads(p))
+        if xo is not None:
+            assert rel(gather(p, u), xo) <= TOL["mixed"]
+        res[mode] = ([s.schur(i)[0] for i in range(0, p.n_sub, max(1, p.n_sub // 8))], u)
         s.free()
-    for a, b in zip(res[False], res[True]):
-        assert rel(a, b) <= 1e-5
+    for mode in ("tc1", "simt"):
+        for a, b in zip(res["tc2"][0], res[mode][0]):
+            assert rel(a, b) <= 5e-4
+        assert rel(res["tc2"][1], res[mode][1]) <= TOL["mixed"] * 10
 
 
 def test_refinement_stop_at_1e11_meets_1e10(c1, c2_linear):
