@@ -688,7 +688,7 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
         FrontDev& F = h->fronts[f];
         const int64_t ntr = F.ld / T - 1;  // trailing tiles at the first step
         F.ws_off = w;
-        w += ((ntr + 1) / 2) * (int64_t)DD_TC_ABLOCK;
+        w += ntr * (int64_t)DD_TC_ATILE;
         F.ws_boff = w;
         w += ntr * (int64_t)DD_TC_BTILE;
       }
@@ -704,7 +704,7 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
   std::vector<int32_t> h_level_ids, h_diag;
   std::vector<Task> h_trsm, h_updt, h_tc, h_tc2;
   std::vector<int2> h_grp;
-  // runs of consecutive tasks with the same (front, row block), at most
+  // runs of consecutive tasks with the same (front, row tile), at most
   // kGroupCap long so that the round-robin deal stays balanced
   constexpr int kGroupCap = 8;
   auto add_groups = [&](const std::vector<Task>& tl, int64_t first, int64_t count) -> int {
@@ -756,15 +756,23 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
             if (!h->use_tc) (j == k + 1 ? upd_next : upd_rest).push_back(Task{f, i, j, 0});
           }
         }
-        // tensor-core tasks: 128-row blocks (tiles i0, i0 + 1) x column tile j
-        if (h->use_tc)
-          for (int i0 = k + 1; i0 < nt; i0 += 2)
-            for (int j = k + 1; j <= std::min(i0 + 1, nt - 1); ++j) {
-              if (zero_tile(j)) continue;
-              const int lo = (i0 >= j && !zero_tile(i0)) ? 1 : 0;
-              const int hi = (i0 + 1 < nt && !zero_tile(i0 + 1)) ? 2 : 0;
-              if (lo | hi) (j == k + 1 ? tc_next : tc_rest).push_back(Task{f, i0, j, lo | hi});
-            }
+        // tensor-core tasks: row tile i x column tiles (j, j + 1); column pairs
+        // never straddle the first update-row tile, so both columns of a task
+        // share their structurally zero panels
+        if (h->use_tc) {
+          for (int i = k + 1; i < nt; ++i)
+            if (!zero_tile(i) && !zero_tile(k + 1)) tc_next.push_back(Task{f, i, k + 1, 1 | 4});
+          const int sb[3] = {k + 2, std::max(nte, k + 2), nt};
+          for (int i = k + 2; i < nt; ++i) {
+            if (zero_tile(i)) continue;
+            for (int sg = 0; sg < 2; ++sg)
+              for (int j = sb[sg]; j < sb[sg + 1] && j <= i; j += 2) {
+                if (zero_tile(j)) continue;
+                const int two = (j + 1 < sb[sg + 1] && j + 1 <= i) ? 2 : 0;
+                tc_rest.push_back(Task{f, i, j, 1 | two | 4});
+              }
+          }
+        }
       }
       R.n_upd_next = (int)upd_next.size();
       R.n_tc_next = (int)tc_next.size();
@@ -784,8 +792,8 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
       R.n_grp_rest = add_groups(h_tc, R.tc_off + R.n_tc_next, R.n_tc - R.n_tc_next);
       L.steps.push_back(R);
     }
-    // two-panel updates: row blocks never straddle the first update-row tile,
-    // so within a block every row tile has the same structurally zero panels
+    // two-panel updates: column pairs never straddle the first update-row
+    // tile, so both columns of a task share their structurally zero panels
     if (h->pair_panels)
       for (int k = 0; k + 1 < max_steps; k += 2) {
         PairRange P{};
@@ -798,18 +806,17 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
           if (k >= nte) continue;
           const int np = (k + 1 < nte) ? 2 : 1;
           auto zero = [&](int p, int i) { return F.kind == 0 && i >= nte && (p + 1) * T <= F.n_int; };
-          const int seg[3] = {k + 2, std::max(nte, k + 2), nt};
-          for (int sg = 0; sg < 2; ++sg)
-            for (int i0 = seg[sg]; i0 < seg[sg + 1]; i0 += 2) {
-              const int i1 = i0 + 1 < seg[sg + 1] ? i0 + 1 : -1;
-              for (int j = k + 2; j <= std::min(i1 >= 0 ? i1 : i0, nt - 1); ++j) {
-                const int lo = i0 >= j ? 1 : 0, hi = i1 >= 0 ? 2 : 0;
+          const int sb[3] = {k + 2, std::max(nte, k + 2), nt};
+          for (int i = k + 2; i < nt; ++i)
+            for (int sg = 0; sg < 2; ++sg)
+              for (int j = sb[sg]; j < sb[sg + 1] && j <= i; j += 2) {
                 int pm = 0;
                 for (int pp = 0; pp < np; ++pp)
-                  if (!zero(k + pp, i0) && !zero(k + pp, j)) pm |= 4 << pp;
-                if ((lo | hi) && pm) (j <= k + 3 ? near : far).push_back(Task{f, i0, j, lo | hi | pm});
+                  if (!zero(k + pp, i) && !zero(k + pp, j)) pm |= 4 << pp;
+                if (!pm) continue;
+                const int two = (j + 1 < sb[sg + 1] && j + 1 <= i) ? 2 : 0;
+                (j <= k + 3 ? near : far).push_back(Task{f, i, j, 1 | two | pm});
               }
-            }
         }
         P.n_near = (int)near.size();
         P.n_far = (int)far.size();
@@ -1036,7 +1043,7 @@ int dd_factor(dd_handle* h) {
       if (e != cudaSuccess) return e;
       if (h->use_tc)
         ddk::launch_update_tc(h->pool, h->d_fronts, h->d_tc, h->d_grp + R.grp_off + (next_part ? 0 : R.n_grp_next),
-                              next_part ? R.n_grp_next : R.n_grp_rest, R.k, ws, h->d_status, on, cap,
+                              next_part ? R.n_grp_next : R.n_grp_rest, R.k, ws, nullptr, h->d_status, on, cap,
                               h->d_counters + (next_counter++ % h->n_counters));
       else
         ddk::launch_update(p, h->pool, h->d_fronts, h->d_updt + first, n, R.k, on);
@@ -1047,7 +1054,7 @@ int dd_factor(dd_handle* h) {
     auto pair_update = [&](const PairRange& P, bool near_part, cudaStream_t on, int cap) -> cudaError_t {
       cudaError_t e = mark_on(DD_K_UPDATE, true, on);
       if (e != cudaSuccess) return e;
-      ddk::launch_update_tc2(h->pool, h->d_fronts, h->d_tc2, h->d_grp + P.grp_off + (near_part ? 0 : P.n_grp_near),
+      ddk::launch_update_tc(h->pool, h->d_fronts, h->d_tc2, h->d_grp + P.grp_off + (near_part ? 0 : P.n_grp_near),
                              near_part ? P.n_grp_near : P.n_grp_far, P.k, wsp(P.k), wsp(P.k + 1), h->d_status, on,
                              cap, h->d_counters + (next_counter++ % h->n_counters));
       count(DD_K_UPDATE, near_part ? P.n_near : P.n_far);

@@ -41,15 +41,18 @@ struct FrontDev {
   int64_t ws_boff;   // mixed form: byte offset of its B operand images
 };
 
-// Panel operand images for the tensor-core trailing update (mixed form).
-// A image of a 128-row block: planes (Re hi, Re lo, Im hi, Im lo) x 2 K-atoms of
-// 32 tf32 each, 16 KB per (plane, atom), 128B-swizzled K-major; the two 64-row
-// tiles of the block fill its first and second 8 KB half.  B image of a 64-row
-// column tile: split (hi, lo) x 2 K-atoms x [Re W][Im W], 8 KB each.
+// Panel operand images for the tensor-core trailing update (mixed form), one
+// per trailing 64-row tile t of a panel step, 128B-swizzled K-major, in pieces
+// of 128 rows x one K atom (32 tf32) = 16 KB, indexed (split hi/lo, atom):
+//   A image (rows of L): within a piece, for each group of 16 tile rows, their
+//     real parts then their imaginary parts (piece row 32 (r / 16) + r % 16 and
+//     + 16), so the two parts of a row land in one TMEM sub-partition;
+//   B image (rows of W = L D): within a piece, the 64 real rows then the 64
+//     imaginary rows.
 #define DD_TC_ATOM 16384
 #define DD_TC_HALF 8192
-#define DD_TC_ABLOCK (4 * 2 * DD_TC_ATOM)
-#define DD_TC_BTILE (2 * 2 * 2 * DD_TC_HALF)
+#define DD_TC_ATILE (2 * 2 * DD_TC_ATOM)
+#define DD_TC_BTILE (2 * 2 * DD_TC_ATOM)
 
 struct LeafDev {
   int64_t csr_off;   // offset of the domain's nonzeros in the concatenated CSR arrays
@@ -101,18 +104,14 @@ void launch_diag_mx(int diag_fp64, void* pool, const FrontDev* fronts, const int
                     DevStatus* st, void* linv, cudaStream_t s, uint8_t* piv = nullptr);
 void launch_trsm_mx(void* pool, const FrontDev* fronts, const Task* tasks, int n, int k, DevStatus* st,
                     const void* linv, unsigned char* ws, cudaStream_t s, const uint8_t* piv = nullptr);
-// tensor-core trailing update (mixed form): task (front, first row tile i0 of a
-// 128-row block, column tile j, store mask in .pad: bit 0 rows of i0, bit 1 rows of i0+1)
-// groups: (first task, count) of each run of tasks sharing one A block; n = number of groups;
+// tensor-core trailing update (mixed form): task (front, row tile i, column
+// tile j); .pad bits 0 / 1 store column tiles j / j + 1, bits 2 / 3 add the
+// products of panel k (images in ws0) / panel k + 1 (images in ws1).
+// groups: (first task, count) of runs of tasks of one row tile; n = number of groups;
 // counter: a zeroed int in device memory used to claim groups dynamically (one per launch)
 void launch_update_tc(void* pool, const FrontDev* fronts, const Task* tasks, const int2* groups, int n, int k,
-                      const unsigned char* ws, DevStatus* st, cudaStream_t s, int reserve_sms, int* counter);
-// two-panel form: C -= [L_ik L_i,k+1] [W_jk W_j,k+1]^T (K = 128) with the operand
-// images of panel k in ws0 and of panel k + 1 in ws1; task .pad bits 0 / 1 store
-// the rows of tile i0 / i0 + 1, bits 2 / 3 enable panel k / k + 1
-void launch_update_tc2(void* pool, const FrontDev* fronts, const Task* tasks, const int2* groups, int n, int k,
-                       const unsigned char* ws0, const unsigned char* ws1, DevStatus* st, cudaStream_t s,
-                       int reserve_sms, int* counter);
+                      const unsigned char* ws0, const unsigned char* ws1, DevStatus* st, cudaStream_t s,
+                      int reserve_sms, int* counter);
 void launch_update(int prec, void* pool, const FrontDev* fronts, const Task* tasks, int n, int k,
                    cudaStream_t s);
 void launch_extend_add(int prec, void* pool, const FrontDev* fronts, const int32_t* node_ids, int n,

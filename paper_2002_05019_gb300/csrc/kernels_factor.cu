@@ -41,28 +41,28 @@ __device__ __forceinline__ void put_img(unsigned char* base, int row, int k, flo
 
 template <typename S>
 __device__ __forceinline__ void write_images(unsigned char*, const FrontDev&, int, int, S, S) {}
-// mixed form: A planes of L_ik and B planes of W_ik = L_ik D_k for the tensor-core update
+// mixed form: A image of L_ik and B image of W_ik = L_ik D_k for the tensor-core update
 template <>
 __device__ __forceinline__ void write_images<float2>(unsigned char* ws, const FrontDev& F, int ti, int rc, float2 L,
                                                      float2 W) {
   const int r = rc >> 6, p = rc & 63;              // row of the tile, K index
   const int a = p >> 5, kk = p & 31;
-  unsigned char* Ab = ws + F.ws_off + (int64_t)(ti >> 1) * DD_TC_ABLOCK + (ti & 1) * DD_TC_HALF;
+  const int ra = (r >> 4) * 32 + (r & 15);         // A piece row of the real part (imaginary: + 16)
+  unsigned char* Ab = ws + F.ws_off + (int64_t)ti * DD_TC_ATILE;
   unsigned char* Bb = ws + F.ws_boff + (int64_t)ti * DD_TC_BTILE;
   float h, l;
   split_tf32(L.x, h, l);
-  put_img(Ab + (0 * 2 + a) * DD_TC_ATOM, r, kk, h);
-  put_img(Ab + (1 * 2 + a) * DD_TC_ATOM, r, kk, l);
+  put_img(Ab + (0 * 2 + a) * DD_TC_ATOM, ra, kk, h);
+  put_img(Ab + (1 * 2 + a) * DD_TC_ATOM, ra, kk, l);
   split_tf32(L.y, h, l);
-  put_img(Ab + (2 * 2 + a) * DD_TC_ATOM, r, kk, h);
-  put_img(Ab + (3 * 2 + a) * DD_TC_ATOM, r, kk, l);
-  const float parts[2] = {W.x, W.y};
-#pragma unroll
-  for (int v = 0; v < 2; ++v) {
-    split_tf32(parts[v], h, l);
-    put_img(Bb + ((0 * 2 + a) * 2 + v) * DD_TC_HALF, r, kk, h);
-    put_img(Bb + ((1 * 2 + a) * 2 + v) * DD_TC_HALF, r, kk, l);
-  }
+  put_img(Ab + (0 * 2 + a) * DD_TC_ATOM, ra + 16, kk, h);
+  put_img(Ab + (1 * 2 + a) * DD_TC_ATOM, ra + 16, kk, l);
+  split_tf32(W.x, h, l);
+  put_img(Bb + (0 * 2 + a) * DD_TC_ATOM, r, kk, h);
+  put_img(Bb + (1 * 2 + a) * DD_TC_ATOM, r, kk, l);
+  split_tf32(W.y, h, l);
+  put_img(Bb + (0 * 2 + a) * DD_TC_ATOM, r + 64, kk, h);
+  put_img(Bb + (1 * 2 + a) * DD_TC_ATOM, r + 64, kk, l);
 }
 
 __device__ void status_pivot(DevStatus* st, int front, int row) {
