@@ -82,7 +82,10 @@ typedef struct {
                                DD_PREC_MIXED: complex64 factors and solves,
                                FP64 pivot blocks of the auxiliary matrix and
                                FP64 iterative refinement on the arrowhead system. */
-  double refine_tol;        /* MIXED: stop when |du|/|u| <= refine_tol (default 1e-13) */
+  double refine_tol;        /* MIXED: stop when |du|/|u| <= refine_tol, or when the error left
+                               after the update, estimated from the contraction of successive
+                               corrections (|du_k|^2 / |du_k-1|, the direct solve being du_0
+                               of relative size 1), is <= refine_tol (default 1e-13) */
   int32_t max_refine;       /* MIXED: refinement iteration cap (default 10); FP64: extra
                                FP64 refinement steps after the direct solve (default 0) */
   int32_t pivoting;         /* 0: unpivoted LDL^T everywhere (it exists for lossy domains).

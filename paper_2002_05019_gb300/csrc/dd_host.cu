@@ -1210,7 +1210,10 @@ static int solve_block(dd_handle* h, int32_t nrhs, const dd_c128* f, int64_t ldf
   int iters = 0;
   double ratio = 0.0;
   int status = DD_OK;
-  double prev_col[kSolveBlock] = {};
+  // relative size of the previous correction per right-hand side; the direct
+  // solve itself is the first correction (from zero), of relative size 1
+  double prev_col[kSolveBlock];
+  for (int j = 0; j < kSolveBlock; ++j) prev_col[j] = 1.0;
   const int64_t nu_el = h->n_loc * (int64_t)nrhs;
   const int64_t nl_el = (int64_t)h->n_dual * nrhs;
   for (int it = 0; it < h->max_refine; ++it) {
@@ -1245,7 +1248,7 @@ static int solve_block(dd_handle* h, int32_t nrhs, const dd_c128* f, int64_t ldf
       const double r = su > 0 ? std::sqrt(sdu / su) : 0.0;
       if (!std::isfinite(r)) finite = false;
       double err = r;
-      if (it > 0 && prev_col[j] > 0 && r < prev_col[j]) err = std::min(err, r * (r / prev_col[j]));
+      if (prev_col[j] > 0 && r < prev_col[j]) err = std::min(err, r * (r / prev_col[j]));
       prev_col[j] = r;
       worst = std::max(worst, err);
       if (!(err <= h->refine_tol)) all_done = false;
