@@ -252,36 +252,68 @@ __device__ __forceinline__ uint16_t pb_elem(int e) {
   return (uint16_t)((r << 8) | c);
 }
 
-// Unpivoted LDL^T of pivot block jb of the tile in precision C.  Per column j:
-// the rows below scale their entry (one barrier), then every thread updates
-// its elements of the trailing triangle, the owner of (j+1, j+1) also forming
-// the next reciprocal pivot (one barrier).
+// Unpivoted LDL^T of pivot block jb of the tile in precision C, and the FP32
+// inverse N = L^{-1} of its unit-lower factor built alongside (N <- E_j N for
+// the elimination E_j of column j: rows r > j of N lose l_rj times row j).  Per
+// column j: the rows below scale their entry (one barrier), then every thread
+// updates its elements of the trailing triangle (precision C) and of N (FP32),
+// the owner of (j+1, j+1) also forming the next reciprocal pivot (one barrier).
+// Each thread owns at most two trailing elements (a column-descending
+// enumeration, so the elements with c > j are e < (31 - j)(32 - j) / 2) and
+// the row r = tid / 8 of N at columns tid % 8 + 8 m.
 template <typename C>
-__device__ void factor_pivot32(float2* a, int jb, C* ap, C* w, C* rinv, const uint16_t* etab) {
-  for (int idx = threadIdx.x; idx < PB * PB; idx += blockDim.x) {
+__device__ void factor_pivot32(float2* a, int jb, C* ap, C* w, float2* lcol, C* rinv, float2* li) {
+  const int tid = threadIdx.x;
+  int er[2], ec[2], erc[2], er0[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int e = tid + h * 256;
+    const uint16_t rc = e < PB * (PB - 1) / 2 ? pb_elem(e) : (uint16_t)0;
+    er[h] = rc >> 8;
+    ec[h] = e < PB * (PB - 1) / 2 ? (rc & 255) : -1;   // -1: no element
+    erc[h] = tri(er[h], ec[h] < 0 ? 0 : ec[h]);
+    er0[h] = tri(er[h], 0);
+  }
+  const int nr = tid >> 3, nq = tid & 7;          // this thread's row of N and first column
+  const int nbase = tri(jb + nr, jb);             // N[nr][q] at li[nbase + q]
+  for (int idx = tid; idx < PB * PB; idx += blockDim.x) {
     const int i = idx / PB, c = idx % PB;
-    if (c <= i) ap[tri(i, c)] = cconv<C>(a[tri(jb + i, jb + c)]);
+    if (c <= i) {
+      ap[tri(i, c)] = cconv<C>(a[tri(jb + i, jb + c)]);
+      li[tri(jb + i, jb + c)] = make_float2(c == i ? 1.f : 0.f, 0.f);
+    }
   }
   __syncthreads();
-  if (threadIdx.x == 0) *rinv = crcp(ap[0]);
+  if (tid == 0) *rinv = crcp(ap[0]);
   __syncthreads();
   for (int j = 0; j < PB - 1; ++j) {
-    if (threadIdx.x > j && threadIdx.x < PB) {
-      const C v = ap[tri(threadIdx.x, j)];
-      w[threadIdx.x] = v;
-      ap[tri(threadIdx.x, j)] = cmul(v, *rinv);
+    if (tid > j && tid < PB) {
+      const C v = ap[tri(tid, j)];
+      const C l = cmul(v, *rinv);
+      w[tid] = v;
+      ap[tri(tid, j)] = l;
+      lcol[tid] = cconv<float2>(l);
     }
     __syncthreads();
-    const int nj = (PB - 1 - j) * (PB - j) / 2;
-    for (int e = threadIdx.x; e < nj; e += blockDim.x) {
-      const int r = etab[e] >> 8, c = etab[e] & 255;
-      const C v = cfms(ap[tri(r, j)], w[c], ap[tri(r, c)]);
-      ap[tri(r, c)] = v;
-      if (c == j + 1 && r == j + 1) *rinv = crcp(v);
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+      if (ec[h] > j) {
+        const C v = cfms(ap[er0[h] + j], w[ec[h]], ap[erc[h]]);
+        ap[erc[h]] = v;
+        if (ec[h] == j + 1 && er[h] == j + 1) *rinv = crcp(v);
+      }
+    if (nr > j) {
+      const float2 l = lcol[nr];
+      const int jrow = tri(jb + j, jb);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int q = nq + 8 * m;
+        if (q <= j) li[nbase + q] = cfms(l, li[jrow + q], li[nbase + q]);
+      }
     }
     __syncthreads();
   }
-  for (int idx = threadIdx.x; idx < PB * PB; idx += blockDim.x) {
+  for (int idx = tid; idx < PB * PB; idx += blockDim.x) {
     const int i = idx / PB, c = idx % PB;
     if (c <= i) a[tri(jb + i, jb + c)] = cconv<float2>(ap[tri(i, c)]);
   }
@@ -339,7 +371,7 @@ __global__ void __launch_bounds__(256, 1) k_diag_mx(float2* pool, const FrontDev
   float2 (*x21)[PB + 1] = reinterpret_cast<float2 (*)[PB + 1]>(ap_raw);
   __shared__ C w[PB];
   __shared__ C rinv;
-  __shared__ uint16_t etab[PB * (PB + 1) / 2];
+  __shared__ float2 lcol[PB];    // the scaled column of the current pivot, FP32, for N
   __shared__ float2 d1inv[PB];   // D1^{-1}: (D1^{-1} x)_c = d1inv[c] x_c + g1[c] x_{q1[c]}
   // restricted Bunch-Kaufman (fronts that pivot): 2x2 column, permutation, 2x2 off-diagonals
   __shared__ C w1[PB];
@@ -356,11 +388,10 @@ __global__ void __launch_bounds__(256, 1) k_diag_mx(float2* pool, const FrontDev
     const int i = idx / T, c = idx % T;
     if (c <= i) a[tri(i, c)] = base[(int64_t)i * F.ld + c];
   }
-  for (int e = threadIdx.x; e < PB * (PB - 1) / 2; e += blockDim.x) etab[e] = pb_elem(e);
   if (threadIdx.x < 2) cnt[threadIdx.x] = 0;
   __syncthreads();
   if (pv) factor_pivot32_bk<C>(a, 0, ap, w, w1, perm, dsup, cnt);
-  else factor_pivot32<C>(a, 0, ap, w, &rinv, etab);
+  else factor_pivot32<C>(a, 0, ap, w, lcol, &rinv, li);
   // D1^{-1} (from the precision-C factor while ap still holds it) and N11
   if (threadIdx.x < PB) {
     const int c = threadIdx.x;
@@ -382,7 +413,7 @@ __global__ void __launch_bounds__(256, 1) k_diag_mx(float2* pool, const FrontDev
       q1[c] = first ? c + 1 : c - 1;
     }
   }
-  inv_unit_lower32(a, 0, li);
+  if (pv) inv_unit_lower32(a, 0, li);   // the unpivoted path formed N11 with the factor
   __syncthreads();   // ap (the precision-C block) is dead from here until pivot block 2
   {
     // X21 = A21 P1^T N11^T: x21[r][c] = sum_{q <= c} A21[r][perm q] N11[c][q]
@@ -426,10 +457,10 @@ __global__ void __launch_bounds__(256, 1) k_diag_mx(float2* pool, const FrontDev
     __syncthreads();
     if (threadIdx.x < PB) perm[PB + threadIdx.x] += PB;
   } else {
-    factor_pivot32<C>(a, PB, ap, w, &rinv, etab);
+    factor_pivot32<C>(a, PB, ap, w, lcol, &rinv, li);
   }
-  // N22, then N21 = -N22 (L21 N11) through x21 = L21 N11
-  inv_unit_lower32(a, PB, li);
+  // N22 (formed with the factor when unpivoted), then N21 = -N22 (L21 N11) through x21 = L21 N11
+  if (pv) inv_unit_lower32(a, PB, li);
   {
     const int r = threadIdx.x >> 3, cg = threadIdx.x & 7;
 #pragma unroll
