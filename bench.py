@@ -115,7 +115,7 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # CPU oracle leg (the only place bench.py runs oracle/): one thread, bounded
 # ---------------------------------------------------------------------------
-def oracle_sample_worker(workload: str, budget_s: float, max_domains: int, out_path: str):
+def oracle_sample_worker(workload: str, budget_s: float, max_domains: int, out_path: str, with_skyline: bool = False):
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     import femgen
     import oracle
@@ -135,21 +135,23 @@ def oracle_sample_worker(workload: str, budget_s: float, max_domains: int, out_p
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
+    # O2's factor memory: skyline (envelope) of the undecomposed RCM-ordered system (untimed)
+    sky = oracle.envelope_entries(p.A_indptr, p.A_indices) if with_skyline else None
     n3_all = float(sum(float(s.n) ** 3 for s in p.subs))
     n3_s = float(sum(float(p.subs[i].n) ** 3 for i in done))
     t_est = dt * n3_all / n3_s
     with open(out_path, "w") as fh:
         json.dump({"seconds": dt, "domains": done, "n_global": p.n, "t_est": t_est,
-                   "value": p.n / t_est, "n3_fraction": n3_s / n3_all}, fh)
+                   "value": p.n / t_est, "n3_fraction": n3_s / n3_all, "skyline_entries": sky}, fh)
 
 
-def run_oracle_sample(workload: str, budget_s: float, max_domains: int = 10 ** 9):
+def run_oracle_sample(workload: str, budget_s: float, max_domains: int = 10 ** 9, with_skyline: bool = False):
     import tempfile
     fd, path = tempfile.mkstemp(suffix=".json")
     os.close(fd)
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ("import sys; sys.path.insert(0, %r); import bench; bench.oracle_sample_worker(%r, %r, %r, %r)"
-            % (ROOT, workload, budget_s, max_domains, path))
+    code = ("import sys; sys.path.insert(0, %r); import bench; bench.oracle_sample_worker(%r, %r, %r, %r, %r)"
+            % (ROOT, workload, budget_s, max_domains, path, with_skyline))
     subprocess.run([sys.executable, "-c", code], env=env, check=True)
     with open(path) as fh:
         r = json.load(fh)
@@ -343,6 +345,9 @@ def ours_arm(args):
         "roofline": roofline,
         "gpu_launches": main["launches"],
         "clocks": main["clocks"],
+        # factor memory (the paper's headline comparison): stored L and D of every front
+        "memory": {"factor_bytes": st["bytes_factor"], "device_bytes": st["bytes_device"],
+                   "skyline_factor_bytes_c128": None},
     }
     if "e2e" in main:
         line["e2e"] = {k: main["e2e"][k] for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step")}
@@ -357,8 +362,10 @@ def ours_arm(args):
                              "kernel_ms_per_step": {c: v / args.steps for c, v in f["kernel_ms"].items()}}
     line["kernel_ms_per_step"] = {c: v / args.steps for c, v in main["kernel_ms"].items()}
     if rank == 0 and not args.no_cpu_baseline:
-        r = run_oracle_sample(args.workload, budget_s=args.cpu_budget)
+        r = run_oracle_sample(args.workload, budget_s=args.cpu_budget, with_skyline=True)
         line["cpu_baseline"] = cpu_baseline_entry(r, args.workload)
+        if r.get("skyline_entries"):
+            line["memory"]["skyline_factor_bytes_c128"] = 16 * int(r["skyline_entries"])
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -177,6 +177,22 @@ int dd_factor(dd_handle* h);
 int dd_solve(dd_handle* h, int32_t nrhs, const dd_c128* f, int64_t ldf, dd_c128* u, int64_t ldu,
              dd_c128* lambda, int64_t ldl);
 
+/* Solve as dd_solve but recover the primal unknowns of the listed domains only
+ * (Section II: only the requested subdomains' primal unknowns need be
+ * recovered after the auxiliary solve).
+ *   f       all domains' loads, as for dd_solve
+ *   req     n_req distinct domain ids in [0, n_sub), host memory
+ *   u       (sum over req of n_i) x nrhs, column-major (ldu): u_i of the listed
+ *           domains stacked in the order of req, each in its caller row order
+ *   lambda  as for dd_solve (all duals), or NULL
+ * Without refinement (FP64 form, max_refine = 0) the backward substitution
+ * and output run for the listed domains only; with refinement every domain
+ * is solved (the FP64 residual needs all of u) and the listed rows returned.
+ * Errors: DD_ERR_INVALID_ARG for a bad, repeated or out-of-range id or a short
+ * ldu; otherwise as dd_solve. */
+int dd_solve_subset(dd_handle* h, int32_t nrhs, const dd_c128* f, int64_t ldf, int32_t n_req, const int32_t* req,
+                    dd_c128* u, int64_t ldu, dd_c128* lambda, int64_t ldl);
+
 /* Copy F_i = B_i A_i^{-1} B_i^T of domain i (Section II: the domain's
  * contribution to the auxiliary matrix) into host memory `out`
  * (m_i x m_i, column-major, ld m_i), with `duals` (m_i entries, may be NULL)

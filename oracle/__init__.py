@@ -8,6 +8,7 @@ only inputs are the seeded problems from `femgen`.
 Routes to the same solution x = A^{-1} b of the assembled FEM system:
   * dense.lu_solve          - dense LU with partial pivoting (tiny systems);
   * skyline.BandLDLT        - RCM + band-profile LDL^T of the undecomposed system;
+  * skyline.envelope_entries - its skyline (envelope) factor size: O2's factor memory;
   * dd.DDOracle             - the paper's decomposition route (Section II):
                               per-domain LDL^T, F = sum B_i A_i^{-1} B_i^T,
                               F lambda = d, primal recovery;
@@ -21,10 +22,10 @@ Parity status: pinned by closed forms and library special cases (see the
 tests); the paper prints no numerical values, so no value of the paper pins it.
 """
 from .dense import lu_solve, ldlt, ldlt_solve, ldlt_bk_restricted, ldlt_bk_solve
-from .skyline import BandLDLT, rcm
+from .skyline import BandLDLT, rcm, envelope_entries
 from .dd import DDOracle, subdomain_schur, arrow_residual, local_B, arrow_dense, arrow_solve
 from .refine import residual_dd, refine, backward_error
 
-__all__ = ["lu_solve", "ldlt", "ldlt_solve", "ldlt_bk_restricted", "ldlt_bk_solve", "BandLDLT", "rcm",
+__all__ = ["lu_solve", "ldlt", "ldlt_solve", "ldlt_bk_restricted", "ldlt_bk_solve", "BandLDLT", "rcm", "envelope_entries",
            "DDOracle", "subdomain_schur", "arrow_residual", "local_B", "arrow_dense", "arrow_solve",
            "residual_dd", "refine", "backward_error"]

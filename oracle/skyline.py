@@ -131,3 +131,22 @@ class BandLDLT:
         x = np.empty_like(z)
         x[self.perm] = z
         return x[:, 0] if vec else x
+
+
+def envelope_entries(indptr: np.ndarray, indices: np.ndarray, perm: np.ndarray | None = None) -> int:
+    """Stored entries of a skyline (envelope) LDL^T factor after the ordering
+    perm (RCM by default): for each row i of the permuted matrix, the entries
+    from its first nonzero column to the diagonal.  The profile holds all fill
+    of an LDL^T without pivoting, so this is the factor memory of O2."""
+    n = indptr.size - 1
+    if n == 0:
+        return 0
+    if perm is None:
+        perm = rcm(indptr, indices)
+    inv = np.empty(n, dtype=np.int64)
+    inv[perm] = np.arange(n)
+    rows = np.repeat(np.arange(n), np.diff(indptr))
+    pi, pj = inv[rows], inv[indices]
+    first = np.arange(n, dtype=np.int64)
+    np.minimum.at(first, pi, pj)
+    return int(np.sum(np.arange(n) - first + 1))

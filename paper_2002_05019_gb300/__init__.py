@@ -65,7 +65,7 @@ class Stats(C.Structure):
                 ("interchanges", C.c_int64), ("pivots_2x2", C.c_int64)]
 
 
-EXPORTS = ["dd_default_options", "dd_setup", "dd_set_values", "dd_factor", "dd_solve", "dd_get_schur",
+EXPORTS = ["dd_default_options", "dd_setup", "dd_set_values", "dd_factor", "dd_solve", "dd_solve_subset", "dd_get_schur",
            "dd_get_stats", "dd_strerror", "dd_free", "dd_dense_solve_noalloc", "dd_selftest_wait_timeout"]
 
 
@@ -90,6 +90,8 @@ def load(build_if_missing: bool = True):
     lib.dd_factor.argtypes = [C.c_void_p]
     lib.dd_solve.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_void_p, C.c_int64, C.c_void_p,
                              C.c_int64]
+    lib.dd_solve_subset.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.POINTER(C.c_int32),
+                                    C.c_void_p, C.c_int64, C.c_void_p, C.c_int64]
     lib.dd_get_schur.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     lib.dd_get_stats.argtypes = [C.c_void_p, C.POINTER(Stats)]
     lib.dd_strerror.argtypes = [C.c_int]
@@ -221,6 +223,25 @@ class Solver:
                              self.n_loc, C.c_void_p(lo.ctypes.data) if self.n_dual else None, max(self.n_dual, 1))
         _check(code, "dd_solve", ok)
         self.last_status = code
+        return (uo[:, 0], lo[:, 0]) if vec else (uo, lo)
+
+    def solve_subset(self, f, domains, allow_not_converged: bool = False):
+        """Solve for the stacked local loads f (numpy, n_loc x nrhs) and recover only
+        the listed domains: returns (u of those domains stacked in the given order, lambda)."""
+        ok = (DD_OK, 7) if allow_not_converged else (DD_OK,)
+        req = np.ascontiguousarray(domains, dtype=np.int32)
+        fa = np.asarray(f, dtype=np.complex128)
+        vec = fa.ndim == 1
+        fa = np.asfortranarray(fa[:, None] if vec else fa)
+        nrhs = fa.shape[1]
+        rows = int(sum(self.n[int(i)] for i in req)) if all(0 <= int(i) < len(self.n) for i in req) else 1
+        uo = np.zeros((max(rows, 1), nrhs), dtype=np.complex128, order="F")
+        lo = np.zeros((self.n_dual, nrhs), dtype=np.complex128, order="F")
+        code = _lib.dd_solve_subset(self._h, nrhs, C.c_void_p(fa.ctypes.data), self.n_loc, req.size,
+                                    _ptr(req, C.c_int32), C.c_void_p(uo.ctypes.data), max(rows, 1),
+                                    C.c_void_p(lo.ctypes.data) if self.n_dual else None, max(self.n_dual, 1))
+        _check(code, "dd_solve_subset", ok)
+        uo = uo[:rows]
         return (uo[:, 0], lo[:, 0]) if vec else (uo, lo)
 
     def schur(self, i: int):

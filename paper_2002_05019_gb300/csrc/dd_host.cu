@@ -118,6 +118,10 @@ struct dd_handle {
   std::vector<Level> levels;
   std::vector<std::vector<int32_t>> leaf_duals;  // sorted duals of each domain
   std::vector<int64_t> leaf_vec_off;
+  std::vector<LeafDev> h_leaves_copy;   // for subset recovery
+  std::vector<Task> h_bwd_leaf;         // level-0 backward tasks (front, tile)
+  void* d_sub = nullptr;                // subset recovery scratch (tasks, leaves, segments, rows)
+  size_t sub_cap = 0;
   double max_abs_a = 1.0;
   int64_t rows_total = 0;  // sum of front orders (right-hand-side rows)
 
@@ -180,6 +184,7 @@ struct dd_handle {
 
   ~dd_handle() {
     for (void* q : work_ptrs) cudaFree(q);
+    if (d_sub) cudaFree(d_sub);
     arena.release();
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
@@ -341,7 +346,19 @@ int ensure_work(dd_handle* h, int nrhs) {
 
 // one direct solve with the stored factors: (f [n_loc x nrhs], g [n_dual x nrhs] or NULL)
 // -> (u, lam) in FP64 (assign)
-void direct_solve(dd_handle* h, int nrhs, const double2* f, int64_t ldf, const double2* g, double2* u, double2* lam) {
+// subset (optional): backward tasks of the listed leaves and their output
+// descriptors (vec_off = row offset in u); other leaves are neither
+// back-substituted nor written
+struct LeafSubset {
+  const Task* bwd = nullptr;
+  int n_bwd = 0;
+  const LeafDev* leaves = nullptr;
+  int n_leaves = 0;
+  int64_t ldu = 0;
+};
+
+void direct_solve(dd_handle* h, int nrhs, const double2* f, int64_t ldf, const double2* g, double2* u, double2* lam,
+                  const LeafSubset* sub = nullptr) {
   cudaStream_t s = h->stream;
   const int p = h->prec == DD_PREC_FP64 ? 0 : 1;
   const int ep = ++h->epoch;
@@ -363,13 +380,29 @@ void direct_solve(dd_handle* h, int nrhs, const double2* f, int64_t ldf, const d
   }
   for (size_t l = h->levels.size(); l-- > 0;) {
     const Level& L = h->levels[l];
-    ddk::launch_backward(p, h->pool, h->rpool, h->d_fronts, h->d_bwd + L.bwd_off, L.n_bwd, nrhs, h->d_upd, h->d_sep,
-                         h->lam_work, h->n_dual, h->d_flag_b, ep, h->d_solve_status, s, h->d_linv, h->d_piv);
+    const bool leaf_sub = sub && l == 0;
+    ddk::launch_backward(p, h->pool, h->rpool, h->d_fronts, leaf_sub ? sub->bwd : h->d_bwd + L.bwd_off,
+                         leaf_sub ? sub->n_bwd : L.n_bwd, nrhs, h->d_upd, h->d_sep, h->lam_work, h->n_dual,
+                         h->d_flag_b, ep, h->d_solve_status, s, h->d_linv, h->d_piv);
     h->launches += 1;
   }
-  ddk::launch_leaf_out(p, h->rpool, h->d_fronts, h->d_leaves, h->n_sub, h->d_perm, u, h->n_loc, nrhs, 0, s);
+  if (sub)
+    ddk::launch_leaf_out(p, h->rpool, h->d_fronts, sub->leaves, sub->n_leaves, h->d_perm, u, sub->ldu, nrhs, 0, s);
+  else
+    ddk::launch_leaf_out(p, h->rpool, h->d_fronts, h->d_leaves, h->n_sub, h->d_perm, u, h->n_loc, nrhs, 0, s);
   ddk::launch_lam_out(p, h->lam_work, h->n_dual, h->n_dual, nrhs, lam, h->n_dual, 0, s);
   h->launches += 2;
+}
+
+// rows of listed domains: segment q copies rows [seg[3q], seg[3q] + seg[3q+2]) of
+// src to rows starting at seg[3q+1] of dst, for every right-hand side
+__global__ void k_gather_rows(const double2* src, int64_t lds, double2* dst, int64_t ldd, const int64_t* seg,
+                              int nrhs) {
+  const int64_t so = seg[3 * blockIdx.x], dof = seg[3 * blockIdx.x + 1], len = seg[3 * blockIdx.x + 2];
+  for (int64_t e = threadIdx.x; e < len * nrhs; e += blockDim.x) {
+    const int64_t r = e % len, j = e / len;
+    dst[dof + r + j * ldd] = src[so + r + j * lds];
+  }
 }
 
 __global__ void k_axpy(double2* y, const double2* x, int64_t n) {
@@ -904,6 +937,10 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
   if (h->prec == DD_PREC_MIXED) DD_CUDA(A.alloc(&h->d_linv, (size_t)std::max<int64_t>(h->n_tiles, 1) * T * T));
   if (h->pivoting) DD_CUDA(A.alloc(&h->d_piv, (size_t)std::max<int64_t>(h->n_tiles, 1) * T));
   DD_CUDA(A.upload(&h->d_bwd, h_bwd, s));
+  h->h_leaves_copy = h_leaves;
+  if (!h->levels.empty())
+    h->h_bwd_leaf.assign(h_bwd.begin() + h->levels[0].bwd_off,
+                         h_bwd.begin() + h->levels[0].bwd_off + h->levels[0].n_bwd);
   DD_CUDA(A.alloc(&h->d_flag_f, (size_t)std::max<int64_t>(h->n_tiles, 1)));
   DD_CUDA(A.alloc(&h->d_flag_b, (size_t)std::max<int64_t>(h->n_tiles, 1)));
   DD_CUDA(cudaMemsetAsync(h->d_flag_f, 0, sizeof(int32_t) * std::max<int64_t>(h->n_tiles, 1), s));
@@ -1192,6 +1229,126 @@ int dd_solve(dd_handle* h, int32_t nrhs, const dd_c128* f, int64_t ldf, dd_c128*
   return status;
 }
 
+int dd_solve_subset(dd_handle* h, int32_t nrhs, const dd_c128* f, int64_t ldf, int32_t n_req, const int32_t* req,
+                    dd_c128* u, int64_t ldu, dd_c128* lambda, int64_t ldl) {
+  if (!h || nrhs < 0 || n_req < 0 || (n_req > 0 && !req)) return DD_ERR_INVALID_ARG;
+  if (nrhs == 0) return DD_OK;
+  if (!f || ldf < h->n_loc || (lambda && ldl < h->n_dual)) return DD_ERR_INVALID_ARG;
+  std::vector<char> seen(h->n_sub, 0);
+  int64_t n_rows = 0;
+  for (int32_t q = 0; q < n_req; ++q) {
+    const int32_t id = req[q];
+    if (id < 0 || id >= h->n_sub || seen[id]) return DD_ERR_INVALID_ARG;
+    seen[id] = 1;
+    n_rows += h->h_leaves_copy[id].n;
+  }
+  if (n_rows > 0 && (!u || ldu < n_rows)) return DD_ERR_INVALID_ARG;
+  if (!h->factored) return DD_ERR_NOT_FACTORED;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->device);
+  struct Restore { int d; ~Restore() { cudaSetDevice(d); } } restore{cur};
+  cudaStream_t s = h->stream;
+  // the listed leaves (output offsets in request order), their backward tasks, row segments
+  std::vector<LeafDev> sl(n_req);
+  std::vector<int64_t> seg(3 * (size_t)n_req);
+  std::vector<int> front_listed(h->fronts.size(), 0);
+  int64_t off = 0;
+  for (int32_t q = 0; q < n_req; ++q) {
+    LeafDev L = h->h_leaves_copy[req[q]];
+    seg[3 * q] = L.vec_off;
+    seg[3 * q + 1] = off;
+    seg[3 * q + 2] = L.n;
+    L.vec_off = off;
+    off += L.n;
+    sl[q] = L;
+    front_listed[L.front] = 1;
+  }
+  std::vector<Task> sb;
+  for (const Task& t : h->h_bwd_leaf)
+    if (front_listed[t.f]) sb.push_back(t);
+  const bool refined = h->max_refine > 0;
+  const bool u_dev = n_rows > 0 && is_device_ptr(u);
+  const int32_t chunk = std::min<int32_t>(kSolveBlock, nrhs);
+  auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t b_sb = al(sb.size() * sizeof(Task) + 1), b_sl = al(sl.size() * sizeof(LeafDev) + 1),
+               b_seg = al(seg.size() * sizeof(int64_t) + 1), b_u = al((size_t)n_rows * chunk * 16 + 1);
+  const size_t need = b_sb + b_sl + b_seg + b_u;
+  if (need > h->sub_cap) {
+    if (h->d_sub) cudaFree(h->d_sub);
+    h->d_sub = nullptr;
+    h->sub_cap = 0;
+    DD_CUDA(cudaMalloc(&h->d_sub, need));
+    h->sub_cap = need;
+  }
+  unsigned char* base = static_cast<unsigned char*>(h->d_sub);
+  Task* d_sb = reinterpret_cast<Task*>(base);
+  LeafDev* d_sl = reinterpret_cast<LeafDev*>(base + b_sb);
+  int64_t* d_seg = reinterpret_cast<int64_t*>(base + b_sb + b_sl);
+  double2* d_usub = reinterpret_cast<double2*>(base + b_sb + b_sl + b_seg);
+  if (!sb.empty()) DD_CUDA(cudaMemcpyAsync(d_sb, sb.data(), sb.size() * sizeof(Task), cudaMemcpyHostToDevice, s));
+  if (n_req) {
+    DD_CUDA(cudaMemcpyAsync(d_sl, sl.data(), sl.size() * sizeof(LeafDev), cudaMemcpyHostToDevice, s));
+    DD_CUDA(cudaMemcpyAsync(d_seg, seg.data(), seg.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s));
+  }
+  int status = DD_OK;
+  double t_ms = 0.0;
+  for (int32_t c0 = 0; c0 < nrhs; c0 += kSolveBlock) {
+    const int32_t nb = std::min<int32_t>(kSolveBlock, nrhs - c0);
+    const dd_c128* fc = f + (size_t)c0 * ldf;
+    dd_c128* lc = lambda ? lambda + (size_t)c0 * ldl : nullptr;
+    double2* out = u_dev ? reinterpret_cast<double2*>(u + (size_t)c0 * ldu) : d_usub;
+    const int64_t ldo = u_dev ? ldu : n_rows;
+    if (refined) {
+      // the FP64 residual needs every domain: full refined solve, then the listed rows
+      const int st = solve_block(h, nb, fc, ldf, nullptr, 0, lc, ldl);
+      if (st != DD_OK && st != DD_ERR_NOT_CONVERGED) return st;
+      if (st == DD_ERR_NOT_CONVERGED) status = st;
+      t_ms += h->stats.t_solve_ms;
+      if (n_req) k_gather_rows<<<n_req, 256, 0, s>>>(h->d_u, h->n_loc, out, ldo, d_seg, nb);
+    } else {
+      const int w = ensure_work(h, nb);
+      if (w != DD_OK) return w;
+      h->launches = 0;
+      const size_t row_b = (size_t)h->n_loc * 16;
+      DD_CUDA(cudaEventRecord(h->ev0, s));
+      DD_CUDA(cudaMemcpy2DAsync(h->d_f, row_b, fc, (size_t)ldf * 16, row_b, nb,
+                                is_device_ptr(fc) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+      LeafSubset sub;
+      sub.bwd = d_sb;
+      sub.n_bwd = (int)sb.size();
+      sub.leaves = d_sl;
+      sub.n_leaves = n_req;
+      sub.ldu = ldo;
+      direct_solve(h, nb, h->d_f, h->n_loc, nullptr, out, h->d_lam, &sub);
+      if (lc && h->n_dual)
+        DD_CUDA(cudaMemcpy2DAsync(lc, (size_t)ldl * 16, h->d_lam, (size_t)h->n_dual * 16, (size_t)h->n_dual * 16, nb,
+                                  is_device_ptr(lc) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+      DD_CUDA(cudaEventRecord(h->ev1, s));
+      DevStatus sst{};
+      DD_CUDA(cudaMemcpyAsync(&sst, h->d_solve_status, sizeof(sst), cudaMemcpyDeviceToHost, s));
+      DD_CUDA(cudaStreamSynchronize(s));
+      if (sst.code != 0) {
+        DD_CUDA(cudaMemsetAsync(h->d_solve_status, 0, sizeof(DevStatus), s));
+        DD_CUDA(cudaStreamSynchronize(s));
+        return sst.code == 8 ? DD_ERR_TIMEOUT : DD_ERR_CUDA;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+      t_ms += ms;
+      h->stats.launches_solve = h->launches;
+      h->stats.refine_iters = 0;
+    }
+    if (!u_dev && n_rows > 0)
+      DD_CUDA(cudaMemcpy2DAsync(u + (size_t)c0 * ldu, (size_t)ldu * 16, d_usub, (size_t)n_rows * 16,
+                                (size_t)n_rows * 16, nb, cudaMemcpyDeviceToHost, s));
+  }
+  DD_CUDA(cudaGetLastError());
+  DD_CUDA(cudaStreamSynchronize(s));
+  h->stats.t_solve_ms = t_ms;
+  return status;
+}
+
 static int solve_block(dd_handle* h, int32_t nrhs, const dd_c128* f, int64_t ldf, dd_c128* u, int64_t ldu,
                        dd_c128* lambda, int64_t ldl) {
   int cur = 0;
@@ -1257,8 +1414,9 @@ static int solve_block(dd_handle* h, int32_t nrhs, const dd_c128* f, int64_t ldf
     if (!finite || all_done) break;
   }
   if (h->prec == DD_PREC_MIXED && h->max_refine > 0 && !(ratio <= h->refine_tol)) status = DD_ERR_NOT_CONVERGED;
-  DD_CUDA(cudaMemcpy2DAsync(u, (size_t)ldu * 16, h->d_u, row_b, row_b, nrhs,
-                            is_device_ptr(u) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  if (u)
+    DD_CUDA(cudaMemcpy2DAsync(u, (size_t)ldu * 16, h->d_u, row_b, row_b, nrhs,
+                              is_device_ptr(u) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
   if (lambda && h->n_dual)
     DD_CUDA(cudaMemcpy2DAsync(lambda, (size_t)ldl * 16, h->d_lam, (size_t)h->n_dual * 16, (size_t)h->n_dual * 16,
                               nrhs, is_device_ptr(lambda) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));

@@ -224,3 +224,42 @@ def test_arrow_solve_on_indefinite_chain():
     # exactly zero diagonal: the unpivoted LDL^T of a domain breaks down at once
     with pytest.raises(np.linalg.LinAlgError):
         oracle.ldlt(odd._csr_dense(p.subs[0]))
+
+
+# ---------------------------------------------------------------------------
+# skyline (envelope) factor size of O2, the memory the paper compares against
+# ---------------------------------------------------------------------------
+def _csr(A):
+    import scipy.sparse as sp
+    M = sp.csr_matrix(A)
+    M.sort_indices()
+    return M.indptr.astype(np.int64), M.indices.astype(np.int64)
+
+
+def test_envelope_closed_forms():
+    n = 9
+    ident = np.arange(n)
+    ip, ix = _csr(np.eye(n))
+    assert oracle.envelope_entries(ip, ix, ident) == n                       # diagonal: n
+    T = np.eye(n) + np.eye(n, k=1) + np.eye(n, k=-1)
+    ip, ix = _csr(T)
+    assert oracle.envelope_entries(ip, ix, ident) == 2 * n - 1               # tridiagonal: 2n - 1
+    ip, ix = _csr(np.ones((n, n)))
+    assert oracle.envelope_entries(ip, ix, ident) == n * (n + 1) // 2        # dense: n(n+1)/2
+    # arrow pointing down-right (last row full): n + (n - 1)(n)/2 ... its reversal is 2n - 1
+    Ar = np.eye(n)
+    Ar[-1, :] = Ar[:, -1] = 1
+    ip, ix = _csr(Ar)
+    assert oracle.envelope_entries(ip, ix, ident) == 2 * n - 1
+    assert oracle.envelope_entries(ip, ix, ident[::-1].copy()) == n * (n + 1) // 2
+
+
+def test_envelope_holds_the_band_factor():
+    # the unpivoted LDL^T of the RCM-ordered matrix has no fill outside the envelope
+    p = femgen.tiny(3, 2)
+    A = p.A_csr().toarray()
+    perm = oracle.rcm(p.A_indptr, p.A_indices)
+    L, _ = oracle.ldlt(A[np.ix_(perm, perm)])
+    nz = np.abs(np.tril(L)) > 0
+    first = np.argmax(nz, axis=1)
+    assert int(np.sum(np.arange(A.shape[0]) - first + 1)) <= oracle.envelope_entries(p.A_indptr, p.A_indices, perm)
