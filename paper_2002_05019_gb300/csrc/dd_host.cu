@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <numeric>
 #include <vector>
@@ -120,6 +121,10 @@ struct dd_handle {
   std::vector<int64_t> leaf_vec_off;
   std::vector<LeafDev> h_leaves_copy;   // for subset recovery
   std::vector<Task> h_bwd_leaf;         // level-0 backward tasks (front, tile)
+  cudaGraphExec_t factor_exec = nullptr; // the captured factorization (no per-launch timing)
+  int factor_graph_launches = 0;
+  size_t fact_nev = 0;                  // timed event pairs in the graph and the class of each
+  std::vector<int> fact_cls;
   void* d_sub = nullptr;                // subset recovery scratch (tasks, leaves, segments, rows)
   size_t sub_cap = 0;
   double max_abs_a = 1.0;
@@ -156,6 +161,7 @@ struct dd_handle {
   uint8_t* d_piv = nullptr;        // restricted Bunch-Kaufman: permutation of every diagonal tile (64 bytes each)
   int pivoting = 0;
   cudaStream_t s2 = nullptr;       // look-ahead: bulk trailing updates run here
+  cudaStream_t own_stream = nullptr;  // created when the caller gives no stream
   cudaEvent_t ev_panel = nullptr, ev_rest = nullptr;
   size_t ws_bytes = 0;
   int use_tc = 0;
@@ -169,6 +175,19 @@ struct dd_handle {
 
   // solve work (grown on demand, freed with the handle)
   int nrhs_cap = 0;
+  // captured direct solve (a) and refinement step (b) per right-hand-side count
+  struct SolveGraphs {
+    cudaGraphExec_t a = nullptr, b = nullptr;
+    int la = 0, lb = 0;
+  };
+  std::map<int, SolveGraphs> solve_graphs;
+  void drop_solve_graphs() {
+    for (auto& kv : solve_graphs) {
+      if (kv.second.a) cudaGraphExecDestroy(kv.second.a);
+      if (kv.second.b) cudaGraphExecDestroy(kv.second.b);
+    }
+    solve_graphs.clear();
+  }
   void* rpool = nullptr;
   void* lam_work = nullptr;
   double2 *d_f = nullptr, *d_u = nullptr, *d_r = nullptr, *d_du = nullptr;
@@ -183,6 +202,8 @@ struct dd_handle {
   int launches = 0;
 
   ~dd_handle() {
+    if (factor_exec) cudaGraphExecDestroy(factor_exec);
+    drop_solve_graphs();
     for (void* q : work_ptrs) cudaFree(q);
     if (d_sub) cudaFree(d_sub);
     arena.release();
@@ -192,6 +213,7 @@ struct dd_handle {
     if (ev_panel) cudaEventDestroy(ev_panel);
     if (ev_rest) cudaEventDestroy(ev_rest);
     if (s2) cudaStreamDestroy(s2);
+    if (own_stream) cudaStreamDestroy(own_stream);
   }
 };
 
@@ -320,6 +342,7 @@ void add_flops(dd_handle* h, double ne, double nu, double n_gamma, bool leaf) {
 
 int ensure_work(dd_handle* h, int nrhs) {
   if (nrhs <= h->nrhs_cap) return DD_OK;
+  h->drop_solve_graphs();   // they refer to the buffers freed here
   for (void* q : h->work_ptrs) cudaFree(q);
   h->work_ptrs.clear();
   h->nrhs_cap = 0;
@@ -361,7 +384,10 @@ void direct_solve(dd_handle* h, int nrhs, const double2* f, int64_t ldf, const d
                   const LeafSubset* sub = nullptr) {
   cudaStream_t s = h->stream;
   const int p = h->prec == DD_PREC_FP64 ? 0 : 1;
-  const int ep = ++h->epoch;
+  // ready flags restart from zero every solve, so a captured solve replays unchanged
+  cudaMemsetAsync(h->d_flag_f, 0, sizeof(int32_t) * std::max<int64_t>(h->n_tiles, 1), s);
+  cudaMemsetAsync(h->d_flag_b, 0, sizeof(int32_t) * std::max<int64_t>(h->n_tiles, 1), s);
+  const int ep = 1;
   ddk::launch_rhs_leaf(p, h->rpool, h->d_fronts, h->d_leaves, h->n_sub, h->d_perm, f, ldf, nrhs, s);
   h->launches += 1;
   for (size_t l = 0; l < h->levels.size(); ++l) {
@@ -392,6 +418,12 @@ void direct_solve(dd_handle* h, int nrhs, const double2* f, int64_t ldf, const d
     ddk::launch_leaf_out(p, h->rpool, h->d_fronts, h->d_leaves, h->n_sub, h->d_perm, u, h->n_loc, nrhs, 0, s);
   ddk::launch_lam_out(p, h->lam_work, h->n_dual, h->n_dual, nrhs, lam, h->n_dual, 0, s);
   h->launches += 2;
+}
+
+__global__ void k_status_init(DevStatus* st) {
+  DevStatus z{};
+  z.min_abs_d = 0x7FF0000000000000ull;   // +inf
+  *st = z;
 }
 
 // rows of listed domains: segment q copies rows [seg[3q], seg[3q] + seg[3q+2]) of
@@ -931,6 +963,14 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
   }
   if (h->use_tc) DD_CUDA(A.alloc(&h->d_ws, h->ws_bytes));
   DD_CUDA(cudaStreamCreateWithFlags(&h->s2, cudaStreamNonBlocking));
+  // the legacy default stream cannot be captured into a graph: without a caller
+  // stream the handle works on its own blocking stream, which is ordered with
+  // the legacy stream like the legacy stream itself
+  if (!h->stream) {
+    DD_CUDA(cudaStreamCreate(&h->own_stream));
+    h->stream = h->own_stream;
+    s = h->stream;
+  }
   DD_CUDA(cudaEventCreateWithFlags(&h->ev_panel, cudaEventDisableTiming));
   DD_CUDA(cudaEventCreateWithFlags(&h->ev_rest, cudaEventDisableTiming));
   // mixed form: L^{-1} of every diagonal tile (panel products and the substitution)
@@ -977,24 +1017,17 @@ int dd_set_values(dd_handle* h, const dd_c128* vals) {
   return cuda_status(e);
 }
 
-int dd_factor(dd_handle* h) {
-  if (!h) return DD_ERR_INVALID_ARG;
-  int cur = 0;
-  cudaGetDevice(&cur);
-  cudaSetDevice(h->device);
-  struct Restore { int d; ~Restore() { cudaSetDevice(d); } } restore{cur};
-  cudaStream_t s = h->stream;
-  h->factored = false;
+// Enqueues one numeric factorization on stream s (and the look-ahead stream):
+// the same launch sequence every call, so it can be captured once as a CUDA
+// graph.  With time_kernels, event pairs around every launch (not captured).
+static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& nev, std::vector<int>& cls_of) {
   const int p = h->prec == DD_PREC_FP64 ? 0 : 1;
-  DevStatus st0{};
-  st0.min_abs_d = 0x7FF0000000000000ull;  // +inf
-  DD_CUDA(cudaEventRecord(h->ev0, s));
-  DD_CUDA(cudaMemcpyAsync(h->d_status, &st0, sizeof(st0), cudaMemcpyHostToDevice, s));
-  int launches = 0;
+  k_status_init<<<1, 1, 0, s>>>(h->d_status);
+  launches = 0;
   // optional per-launch timing: an event pair around every launch of a class
   constexpr size_t kMaxTimed = 8192;
-  size_t nev = 0;
-  std::vector<int> cls_of(h->time_kernels ? kMaxTimed : 0);
+  nev = 0;
+  cls_of.assign(h->time_kernels ? kMaxTimed : 0, 0);
   auto mark_on = [&](int cls, bool begin, cudaStream_t on) -> cudaError_t {
     if (!h->time_kernels || nev >= 2 * kMaxTimed) return cudaSuccess;
     if (begin) cls_of[nev / 2] = cls;
@@ -1004,7 +1037,8 @@ int dd_factor(dd_handle* h) {
       if (err != cudaSuccess) return err;
       h->kev.push_back(e);
     }
-    return cudaEventRecord(h->kev[nev++], on);
+    // inside stream capture this becomes an event-record node of the graph
+    return cudaEventRecordWithFlags(h->kev[nev++], on, cudaEventRecordExternal);
   };
   auto mark = [&](int cls, bool begin) { return mark_on(cls, begin, s); };
   for (int c = 0; c < DD_K_NCLASS; ++c) {
@@ -1142,6 +1176,9 @@ int dd_factor(dd_handle* h) {
       // the far part of each two-panel update runs on the second stream while
       // the main stream forms the next two panels; before touching columns the
       // far part also updates, the main stream waits for it
+      // the second stream joins here (also inside graph capture), with nothing pending
+      DD_CUDA(cudaEventRecord(h->ev_panel, s));
+      DD_CUDA(cudaStreamWaitEvent(h->s2, h->ev_panel, 0));
       DD_CUDA(cudaEventRecord(h->ev_rest, h->s2));
       DD_CUDA(panel(L.steps[0]));
       for (size_t q = 0; q < ns;) {
@@ -1171,6 +1208,44 @@ int dd_factor(dd_handle* h) {
     }
   }
   DD_CUDA(cudaGetLastError());
+  return DD_OK;
+}
+
+int dd_factor(dd_handle* h) {
+  if (!h) return DD_ERR_INVALID_ARG;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  cudaSetDevice(h->device);
+  struct Restore { int d; ~Restore() { cudaSetDevice(d); } } restore{cur};
+  cudaStream_t s = h->stream;
+  h->factored = false;
+  // the whole factorization as one CUDA graph, captured on the first call
+  // (with time_kernels the graph also records an event pair around every launch)
+  if (!h->factor_exec) {
+    int launches = 0;
+    DD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    const int st = enqueue_factor(h, s, launches, h->fact_nev, h->fact_cls);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (st != DD_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return st != DD_OK ? st : cuda_status(e);
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&h->factor_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      h->factor_exec = nullptr;
+      return cuda_status(ei);
+    }
+    h->factor_graph_launches = launches;
+  }
+  const int launches = h->factor_graph_launches;
+  const size_t nev = h->fact_nev;
+  const std::vector<int>& cls_of = h->fact_cls;
+  DD_CUDA(cudaEventRecord(h->ev0, s));
+  DD_CUDA(cudaGraphLaunch(h->factor_exec, s));
+  DD_CUDA(cudaGetLastError());
   DD_CUDA(cudaEventRecord(h->ev1, s));
   DevStatus st{};
   DD_CUDA(cudaMemcpyAsync(&st, h->d_status, sizeof(st), cudaMemcpyDeviceToHost, s));
@@ -1179,6 +1254,7 @@ int dd_factor(dd_handle* h) {
   cudaEventElapsedTime(&ms, h->ev0, h->ev1);
   h->stats.t_factor_ms = ms;
   h->stats.launches_factor = launches;
+  for (int c = 0; c < DD_K_NCLASS; ++c) h->stats.kernel_ms[c] = 0.0;
   for (size_t q = 0; q + 1 < nev; q += 2) {
     float dt = 0.f;
     if (cudaEventElapsedTime(&dt, h->kev[q], h->kev[q + 1]) == cudaSuccess) h->stats.kernel_ms[cls_of[q / 2]] += dt;
@@ -1360,10 +1436,59 @@ static int solve_block(dd_handle* h, int32_t nrhs, const dd_c128* f, int64_t ldf
   if (st != DD_OK) return st;
   h->launches = 0;
   const size_t row_b = (size_t)h->n_loc * 16;
+  const int64_t nu_el = h->n_loc * (int64_t)nrhs;
+  const int64_t nl_el = (int64_t)h->n_dual * nrhs;
+  // the direct solve (a) and one refinement step (b) are captured once per
+  // right-hand-side count and replayed; the host only reads the norms between steps
+  dd_handle::SolveGraphs& gr = h->solve_graphs[nrhs];
+  auto capture = [&](auto&& body, cudaGraphExec_t* out, int* launches) -> int {
+    h->launches = 0;
+    DD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    body();
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      return cuda_status(e);
+    }
+    const cudaError_t ei = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      *out = nullptr;
+      return cuda_status(ei);
+    }
+    *launches = h->launches;
+    return DD_OK;
+  };
+  if (!gr.a) {
+    const int c = capture([&] { direct_solve(h, nrhs, h->d_f, h->n_loc, nullptr, h->d_u, h->d_lam); }, &gr.a, &gr.la);
+    if (c != DD_OK) return c;
+  }
+  if (h->max_refine > 0 && !gr.b) {
+    const int c = capture(
+        [&] {
+          ddk::launch_residual(h->d_leaves, h->n_sub, h->d_rowptr, h->d_colind, h->d_val, h->d_blptr, h->d_bldual,
+                               h->d_blsign, h->d_f, h->n_loc, h->d_u, h->n_loc, h->d_lam, h->n_dual, h->d_r,
+                               h->n_loc, nrhs, s);
+          ddk::launch_dual_residual(h->n_dual, h->d_btptr, h->d_btrow, h->d_btsign, h->d_u, h->n_loc, h->d_g,
+                                    h->n_dual, nrhs, s);
+          direct_solve(h, nrhs, h->d_r, h->n_loc, h->d_g, h->d_du, h->d_dlam);
+          ddk::launch_sumsq_cols(h->d_du, h->n_loc, nrhs, kNormBlocks, h->d_partials, s);
+          ddk::launch_sumsq_cols(h->d_u, h->n_loc, nrhs, kNormBlocks, h->d_partials + kSolveBlock * kNormBlocks, s);
+          k_axpy<<<1024, 256, 0, s>>>(h->d_u, h->d_du, nu_el);
+          if (nl_el) k_axpy<<<256, 256, 0, s>>>(h->d_lam, h->d_dlam, nl_el);
+          h->launches += 6;
+        },
+        &gr.b, &gr.lb);
+    if (c != DD_OK) return c;
+  }
+  h->launches = 0;
   DD_CUDA(cudaEventRecord(h->ev0, s));
   DD_CUDA(cudaMemcpy2DAsync(h->d_f, row_b, f, (size_t)ldf * 16, row_b, nrhs,
                             is_device_ptr(f) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-  direct_solve(h, nrhs, h->d_f, h->n_loc, nullptr, h->d_u, h->d_lam);
+  DD_CUDA(cudaGraphLaunch(gr.a, s));
+  h->launches += gr.la;
   int iters = 0;
   double ratio = 0.0;
   int status = DD_OK;
@@ -1371,20 +1496,9 @@ static int solve_block(dd_handle* h, int32_t nrhs, const dd_c128* f, int64_t ldf
   // solve itself is the first correction (from zero), of relative size 1
   double prev_col[kSolveBlock];
   for (int j = 0; j < kSolveBlock; ++j) prev_col[j] = 1.0;
-  const int64_t nu_el = h->n_loc * (int64_t)nrhs;
-  const int64_t nl_el = (int64_t)h->n_dual * nrhs;
   for (int it = 0; it < h->max_refine; ++it) {
-    ddk::launch_residual(h->d_leaves, h->n_sub, h->d_rowptr, h->d_colind, h->d_val, h->d_blptr, h->d_bldual,
-                         h->d_blsign, h->d_f, h->n_loc, h->d_u, h->n_loc, h->d_lam, h->n_dual, h->d_r, h->n_loc,
-                         nrhs, s);
-    ddk::launch_dual_residual(h->n_dual, h->d_btptr, h->d_btrow, h->d_btsign, h->d_u, h->n_loc, h->d_g, h->n_dual,
-                              nrhs, s);
-    direct_solve(h, nrhs, h->d_r, h->n_loc, h->d_g, h->d_du, h->d_dlam);
-    ddk::launch_sumsq_cols(h->d_du, h->n_loc, nrhs, kNormBlocks, h->d_partials, s);
-    ddk::launch_sumsq_cols(h->d_u, h->n_loc, nrhs, kNormBlocks, h->d_partials + kSolveBlock * kNormBlocks, s);
-    k_axpy<<<1024, 256, 0, s>>>(h->d_u, h->d_du, nu_el);
-    if (nl_el) k_axpy<<<256, 256, 0, s>>>(h->d_lam, h->d_dlam, nl_el);
-    h->launches += 6;
+    DD_CUDA(cudaGraphLaunch(gr.b, s));
+    h->launches += gr.lb;
     double part[2 * kSolveBlock * kNormBlocks];
     DevStatus sst{};
     DD_CUDA(cudaMemcpyAsync(part, h->d_partials, sizeof(part), cudaMemcpyDeviceToHost, s));
