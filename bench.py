@@ -214,6 +214,9 @@ def time_form(p, precision, args, torch, stream):
     s = dd.Solver.from_problem(p, precision=precision, stream=stream.cuda_stream, device=torch.cuda.current_device(),
                                time_kernels=not args.no_kernel_timing, refine_tol=args.refine_tol,
                                pivoting=args.pivoting, update_panels=args.update_panels)
+    sched = None
+    if precision == "mixed" and not args.no_autotune:
+        sched = s.autotune(repeats=2)      # untimed: picks the factor schedule for this workload
     f_host = dd.stacked_loads(p)
     f_dev = torch.from_numpy(f_host).cuda()
     for _ in range(args.warmup):
@@ -251,7 +254,7 @@ def time_form(p, precision, args, torch, stream):
     u_host = u.cpu().numpy()
     res = {"ms_per_step": ms / args.steps, "stats": st, "kernel_ms": kms, "kernel_launches": kl,
            "kernel_flops": kfl, "launches": launches, "refine_iters": iters,
-           "backward_error": backward_error(p, u_host), "clocks": clk.summary()}
+           "backward_error": backward_error(p, u_host), "clocks": clk.summary(), "schedule": sched}
 
     # end to end through the C ABI with host buffers: new values + factor + solve
     if not args.no_e2e:
@@ -338,6 +341,7 @@ def ours_arm(args):
         "config": {"workload": WORKLOADS[args.workload][1], "form": args.precision, "n_dofs": p.n,
                    "n_domains": p.n_sub, "n_duals": p.n_dual, "nrhs": p.nrhs, "pivoting": args.pivoting,
                    "update_panels": args.update_panels,
+                   "schedule": main.get("schedule"),
                    "l2": "working set (front pool) far larger than the 129 MB L2",
                    "parallelism": f"replicas x{ws}"},
         "tflops": flops_step / t_step / 1e12,
@@ -390,6 +394,7 @@ def main():
                     help="restricted Bunch-Kaufman: 0 none, 1 auxiliary fronts, 2 every front")
     ap.add_argument("--update-panels", type=int, default=2, choices=[1, 2],
                     help="mixed form: panels fused per tensor-core trailing-update pass")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default factor schedule")
     ap.add_argument("--no-kernel-timing", action="store_true",
                     help="no per-launch CUDA events (no kernel breakdown or roofline)")
     ap.add_argument("--refine-tol", type=float, default=1e-11,

@@ -138,6 +138,15 @@ typedef struct {
   int64_t pivots_2x2;        /* pivoting: 2 x 2 pivot blocks in the last dd_factor */
 } dd_stats;
 
+/* Schedule of the tensor-core factorization path (MIXED form). */
+typedef struct {
+  int32_t update_panels;  /* panels fused per trailing-update pass: 1 or 2 */
+  int32_t ahead_fronts;   /* one-step look-ahead on tree levels with at most this many fronts (0: none) */
+  int32_t reserve_sms;    /* SMs the look-ahead update leaves to the panel chain */
+  double factor_ms;       /* dd_autotune: device time of one dd_factor with this schedule */
+  int32_t configs_tried;  /* dd_autotune: schedules timed */
+} dd_schedule;
+
 /* Fill `opt` with defaults (FP64, no tree, default stream, device 0). */
 int dd_default_options(dd_options* opt);
 
@@ -156,6 +165,21 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
  * holds sum_i rowptr_i[n_i] complex values, domain after domain, host or
  * device memory (detected).  The handle becomes unfactored. */
 int dd_set_values(dd_handle* h, const dd_c128* vals);
+
+/* Set the schedule of the tensor-core path (update_panels 1 or 2, ahead_fronts
+ * in [0, 128], reserve_sms in [0, 64]); factor_ms and configs_tried are ignored.
+ * The factors already computed stay valid; the next dd_factor uses the new
+ * schedule.  No effect in the FP64 form or with simt_update.
+ * DD_ERR_INVALID_ARG for values out of range. */
+int dd_set_schedule(dd_handle* h, const dd_schedule* sched);
+
+/* Autotuner: times dd_factor (the minimum over `repeats` runs each) under every
+ * schedule of the grid update_panels {1, 2} x ahead_fronts {0, 8, 32, 128} x
+ * reserve_sms {8, 16, 32} (look-ahead off: reserve not varied), keeps the
+ * fastest for this handle and returns it in *out; the handle is left factored
+ * with it.  FP64 form / simt_update: one dd_factor, configs_tried = 1.
+ * Errors: as dd_factor; DD_ERR_INVALID_ARG for repeats < 1 or out == NULL. */
+int dd_autotune(dd_handle* h, int32_t repeats, dd_schedule* out);
 
 /* Numeric factorization (Section II): A_i = L_i D_i L_i^T for every domain
  * together with its Schur contribution -F_i, assembly of the auxiliary matrix

@@ -65,7 +65,13 @@ class Stats(C.Structure):
                 ("interchanges", C.c_int64), ("pivots_2x2", C.c_int64)]
 
 
+class Schedule(C.Structure):
+    _fields_ = [("update_panels", C.c_int32), ("ahead_fronts", C.c_int32), ("reserve_sms", C.c_int32),
+                ("factor_ms", C.c_double), ("configs_tried", C.c_int32)]
+
+
 EXPORTS = ["dd_default_options", "dd_setup", "dd_set_values", "dd_factor", "dd_solve", "dd_solve_subset", "dd_get_schur",
+           "dd_set_schedule", "dd_autotune",
            "dd_get_stats", "dd_strerror", "dd_free", "dd_dense_solve_noalloc", "dd_selftest_wait_timeout"]
 
 
@@ -94,6 +100,8 @@ def load(build_if_missing: bool = True):
                                     C.c_void_p, C.c_int64, C.c_void_p, C.c_int64]
     lib.dd_get_schur.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     lib.dd_get_stats.argtypes = [C.c_void_p, C.POINTER(Stats)]
+    lib.dd_set_schedule.argtypes = [C.c_void_p, C.POINTER(Schedule)]
+    lib.dd_autotune.argtypes = [C.c_void_p, C.c_int32, C.POINTER(Schedule)]
     lib.dd_strerror.argtypes = [C.c_int]
     lib.dd_strerror.restype = C.c_char_p
     lib.dd_free.argtypes = [C.c_void_p]
@@ -224,6 +232,17 @@ class Solver:
         _check(code, "dd_solve", ok)
         self.last_status = code
         return (uo[:, 0], lo[:, 0]) if vec else (uo, lo)
+
+    def autotune(self, repeats: int = 2) -> dict:
+        """Time dd_factor under each schedule of the tensor-core path, keep the fastest
+        (the handle is left factored with it); returns the chosen schedule."""
+        sc = Schedule()
+        _check(_lib.dd_autotune(self._h, int(repeats), C.byref(sc)), "dd_autotune")
+        return {k: getattr(sc, k) for k, _ in Schedule._fields_}
+
+    def set_schedule(self, update_panels: int, ahead_fronts: int, reserve_sms: int):
+        sc = Schedule(int(update_panels), int(ahead_fronts), int(reserve_sms), 0.0, 0)
+        _check(_lib.dd_set_schedule(self._h, C.byref(sc)), "dd_set_schedule")
 
     def solve_subset(self, f, domains, allow_not_converged: bool = False):
         """Solve for the stacked local loads f (numpy, n_loc x nrhs) and recover only

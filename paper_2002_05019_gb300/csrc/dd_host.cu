@@ -30,6 +30,7 @@ namespace {
 
 constexpr int T = DD_TILE;
 constexpr int kSolveBlock = 64;   // right-hand sides per direct-solve pass
+constexpr int kAheadMaxFronts = 128;   // look-ahead is possible on levels with at most this many fronts
 constexpr int kNormBlocks = 16;   // reduction blocks per column for the refinement norms
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
@@ -166,6 +167,9 @@ struct dd_handle {
   size_t ws_bytes = 0;
   int use_tc = 0;
   bool pair_panels = false;        // two-panel trailing updates (K = 128)
+  // schedule knobs of the tensor-core path (dd_autotune picks them)
+  int ahead_fronts = 32;           // look-ahead on levels with at most this many fronts (0: off)
+  int reserve_sms = 16;            // SMs the look-ahead leaves to the panel chain
   int32_t *d_flag_f = nullptr, *d_flag_b = nullptr;
   int64_t n_tiles = 0;
   int epoch = 0;
@@ -757,7 +761,7 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
         F.ws_boff = w;
         w += ntr * (int64_t)DD_TC_BTILE;
       }
-      L.ahead = L.ids.size() <= 32;
+      L.ahead = L.ids.size() <= (size_t)kAheadMaxFronts;   // may look ahead (image slots 2, 3)
       need = std::max(need, (size_t)w);
       if (L.ahead) need_ahead = std::max(need_ahead, (size_t)w);
     }
@@ -859,7 +863,7 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
     }
     // two-panel updates: column pairs never straddle the first update-row
     // tile, so both columns of a task share their structurally zero panels
-    if (h->pair_panels)
+    if (h->use_tc)   // built for the tensor-core path whatever update_panels says (dd_autotune)
       for (int k = 0; k + 1 < max_steps; k += 2) {
         PairRange P{};
         P.k = k;
@@ -1077,8 +1081,8 @@ static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& n
     // one-step look-ahead on levels with few fronts: the main stream updates
     // only the next panel columns and factors those panels, while the second
     // stream applies the rest of the trailing update
-    const bool ahead = h->use_tc && L.ahead && L.steps.size() > 1;
-    const int reserve = ahead ? 16 : 0;   // SMs left free for the panel chain
+    const bool ahead = h->use_tc && L.ahead && (int)L.ids.size() <= h->ahead_fronts && L.steps.size() > 1;
+    const int reserve = ahead ? h->reserve_sms : 0;   // SMs left free for the panel chain
     // image slot of panel k: even / odd panels alternate, the look-ahead levels over four slots
     auto wsp = [&](int k) -> unsigned char* { return h->d_ws + h->ws_slot_off[ahead ? (k & 3) : (k & 1)]; };
     auto panel = [&](const StepRange& R) -> cudaError_t {
@@ -1271,6 +1275,62 @@ int dd_factor(dd_handle* h) {
   if (st.code != 0) return DD_ERR_SINGULAR_PIVOT;
   h->factored = true;
   return DD_OK;
+}
+
+int dd_set_schedule(dd_handle* h, const dd_schedule* sc) {
+  if (!h || !sc) return DD_ERR_INVALID_ARG;
+  if ((sc->update_panels != 1 && sc->update_panels != 2) || sc->ahead_fronts < 0 ||
+      sc->ahead_fronts > kAheadMaxFronts || sc->reserve_sms < 0 || sc->reserve_sms > 64)
+    return DD_ERR_INVALID_ARG;
+  if (!h->use_tc) return DD_OK;
+  h->pair_panels = sc->update_panels == 2;
+  h->ahead_fronts = sc->ahead_fronts;
+  h->reserve_sms = sc->reserve_sms;
+  if (h->factor_exec) cudaGraphExecDestroy(h->factor_exec);   // recaptured by the next dd_factor
+  h->factor_exec = nullptr;
+  h->fact_nev = 0;
+  h->fact_cls.clear();
+  return DD_OK;
+}
+
+int dd_autotune(dd_handle* h, int32_t repeats, dd_schedule* out) {
+  if (!h || !out || repeats < 1) return DD_ERR_INVALID_ARG;
+  auto time_it = [&](double* best) -> int {
+    *best = 1e300;
+    for (int r = 0; r < repeats; ++r) {
+      const int st = dd_factor(h);
+      if (st != DD_OK) return st;
+      *best = std::min(*best, h->stats.t_factor_ms);
+    }
+    return DD_OK;
+  };
+  dd_schedule cur{h->pair_panels ? 2 : 1, h->ahead_fronts, h->reserve_sms, 0.0, 0};
+  if (!h->use_tc) {
+    const int st = time_it(&cur.factor_ms);
+    cur.configs_tried = 1;
+    *out = cur;
+    return st;
+  }
+  std::vector<dd_schedule> grid;
+  for (int panels : {1, 2})
+    for (int ahead : {0, 8, 32, 128})
+      for (int reserve : {8, 16, 32}) {
+        if (ahead == 0 && reserve != 16) continue;   // no look-ahead: the reserve is unused
+        grid.push_back(dd_schedule{panels, ahead, reserve, 0.0, 0});
+      }
+  dd_schedule best = cur;
+  best.factor_ms = 1e300;
+  for (dd_schedule& c : grid) {
+    int st = dd_set_schedule(h, &c);
+    if (st == DD_OK) st = time_it(&c.factor_ms);
+    if (st != DD_OK) return st;
+    if (c.factor_ms < best.factor_ms) best = c;
+  }
+  best.configs_tried = (int32_t)grid.size();
+  int st = dd_set_schedule(h, &best);
+  if (st == DD_OK) st = dd_factor(h);
+  *out = best;
+  return st;
 }
 
 static int solve_block(dd_handle* h, int32_t nrhs, const dd_c128* f, int64_t ldf, dd_c128* u, int64_t ldu,

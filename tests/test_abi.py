@@ -61,6 +61,8 @@ def test_null_handles_are_rejected():
     assert lib.dd_factor(None) == 1
     assert lib.dd_solve(None, 1, None, 1, None, 1, None, 1) == 1
     assert lib.dd_solve_subset(None, 1, None, 1, 0, None, None, 1, None, 1) == 1
+    assert lib.dd_autotune(None, 1, None) == 1
+    assert lib.dd_set_schedule(None, None) == 1
     assert lib.dd_get_stats(None, None) == 1
 
 
