@@ -143,22 +143,11 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_forward(const S* pool, S* rpo
   // restricted Bunch-Kaufman: the tile's right-hand side is permuted (P_i) before its solve
   const bool pv = piv != nullptr && F.piv != 0 && i < nte;
   if (pv && threadIdx.x < T) perm[threadIdx.x] = piv[((int64_t)F.tile_off + i) * T + threadIdx.x];
-  // the tile's own diagonal block (L_ii, or L_ii^{-1} when given) goes to shared
-  // memory before any wait, so it is off the dependency chain
-  if (i < nte) {
+  if (i < nte && Li == nullptr) {
     for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
       const int rr = idx / T, c = idx % T;
-      if (c <= rr) Lt[tri(rr, c)] = Li ? Li[rr * T + c] : L[(r0 + rr) * ld + r0 + c];
+      if (c <= rr) Lt[tri(rr, c)] = L[(r0 + rr) * ld + r0 + c];
     }
-  }
-  // the L block of the last tile this one waits for (the chain's predecessor), read ahead
-  constexpr bool kPre = sizeof(S) == 8;   // FP32 form only: keeps the FP64 kernel's registers
-  S pre[2][RW];
-  if (kPre && kmax > 0) {
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-      for (int q = 0; q < RW; ++q) pre[h][q] = L[(r0 + warp * RW + q) * ld + (kmax - 1) * T + lane + 32 * h];
   }
   for (int j = 0; j < nrhs; ++j) {
     S acc[RW];
@@ -167,15 +156,6 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_forward(const S* pool, S* rpo
     for (int k = 0; k < kmax; ++k) {
       if (j == 0 && !wait_ready(flg + k, epoch, st, t.f, k)) return;
       const int c0 = k * T;
-      if (kPre && k == kmax - 1) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const S zc = ldcg(z + (int64_t)(c0 + lane + 32 * h) * nrhs + j);
-#pragma unroll
-          for (int q = 0; q < RW; ++q) acc[q] = cfma(pre[h][q], zc, acc[q]);
-        }
-        continue;
-      }
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int c = c0 + lane + 32 * h;
@@ -204,7 +184,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_forward(const S* pool, S* rpo
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const int c = part * 16 + q;
-        if (c <= row) acc = cfma(Lt[tri(row, c)], zi[c], acc);
+        if (c <= row) acc = cfma(Li[row * T + c], zi[c], acc);
       }
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
       acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
@@ -268,20 +248,13 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rp
   constexpr int NG = SOLVE_THREADS / T;
   int32_t* flg = flags + F.tile_off;
   const S* Li = linv != nullptr ? linv + ((int64_t)F.tile_off + j) * T * T : nullptr;
-  __shared__ S dvals[T];   // the pivots d (the diagonal of Lt holds L_jj^{-1}'s 1 with an inverse)
-  // the tile's own diagonal block (L_jj, or L_jj^{-1} when given) goes to shared
-  // memory before any wait, so it is off the dependency chain
-  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
-    const int rr = idx / T, c = idx % T;
-    if (c <= rr) Lt[tri(rr, c)] = Li ? Li[rr * T + c] : L[(c0 + rr) * ld + c0 + c];
-  }
-  if (threadIdx.x < T) dvals[threadIdx.x] = L[(c0 + threadIdx.x) * (ld + 1)];
-  // the L block of the last tile this one waits for (tile j + 1), read ahead
-  constexpr bool kPre = sizeof(S) == 8;   // FP32 form only: keeps the FP64 kernel's registers
-  S pre[T / NG];
-  if (kPre && j + 1 < nte) {
-#pragma unroll
-    for (int q = 0; q < T / NG; ++q) pre[q] = L[((j + 1) * T + grp + NG * q) * ld + c0 + col];
+  if (Li == nullptr) {
+    for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+      const int rr = idx / T, c = idx % T;
+      if (c <= rr) Lt[tri(rr, c)] = L[(c0 + rr) * ld + c0 + c];
+    }
+  } else if (threadIdx.x < T) {
+    Lt[tri(threadIdx.x, threadIdx.x)] = L[(c0 + threadIdx.x) * (ld + 1)];   // the pivots d
   }
   const bool pv = piv != nullptr && F.piv != 0;
   if (pv && threadIdx.x < T) {
@@ -299,11 +272,6 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rp
       acc = cfma(L[(F.ne_pad + u) * ld + c0 + col], ldcg(lam + upd[F.upd_off + u] + jj * ld_lam), acc);
     for (int i = nte - 1; i > j; --i) {
       if (jj == 0 && !wait_ready(flg + i, epoch, st, t.f, i)) return;
-      if (kPre && i == j + 1) {
-#pragma unroll
-        for (int q = 0; q < T / NG; ++q) acc = cfma(pre[q], ldcg(z + (int64_t)(i * T + grp + NG * q) * nrhs + jj), acc);
-        continue;
-      }
 #pragma unroll
       for (int rr = grp; rr < T; rr += NG) {
         const int r = i * T + rr;
@@ -321,7 +289,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rp
         const S zq = ldcg(z + (int64_t)(c0 + qs[threadIdx.x]) * nrhs + jj);
         yj[threadIdx.x] = csub(cfma(zq, g1s[threadIdx.x], cmul(zc, g0s[threadIdx.x])), sum);
       } else {
-        yj[threadIdx.x] = csub(cdiv(zc, dvals[threadIdx.x]), sum);
+        yj[threadIdx.x] = csub(cdiv(zc, Lt[tri(threadIdx.x, threadIdx.x)]), sum);
       }
     }
     __syncthreads();
@@ -332,7 +300,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rp
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const int r = part * 16 + q;
-        if (r >= col2) acc = cfma(Lt[tri(r, col2)], yj[r], acc);
+        if (r >= col2) acc = cfma(Li[r * T + col2], yj[r], acc);
       }
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
       acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
