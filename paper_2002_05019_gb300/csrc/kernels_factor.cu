@@ -240,7 +240,11 @@ __device__ __forceinline__ double2 crcp(double2 d) {
   const double s = 1.0 / (d.x * d.x + d.y * d.y);
   return make_double2(d.x * s, -d.y * s);
 }
-__device__ __forceinline__ float2 crcp(float2 d) { return cdiv(make_float2(1.f, 0.f), d); }
+// FP32 pivots: |d|^2 stays in range for pivots between about 1e-19 and 1e19
+__device__ __forceinline__ float2 crcp(float2 d) {
+  const float s = 1.f / (d.x * d.x + d.y * d.y);
+  return make_float2(d.x * s, -d.y * s);
+}
 
 // element e of a column-descending enumeration of the update set of a 32 x 32
 // block: columns c = 31, 30, ..., 1, rows r = c..31 within each, so the
