@@ -582,20 +582,21 @@ __global__ void __launch_bounds__(256) k_trsm_mx(float2* pool, const FrontDev* f
       for (int c = 0; c < 4; ++c) Xs[ty + 16 * r][tx + 16 * c] = acc[r][c];
     __syncthreads();
   }
-  double mx = 0.0;
+  // growth statistic in FP32 (the FP64 pipe is ~1/64 of FP32 on this part): max |l d|^2
+  float mx = 0.f;
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       const int rr = ty + 16 * r, p = tx + 16 * c;
       const float2 x = acc[r][c];
-      mx = fmax(mx, cabs2d(x));
+      mx = fmaxf(mx, x.x * x.x + x.y * x.y);
       const float2 lv = pv ? cfma(Xs[rr][qc[p]], g1[p], cmul(x, rinv[p])) : cmul(x, rinv[p]);
       Aik[(int64_t)rr * ld + p] = lv;
       if (ws) write_images<float2>(ws, F, t.i - k - 1, rr * T + p, lv, x);
     }
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0 && mx > 0.0 && isfinite(mx)) atomic_max_pos(&st->max_abs_l, sqrt(mx));
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx > 0.f && isfinite(mx)) atomic_max_pos(&st->max_abs_l, sqrt((double)mx));
 }
 
 // ---------------------------------------------------------------------------
