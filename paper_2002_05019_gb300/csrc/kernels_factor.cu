@@ -737,24 +737,28 @@ __global__ void __launch_bounds__(256) k_update(S* pool, const FrontDev* fr, con
 // injective), and the two children are added in two launches in a fixed
 // order, so the assembly is deterministic without atomics.
 // ---------------------------------------------------------------------------
+// one warp per row of the child's trailing block (lower triangle), eight rows
+// per CTA: each warp reads its row contiguously and adds it into the parent
+// rows given by the map (grid.y covers the largest child of the level)
 template <typename S>
-__global__ void k_extend_add(S* pool, const FrontDev* fr, const int32_t* nodes, int slot, const int32_t* maps) {
+__global__ void __launch_bounds__(256) k_extend_add(S* pool, const FrontDev* fr, const int32_t* nodes, int slot,
+                                                    const int32_t* maps) {
   const FrontDev P = fr[nodes[blockIdx.x]];
   const int c = P.child[slot];
   if (c < 0) return;
   const FrontDev Cf = fr[c];
+  const int a = blockIdx.y * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (a >= Cf.nu) return;
   const int32_t* map = maps + P.map_off[slot];
-  const S* src = pool + Cf.off + (int64_t)Cf.ne_pad * Cf.ld + Cf.ne_pad;
+  const S* src = pool + Cf.off + (int64_t)(Cf.ne_pad + a) * Cf.ld + Cf.ne_pad;
   S* dst = pool + P.off;
-  for (int a = blockIdx.y; a < Cf.nu; a += gridDim.y) {
-    const int ra = map[a];
-    for (int b = threadIdx.x; b <= a; b += blockDim.x) {
-      const int rb = map[b];
-      const S v = src[(int64_t)a * Cf.ld + b];
-      const int hi = ra > rb ? ra : rb, lo = ra > rb ? rb : ra;
-      S* p = dst + (int64_t)hi * P.ld + lo;
-      *p = cadd(*p, v);
-    }
+  const int ra = map[a];
+  for (int b = lane; b <= a; b += 32) {
+    const int rb = map[b];
+    const S v = src[b];
+    const int hi = ra > rb ? ra : rb, lo = ra > rb ? rb : ra;
+    S* p = dst + (int64_t)hi * P.ld + lo;
+    *p = cadd(*p, v);
   }
 }
 
@@ -835,7 +839,7 @@ void launch_update(int prec, void* pool, const FrontDev* fronts, const Task* tas
 void launch_extend_add(int prec, void* pool, const FrontDev* fronts, const int32_t* node_ids, int n, int slot,
                        const int32_t* maps, int max_nu, cudaStream_t s) {
   if (n <= 0 || max_nu <= 0) return;
-  dim3 grid(n, max_nu < 256 ? max_nu : 256);
+  dim3 grid(n, (max_nu + 7) / 8);
   if (prec == 0) k_extend_add<double2><<<grid, 256, 0, s>>>((double2*)pool, fronts, node_ids, slot, maps);
   else k_extend_add<float2><<<grid, 256, 0, s>>>((float2*)pool, fronts, node_ids, slot, maps);
 }
