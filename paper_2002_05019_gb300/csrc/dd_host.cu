@@ -119,6 +119,7 @@ struct dd_handle {
   std::vector<FrontDev> fronts;
   std::vector<Level> levels;
   std::vector<std::vector<int32_t>> leaf_duals;  // sorted duals of each domain
+  std::vector<std::vector<int32_t>> leaf_upd;    // the same duals in the front's B-row order
   std::vector<int64_t> leaf_vec_off;
   std::vector<LeafDev> h_leaves_copy;   // for subset recovery
   std::vector<Task> h_bwd_leaf;         // level-0 backward tasks (front, tile)
@@ -722,6 +723,57 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
     if (par[v] < 0 && F.nu != 0) return DD_ERR_INVALID_ARG;
     add_flops(h.get(), F.ne, F.nu, 0, false);
     h->stats.max_front = std::max(h->stats.max_front, F.ld);
+  }
+
+  // ---- update-row order: every front's update rows follow its parent's row
+  // order, so each extend-add map is increasing and a child's block lands in
+  // its parent row by row, in order (coalesced, never transposed) ----------------
+  {
+    std::vector<int32_t> rowpos(std::max(n_dual, 1), -1);
+    std::vector<int> order;   // parents before children
+    for (int x = 0; x < n_front; ++x)
+      if (par[x] < 0) order.push_back(x);
+    for (size_t q = 0; q < order.size(); ++q)
+      for (int c : children[order[q]]) order.push_back(c);
+    for (int v : order) {
+      if (v < n_sub) continue;
+      const FrontDev& F = h->fronts[v];
+      for (size_t r = 0; r < sep[v].size(); ++r) rowpos[sep[v][r]] = (int32_t)r;
+      for (size_t r = 0; r < upd[v].size(); ++r) rowpos[upd[v][r]] = F.ne_pad + (int32_t)r;
+      for (int c : children[v])
+        std::sort(upd[c].begin(), upd[c].end(), [&](int a, int b) { return rowpos[a] < rowpos[b]; });
+      for (int d : sep[v]) rowpos[d] = -1;
+      for (int d : upd[v]) rowpos[d] = -1;
+    }
+    h_upd.clear();
+    for (int x = 0; x < n_front; ++x) {
+      h->fronts[x].upd_off = (int32_t)h_upd.size();
+      h_upd.insert(h_upd.end(), upd[x].begin(), upd[x].end());
+    }
+    h_maps.clear();
+    for (int v = n_sub; v < n_front; ++v) {
+      FrontDev& F = h->fronts[v];
+      for (size_t r = 0; r < sep[v].size(); ++r) rowpos[sep[v][r]] = (int32_t)r;
+      for (size_t r = 0; r < upd[v].size(); ++r) rowpos[upd[v][r]] = F.ne_pad + (int32_t)r;
+      for (int slot = 0; slot < 2; ++slot) {
+        const int c = F.child[slot];
+        if (c < 0) continue;
+        F.map_off[slot] = (int32_t)h_maps.size();
+        for (int d : upd[c]) h_maps.push_back(rowpos[d]);
+      }
+      for (int d : sep[v]) rowpos[d] = -1;
+      for (int d : upd[v]) rowpos[d] = -1;
+    }
+    // the B rows of each domain front in their new order
+    h->leaf_upd.assign(n_sub, {});
+    size_t q0 = 0;
+    for (int i = 0; i < n_sub; ++i) {
+      h->leaf_upd[i] = upd[i];
+      for (size_t r = 0; r < upd[i].size(); ++r) rowpos[upd[i][r]] = (int32_t)r;
+      for (int q = 0; q < subs[i].nb; ++q) h_brow[q0 + q] = rowpos[subs[i].b_dual[q]];
+      q0 += subs[i].nb;
+      for (int d : upd[i]) rowpos[d] = -1;
+    }
   }
 
   // ---- offsets, levels, task lists ----------------------------------------------
@@ -1631,10 +1683,15 @@ int dd_get_schur(const dd_handle* h, int32_t i, dd_c128* out, int32_t* duals, in
     DD_CUDA(cudaMemcpy2D(blk.data(), (size_t)m * h->elem, src, (size_t)F.ld * h->elem, (size_t)m * h->elem, m,
                          cudaMemcpyDeviceToHost));
   }
-  // the trailing block holds -F_i in its lower triangle
+  // the trailing block holds -F_i in its lower triangle, rows in the front's
+  // B-row order: pos[a] is the row of the a-th dual in ascending order
+  std::vector<int> pos(m);
+  for (int r = 0; r < m; ++r)
+    pos[std::lower_bound(h->leaf_duals[i].begin(), h->leaf_duals[i].end(), h->leaf_upd[i][r]) -
+        h->leaf_duals[i].begin()] = r;
   for (int a = 0; a < m; ++a)
     for (int b = 0; b < m; ++b) {
-      const int hi = std::max(a, b), lo = std::min(a, b);
+      const int hi = std::max(pos[a], pos[b]), lo = std::min(pos[a], pos[b]);
       double re, im;
       if (h->elem == 16) {
         const double* v = (const double*)blk.data() + 2 * ((size_t)hi * m + lo);
