@@ -20,17 +20,6 @@ namespace {
 constexpr int T = DD_TILE;
 constexpr int SOLVE_THREADS = 256;
 
-int sm_count() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
-  return sms;
-}
-
 template <typename S>
 __device__ __forceinline__ S warp_sum(S v) {
 #pragma unroll
@@ -132,7 +121,7 @@ __device__ __forceinline__ float2 ldcg<float2>(const float2* p) { return __ldcg(
 // final (its ready flag), then tile i is solved with the unit-lower diagonal
 // block.  Tasks are ordered by tile index, so a CTA only waits on CTAs with a
 // smaller block index.  Update tiles (i >= ne_pad / 64) only accumulate.
-template <typename S, bool CHAIN>
+template <typename S>
 __global__ void __launch_bounds__(SOLVE_THREADS) k_forward(const S* pool, S* rpool, const FrontDev* fr,
                                                            const Task* tasks, int nrhs, int32_t* flags, int epoch,
                                                            DevStatus* st, const S* linv, const uint8_t* piv) {
@@ -154,24 +143,11 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_forward(const S* pool, S* rpo
   // restricted Bunch-Kaufman: the tile's right-hand side is permuted (P_i) before its solve
   const bool pv = piv != nullptr && F.piv != 0 && i < nte;
   if (pv && threadIdx.x < T) perm[threadIdx.x] = piv[((int64_t)F.tile_off + i) * T + threadIdx.x];
-  // CHAIN (launches of few tiles, where the substitution is a chain of dependent
-  // tiles): the tile's own diagonal block (L_ii, or L_ii^{-1} when given) goes to
-  // shared memory and the predecessor's L block to registers before any wait, so
-  // neither is on the chain
-  if (i < nte && (Li == nullptr || CHAIN)) {
+  if (i < nte && Li == nullptr) {
     for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
       const int rr = idx / T, c = idx % T;
-      if (c <= rr) Lt[tri(rr, c)] = Li ? Li[rr * T + c] : L[(r0 + rr) * ld + r0 + c];
+      if (c <= rr) Lt[tri(rr, c)] = L[(r0 + rr) * ld + r0 + c];
     }
-  }
-  // the L block of the last tile this one waits for (the chain's predecessor), read ahead
-  constexpr bool kPre = CHAIN && sizeof(S) == 8;   // FP32 form only: keeps the FP64 kernel's registers
-  S pre[2][RW];
-  if (kPre && kmax > 0) {
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-      for (int q = 0; q < RW; ++q) pre[h][q] = L[(r0 + warp * RW + q) * ld + (kmax - 1) * T + lane + 32 * h];
   }
   for (int j = 0; j < nrhs; ++j) {
     S acc[RW];
@@ -180,15 +156,6 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_forward(const S* pool, S* rpo
     for (int k = 0; k < kmax; ++k) {
       if (j == 0 && !wait_ready(flg + k, epoch, st, t.f, k)) return;
       const int c0 = k * T;
-      if (kPre && k == kmax - 1) {
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const S zc = ldcg(z + (int64_t)(c0 + lane + 32 * h) * nrhs + j);
-#pragma unroll
-          for (int q = 0; q < RW; ++q) acc[q] = cfma(pre[h][q], zc, acc[q]);
-        }
-        continue;
-      }
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int c = c0 + lane + 32 * h;
@@ -217,7 +184,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_forward(const S* pool, S* rpo
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const int c = part * 16 + q;
-        if (c <= row) acc = cfma(CHAIN ? Lt[tri(row, c)] : Li[row * T + c], zi[c], acc);
+        if (c <= row) acc = cfma(Li[row * T + c], zi[c], acc);
       }
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
       acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
@@ -258,7 +225,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_forward(const S* pool, S* rpo
 // ordered by decreasing j.  y_j = D_j^{-1} z_j - L_uj^T x_u (update rows: the
 // already solved ancestor duals) - sum_{i>j} L_ij^T x_i (as tiles i finish),
 // then x_j = L_jj^{-T} y_j.  Node fronts publish x into lam.
-template <typename S, bool CHAIN>
+template <typename S>
 __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rpool, const FrontDev* fr,
                                                             const Task* tasks, int nrhs, const int32_t* upd,
                                                             const int32_t* sep, S* lam, int64_t ld_lam,
@@ -281,22 +248,13 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rp
   constexpr int NG = SOLVE_THREADS / T;
   int32_t* flg = flags + F.tile_off;
   const S* Li = linv != nullptr ? linv + ((int64_t)F.tile_off + j) * T * T : nullptr;
-  __shared__ S dvals[T];   // the pivots d (the diagonal of Lt holds L_jj^{-1}'s 1 with an inverse)
-  // the tile's own diagonal block (L_jj, or L_jj^{-1} when given) goes to shared
-  // memory before any wait, so it is off the dependency chain
-  if (Li == nullptr || CHAIN) {
+  if (Li == nullptr) {
     for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
       const int rr = idx / T, c = idx % T;
-      if (c <= rr) Lt[tri(rr, c)] = Li ? Li[rr * T + c] : L[(c0 + rr) * ld + c0 + c];
+      if (c <= rr) Lt[tri(rr, c)] = L[(c0 + rr) * ld + c0 + c];
     }
-  }
-  if (threadIdx.x < T) dvals[threadIdx.x] = L[(c0 + threadIdx.x) * (ld + 1)];
-  // the L block of the last tile this one waits for (tile j + 1), read ahead
-  constexpr bool kPre = CHAIN && sizeof(S) == 8;   // FP32 form only: keeps the FP64 kernel's registers
-  S pre[T / NG];
-  if (kPre && j + 1 < nte) {
-#pragma unroll
-    for (int q = 0; q < T / NG; ++q) pre[q] = L[((j + 1) * T + grp + NG * q) * ld + c0 + col];
+  } else if (threadIdx.x < T) {
+    Lt[tri(threadIdx.x, threadIdx.x)] = L[(c0 + threadIdx.x) * (ld + 1)];   // the pivots d
   }
   const bool pv = piv != nullptr && F.piv != 0;
   if (pv && threadIdx.x < T) {
@@ -314,11 +272,6 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rp
       acc = cfma(L[(F.ne_pad + u) * ld + c0 + col], ldcg(lam + upd[F.upd_off + u] + jj * ld_lam), acc);
     for (int i = nte - 1; i > j; --i) {
       if (jj == 0 && !wait_ready(flg + i, epoch, st, t.f, i)) return;
-      if (kPre && i == j + 1) {
-#pragma unroll
-        for (int q = 0; q < T / NG; ++q) acc = cfma(pre[q], ldcg(z + (int64_t)(i * T + grp + NG * q) * nrhs + jj), acc);
-        continue;
-      }
 #pragma unroll
       for (int rr = grp; rr < T; rr += NG) {
         const int r = i * T + rr;
@@ -336,7 +289,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rp
         const S zq = ldcg(z + (int64_t)(c0 + qs[threadIdx.x]) * nrhs + jj);
         yj[threadIdx.x] = csub(cfma(zq, g1s[threadIdx.x], cmul(zc, g0s[threadIdx.x])), sum);
       } else {
-        yj[threadIdx.x] = csub(cdiv(zc, dvals[threadIdx.x]), sum);
+        yj[threadIdx.x] = csub(cdiv(zc, Lt[tri(threadIdx.x, threadIdx.x)]), sum);
       }
     }
     __syncthreads();
@@ -347,7 +300,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rp
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const int r = part * 16 + q;
-        if (r >= col2) acc = cfma(CHAIN ? Lt[tri(r, col2)] : Li[r * T + col2], yj[r], acc);
+        if (r >= col2) acc = cfma(Li[r * T + col2], yj[r], acc);
       }
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
       acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
@@ -755,22 +708,12 @@ void launch_forward(int prec, const void* pool, void* rpool, const FrontDev* fro
                                    (const float2*)linv, piv);
     return;
   }
-  const bool chain = n <= 4 * sm_count();
-  if (prec == 0) {
-    if (chain)
-      k_forward<double2, true><<<n, SOLVE_THREADS, 0, s>>>((const double2*)pool, (double2*)rpool, fronts, tasks, nrhs,
-                                                          flags, epoch, st, nullptr, piv);
-    else
-      k_forward<double2, false><<<n, SOLVE_THREADS, 0, s>>>((const double2*)pool, (double2*)rpool, fronts, tasks,
-                                                           nrhs, flags, epoch, st, nullptr, piv);
-  } else {
-    if (chain)
-      k_forward<float2, true><<<n, SOLVE_THREADS, 0, s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs,
-                                                         flags, epoch, st, (const float2*)linv, piv);
-    else
-      k_forward<float2, false><<<n, SOLVE_THREADS, 0, s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs,
-                                                          flags, epoch, st, (const float2*)linv, piv);
-  }
+  if (prec == 0)
+    k_forward<double2><<<n, SOLVE_THREADS, 0, s>>>((const double2*)pool, (double2*)rpool, fronts, tasks, nrhs, flags,
+                                                   epoch, st, nullptr, piv);
+  else
+    k_forward<float2><<<n, SOLVE_THREADS, 0, s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs, flags,
+                                                  epoch, st, (const float2*)linv, piv);
 }
 
 void launch_backward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const Task* tasks, int n,
@@ -788,26 +731,13 @@ void launch_backward(int prec, const void* pool, void* rpool, const FrontDev* fr
                                     (float2*)lam_work, ld_lam, flags, epoch, st, (const float2*)linv, piv);
     return;
   }
-  const bool chain = n <= 4 * sm_count();
-  if (prec == 0) {
-    if (chain)
-      k_backward<double2, true><<<n, SOLVE_THREADS, 0, s>>>((const double2*)pool, (double2*)rpool, fronts, tasks, nrhs,
-                                                           upd, sep, (double2*)lam_work, ld_lam, flags, epoch, st,
-                                                           nullptr, piv);
-    else
-      k_backward<double2, false><<<n, SOLVE_THREADS, 0, s>>>((const double2*)pool, (double2*)rpool, fronts, tasks,
-                                                            nrhs, upd, sep, (double2*)lam_work, ld_lam, flags, epoch,
-                                                            st, nullptr, piv);
-  } else {
-    if (chain)
-      k_backward<float2, true><<<n, SOLVE_THREADS, 0, s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs,
-                                                          upd, sep, (float2*)lam_work, ld_lam, flags, epoch, st,
-                                                          (const float2*)linv, piv);
-    else
-      k_backward<float2, false><<<n, SOLVE_THREADS, 0, s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs,
-                                                           upd, sep, (float2*)lam_work, ld_lam, flags, epoch, st,
-                                                           (const float2*)linv, piv);
-  }
+  if (prec == 0)
+    k_backward<double2><<<n, SOLVE_THREADS, 0, s>>>((const double2*)pool, (double2*)rpool, fronts, tasks, nrhs, upd,
+                                                    sep, (double2*)lam_work, ld_lam, flags, epoch, st, nullptr, piv);
+  else
+    k_backward<float2><<<n, SOLVE_THREADS, 0, s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs, upd, sep,
+                                                   (float2*)lam_work, ld_lam, flags, epoch, st, (const float2*)linv,
+                                                   piv);
 }
 
 void launch_leaf_out(int prec, const void* rpool, const FrontDev* fronts, const LeafDev* leaves, int n_leaves,
