@@ -154,7 +154,7 @@ struct dd_handle {
   Task *d_fwd = nullptr, *d_bwd = nullptr;
   Task* d_tc = nullptr;            // tensor-core update tasks (mixed form)
   Task* d_tc2 = nullptr;           // two-panel tensor-core update tasks
-  int2* d_grp = nullptr;           // their groups (first task, count) sharing one A block
+  int2* d_grp = nullptr;           // their groups (first task, count): runs of tasks of one row tile
   int* d_counters = nullptr;       // one group counter per tensor-core update launch of a factor
   int n_counters = 0;
   unsigned char* d_ws = nullptr;   // panel operand images (mixed form), four slots
@@ -826,7 +826,8 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
   std::vector<Task> h_trsm, h_updt, h_tc, h_tc2;
   std::vector<int2> h_grp;
   // runs of consecutive tasks with the same (front, row tile), at most
-  // kGroupCap long so that the round-robin deal stays balanced
+  // kGroupCap long, claimed one at a time by the persistent update kernel (consecutive
+  // groups in flight share their column tiles' operand images through L2)
   constexpr int kGroupCap = 8;
   auto add_groups = [&](const std::vector<Task>& tl, int64_t first, int64_t count) -> int {
     int ng = 0;

@@ -94,6 +94,7 @@ void launch_node_init(int prec, void* pool, const FrontDev* fronts, const int32_
 // piv (optional): one byte per pivot position of every diagonal tile (index
 // (tile_off + tile) * 64 + c), the permutation of the restricted Bunch-Kaufman
 // pivoting of the fronts with FrontDev::piv set; nullptr: no front pivots
+// FP64 form only (prec = 0, diag_fp64 = 0): 64 x 64 diagonal tile and panel tiles in FP64
 void launch_diag(int prec, int diag_fp64, void* pool, const FrontDev* fronts, const int32_t* fids, int n,
                  int k, DevStatus* st, cudaStream_t s, uint8_t* piv = nullptr);
 void launch_trsm(int prec, void* pool, const FrontDev* fronts, const Task* tasks, int n, int k,

@@ -797,12 +797,11 @@ void launch_node_init(int prec, void* pool, const FrontDev* fronts, const int32_
   else k_node_init<float2><<<n, 64, 0, s>>>((float2*)pool, fronts, ids);
 }
 
+// FP64 form (the mixed form uses launch_diag_mx); prec and diag_fp64 must be 0
 void launch_diag(int prec, int diag_fp64, void* pool, const FrontDev* fronts, const int32_t* fids, int n, int k,
                  DevStatus* st, cudaStream_t s, uint8_t* piv) {
-  if (n <= 0) return;
-  if (prec == 0) k_diag<double2, double2><<<n, 256, 0, s>>>((double2*)pool, fronts, fids, k, st, piv);
-  else if (diag_fp64) k_diag<float2, double2><<<n, 256, 0, s>>>((float2*)pool, fronts, fids, k, st, piv);
-  else k_diag<float2, float2><<<n, 256, 0, s>>>((float2*)pool, fronts, fids, k, st, piv);
+  if (n <= 0 || prec != 0 || diag_fp64 != 0) return;
+  k_diag<double2, double2><<<n, 256, 0, s>>>((double2*)pool, fronts, fids, k, st, piv);
 }
 
 void launch_diag_mx(int diag_fp64, void* pool, const FrontDev* fronts, const int32_t* fids, int n, int k,
@@ -820,14 +819,9 @@ void launch_trsm_mx(void* pool, const FrontDev* fronts, const Task* tasks, int n
 
 void launch_trsm(int prec, void* pool, const FrontDev* fronts, const Task* tasks, int n, int k, DevStatus* st,
                  cudaStream_t s, unsigned char* ws, const uint8_t* piv) {
-  if (n <= 0) return;
-  if (prec == 0) {
-    set_trsm_attr<double2>();
-    k_trsm<double2><<<n, 256, trsm_smem<double2>(), s>>>((double2*)pool, fronts, tasks, k, st, nullptr, piv);
-  } else {
-    set_trsm_attr<float2>();
-    k_trsm<float2><<<n, 256, trsm_smem<float2>(), s>>>((float2*)pool, fronts, tasks, k, st, ws, piv);
-  }
+  if (n <= 0 || prec != 0) return;   // FP64 form (the mixed form uses launch_trsm_mx)
+  set_trsm_attr<double2>();
+  k_trsm<double2><<<n, 256, trsm_smem<double2>(), s>>>((double2*)pool, fronts, tasks, k, st, ws, piv);
 }
 
 void launch_update(int prec, void* pool, const FrontDev* fronts, const Task* tasks, int n, int k, cudaStream_t s) {
