@@ -121,7 +121,15 @@ __device__ __forceinline__ float2 ldcg<float2>(const float2* p) { return __ldcg(
 // final (its ready flag), then tile i is solved with the unit-lower diagonal
 // block.  Tasks are ordered by tile index, so a CTA only waits on CTAs with a
 // smaller block index.  Update tiles (i >= ne_pad / 64) only accumulate.
-template <typename S>
+//
+// CHAIN (launches of few tiles, where the substitution is a chain of dependent
+// tiles): everything that does not depend on the tiles being waited for is read
+// before the waits -- the tile's diagonal block (L_ii^{-1} when given) into
+// shared memory, the tile's own right-hand side, and (FP32 form) the L block
+// of the next tile into registers -- so after each wait only the 64 values of
+// the finished tile are read, all issued before the products.  The other
+// launches (many tiles, bandwidth-bound) keep the registers low.
+template <typename S, bool CHAIN>
 __global__ void __launch_bounds__(SOLVE_THREADS) k_forward(const S* pool, S* rpool, const FrontDev* fr,
                                                            const Task* tasks, int nrhs, int32_t* flags, int epoch,
                                                            DevStatus* st, const S* linv, const uint8_t* piv) {
@@ -139,35 +147,62 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_forward(const S* pool, S* rpo
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   int32_t* flg = flags + F.tile_off;
   constexpr int RW = T / (SOLVE_THREADS / 32);  // rows per warp
+  constexpr bool kAhead = CHAIN && sizeof(S) == 8;
   const S* Li = (linv != nullptr && i < nte) ? linv + ((int64_t)F.tile_off + i) * T * T : nullptr;
   // restricted Bunch-Kaufman: the tile's right-hand side is permuted (P_i) before its solve
   const bool pv = piv != nullptr && F.piv != 0 && i < nte;
   if (pv && threadIdx.x < T) perm[threadIdx.x] = piv[((int64_t)F.tile_off + i) * T + threadIdx.x];
-  if (i < nte && Li == nullptr) {
+  if (i < nte && (Li == nullptr || CHAIN)) {
     for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
       const int rr = idx / T, c = idx % T;
-      if (c <= rr) Lt[tri(rr, c)] = L[(r0 + rr) * ld + r0 + c];
+      if (c <= rr) Lt[tri(rr, c)] = Li != nullptr ? Li[rr * T + c] : L[(r0 + rr) * ld + r0 + c];
     }
   }
   for (int j = 0; j < nrhs; ++j) {
-    S acc[RW];
+    S acc[RW], own[RW], lnext[2][RW];
 #pragma unroll
-    for (int q = 0; q < RW; ++q) acc[q] = czero<S>();
+    for (int q = 0; q < RW; ++q) {
+      acc[q] = czero<S>();
+      if (CHAIN) own[q] = ldcg(z + (int64_t)(r0 + warp * RW + q) * nrhs + j);
+    }
+    if (kAhead && kmax > 0) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int q = 0; q < RW; ++q) lnext[h][q] = L[(r0 + warp * RW + q) * ld + lane + 32 * h];
+    }
     for (int k = 0; k < kmax; ++k) {
       if (j == 0 && !wait_ready(flg + k, epoch, st, t.f, k)) return;
       const int c0 = k * T;
+      if (kAhead) {
+        S zc[2];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int c = c0 + lane + 32 * h;
-        const S zc = ldcg(z + (int64_t)c * nrhs + j);
+        for (int h = 0; h < 2; ++h) zc[h] = ldcg(z + (int64_t)(c0 + lane + 32 * h) * nrhs + j);
 #pragma unroll
-        for (int q = 0; q < RW; ++q) acc[q] = cfma(L[(r0 + warp * RW + q) * ld + c], zc, acc[q]);
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int q = 0; q < RW; ++q) acc[q] = cfma(lnext[h][q], zc[h], acc[q]);
+        if (k + 1 < kmax) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int q = 0; q < RW; ++q) lnext[h][q] = L[(r0 + warp * RW + q) * ld + c0 + T + lane + 32 * h];
+        }
+      } else {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int c = c0 + lane + 32 * h;
+          const S zc = ldcg(z + (int64_t)c * nrhs + j);
+#pragma unroll
+          for (int q = 0; q < RW; ++q) acc[q] = cfma(L[(r0 + warp * RW + q) * ld + c], zc, acc[q]);
+        }
       }
     }
 #pragma unroll
     for (int q = 0; q < RW; ++q) {
       const S v = warp_sum(acc[q]);
-      if (lane == 0) zi[warp * RW + q] = csub(ldcg(z + (int64_t)(r0 + warp * RW + q) * nrhs + j), v);
+      if (lane == 0)
+        zi[warp * RW + q] = csub(CHAIN ? own[q] : ldcg(z + (int64_t)(r0 + warp * RW + q) * nrhs + j), v);
     }
     __syncthreads();
     if (pv) {
@@ -184,7 +219,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_forward(const S* pool, S* rpo
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const int c = part * 16 + q;
-        if (c <= row) acc = cfma(Li[row * T + c], zi[c], acc);
+        if (c <= row) acc = cfma(CHAIN ? Lt[tri(row, c)] : Li[row * T + c], zi[c], acc);
       }
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
       acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
@@ -224,8 +259,11 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_forward(const S* pool, S* rpo
 // Backward substitution, one CTA per (front, eliminated column tile j), tasks
 // ordered by decreasing j.  y_j = D_j^{-1} z_j - L_uj^T x_u (update rows: the
 // already solved ancestor duals) - sum_{i>j} L_ij^T x_i (as tiles i finish),
-// then x_j = L_jj^{-T} y_j.  Node fronts publish x into lam.
-template <typename S>
+// then x_j = L_jj^{-T} y_j.  Node fronts publish x into lam.  CHAIN: as in the
+// forward substitution, everything independent of the awaited tiles (the
+// diagonal block or its inverse, the pivots, z_j, the destination indices and,
+// FP32 form, the next L block) is read before the waits.
+template <typename S, bool CHAIN>
 __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rpool, const FrontDev* fr,
                                                             const Task* tasks, int nrhs, const int32_t* upd,
                                                             const int32_t* sep, S* lam, int64_t ld_lam,
@@ -234,6 +272,9 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rp
   __shared__ S Lt[T * (T + 1) / 2];
   __shared__ S part[SOLVE_THREADS];
   __shared__ S yj[T];
+  __shared__ S dv[T];            // the pivots d when Lt holds L_jj^{-1}
+  constexpr int kUChunk = sizeof(S) == 8 ? 512 : 256;
+  __shared__ S xu[kUChunk];      // gathered ancestor duals of the update rows
   __shared__ S g0s[T], g1s[T];   // D_j^{-1} coefficients when the tile pivoted
   __shared__ int qs[T], perm[T];
   const Task t = tasks[blockIdx.x];
@@ -246,16 +287,17 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rp
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int col = threadIdx.x % T, grp = threadIdx.x / T;  // 64 columns x 4 row groups
   constexpr int NG = SOLVE_THREADS / T;
+  constexpr int NQ = T / NG;   // rows of a tile per thread
+  constexpr bool kAhead = CHAIN && sizeof(S) == 8;
   int32_t* flg = flags + F.tile_off;
   const S* Li = linv != nullptr ? linv + ((int64_t)F.tile_off + j) * T * T : nullptr;
-  if (Li == nullptr) {
+  if (Li == nullptr || CHAIN) {
     for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
       const int rr = idx / T, c = idx % T;
-      if (c <= rr) Lt[tri(rr, c)] = L[(c0 + rr) * ld + c0 + c];
+      if (c <= rr) Lt[tri(rr, c)] = Li != nullptr ? Li[rr * T + c] : L[(c0 + rr) * ld + c0 + c];
     }
-  } else if (threadIdx.x < T) {
-    Lt[tri(threadIdx.x, threadIdx.x)] = L[(c0 + threadIdx.x) * (ld + 1)];   // the pivots d
   }
+  if (Li != nullptr && threadIdx.x < T) dv[threadIdx.x] = L[(c0 + threadIdx.x) * (ld + 1)];
   const bool pv = piv != nullptr && F.piv != 0;
   if (pv && threadIdx.x < T) {
     S g0, g1;
@@ -266,16 +308,54 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rp
     qs[threadIdx.x] = q;
     perm[threadIdx.x] = piv[((int64_t)F.tile_off + j) * T + threadIdx.x];
   }
+  // where x_j goes: its row of z and (node fronts) its dual index
+  int xrow = 0, xdual = -1;
+  if (threadIdx.x < T) {
+    xrow = c0 + (pv ? perm[threadIdx.x] : threadIdx.x);
+    if (F.kind == 1 && xrow < F.ne) xdual = sep[F.sep_off + xrow];
+  }
   for (int jj = 0; jj < nrhs; ++jj) {
+    S zc = czero<S>(), zq = czero<S>();
+    if (CHAIN && threadIdx.x < T) {
+      zc = ldcg(z + (int64_t)(c0 + threadIdx.x) * nrhs + jj);
+      if (pv) zq = ldcg(z + (int64_t)(c0 + qs[threadIdx.x]) * nrhs + jj);
+    }
+    S lnext[NQ];
+    if (kAhead && j + 1 < nte) {
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) lnext[q] = L[((nte - 1) * T + grp + NG * q) * ld + c0 + col];
+    }
+    // update rows: the ancestor duals x_u, final since earlier launches (plain
+    // loads), gathered into shared memory a chunk at a time
     S acc = czero<S>();
-    for (int u = grp; u < F.nu; u += NG)
-      acc = cfma(L[(F.ne_pad + u) * ld + c0 + col], ldcg(lam + upd[F.upd_off + u] + jj * ld_lam), acc);
+    for (int u0 = 0; u0 < F.nu; u0 += kUChunk) {
+      const int nuc = min(kUChunk, F.nu - u0);
+      __syncthreads();
+#pragma unroll 2
+      for (int e = threadIdx.x; e < nuc; e += SOLVE_THREADS) xu[e] = lam[upd[F.upd_off + u0 + e] + jj * ld_lam];
+      __syncthreads();
+      const S* Lu = L + (int64_t)(F.ne_pad + u0) * ld + c0 + col;
+#pragma unroll 8
+      for (int u = grp; u < nuc; u += NG) acc = cfma(Lu[(int64_t)u * ld], xu[u], acc);
+    }
     for (int i = nte - 1; i > j; --i) {
       if (jj == 0 && !wait_ready(flg + i, epoch, st, t.f, i)) return;
+      if (kAhead) {
+        S xr[NQ];
 #pragma unroll
-      for (int rr = grp; rr < T; rr += NG) {
-        const int r = i * T + rr;
-        acc = cfma(L[r * ld + c0 + col], ldcg(z + (int64_t)r * nrhs + jj), acc);
+        for (int q = 0; q < NQ; ++q) xr[q] = ldcg(z + (int64_t)(i * T + grp + NG * q) * nrhs + jj);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) acc = cfma(lnext[q], xr[q], acc);
+        if (i - 1 > j) {
+#pragma unroll
+          for (int q = 0; q < NQ; ++q) lnext[q] = L[((i - 1) * T + grp + NG * q) * ld + c0 + col];
+        }
+      } else {
+#pragma unroll
+        for (int rr = grp; rr < T; rr += NG) {
+          const int r = i * T + rr;
+          acc = cfma(L[r * ld + c0 + col], ldcg(z + (int64_t)r * nrhs + jj), acc);
+        }
       }
     }
     part[threadIdx.x] = acc;
@@ -284,12 +364,14 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rp
       S sum = part[threadIdx.x];
 #pragma unroll
       for (int g = 1; g < NG; ++g) sum = cadd(sum, part[g * T + threadIdx.x]);
-      const S zc = ldcg(z + (int64_t)(c0 + threadIdx.x) * nrhs + jj);
+      if (!CHAIN) {
+        zc = ldcg(z + (int64_t)(c0 + threadIdx.x) * nrhs + jj);
+        if (pv) zq = ldcg(z + (int64_t)(c0 + qs[threadIdx.x]) * nrhs + jj);
+      }
       if (pv) {
-        const S zq = ldcg(z + (int64_t)(c0 + qs[threadIdx.x]) * nrhs + jj);
         yj[threadIdx.x] = csub(cfma(zq, g1s[threadIdx.x], cmul(zc, g0s[threadIdx.x])), sum);
       } else {
-        yj[threadIdx.x] = csub(cdiv(zc, Lt[tri(threadIdx.x, threadIdx.x)]), sum);
+        yj[threadIdx.x] = csub(cdiv(zc, Li != nullptr ? dv[threadIdx.x] : Lt[tri(threadIdx.x, threadIdx.x)]), sum);
       }
     }
     __syncthreads();
@@ -300,7 +382,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rp
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const int r = part * 16 + q;
-        if (r >= col2) acc = cfma(Li[r * T + col2], yj[r], acc);
+        if (r >= col2) acc = cfma(CHAIN ? Lt[tri(r, col2)] : Li[r * T + col2], yj[r], acc);
       }
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
       acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
@@ -322,10 +404,9 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rp
       yj[lane + 32] = v1;
     }
     __syncthreads();
-    if (threadIdx.x < T) {
-      const int r = c0 + (pv ? perm[threadIdx.x] : threadIdx.x);   // x_j = P_j^T (L_jj^{-T} y_j)
-      z[(int64_t)r * nrhs + jj] = yj[threadIdx.x];
-      if (F.kind == 1 && r < F.ne) lam[sep[F.sep_off + r] + jj * ld_lam] = yj[threadIdx.x];
+    if (threadIdx.x < T) {   // x_j = P_j^T (L_jj^{-T} y_j)
+      z[(int64_t)xrow * nrhs + jj] = yj[threadIdx.x];
+      if (xdual >= 0) lam[xdual + jj * ld_lam] = yj[threadIdx.x];
     }
     __syncthreads();
   }
@@ -502,7 +583,7 @@ __global__ void __launch_bounds__(256) k_backward_mr(const float2* pool, float2*
       const int kk = idx / T, cc = idx % T;   // row kk of the chunk, column cc
       const int u = u0 + kk;
       sm.As[kk][cc] = u < F.nu ? L[(F.ne_pad + u) * ld + c0 + cc] : make_float2(0.f, 0.f);
-      sm.Bs[kk][cc] = (u < F.nu && cc < nrhs) ? ldcg(lam + upd[F.upd_off + u] + cc * ld_lam) : make_float2(0.f, 0.f);
+      sm.Bs[kk][cc] = (u < F.nu && cc < nrhs) ? lam[upd[F.upd_off + u] + cc * ld_lam] : make_float2(0.f, 0.f);
     }
     __syncthreads();
     mr_fma(sm, acc, tx, ty);
@@ -694,6 +775,17 @@ void launch_rhs_extend_add(int prec, void* rpool, const FrontDev* fronts, const 
   else k_rhs_extend_add<float2><<<n, 256, 0, s>>>((float2*)rpool, fronts, ids, slot, maps, nrhs);
 }
 
+// A substitution launch whose tiles all fit on the GPU at once is a chain of
+// dependent tiles (separator fronts): it takes the read-ahead (CHAIN) form.
+template <typename K>
+bool fits_one_wave(K kernel, int n) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, SOLVE_THREADS, 0);
+  return n <= sms * per_sm;
+}
+
 void launch_forward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const Task* tasks, int n,
                     int nrhs, int32_t* flags, int epoch, DevStatus* st, cudaStream_t s, const void* linv,
                     const uint8_t* piv) {
@@ -708,12 +800,21 @@ void launch_forward(int prec, const void* pool, void* rpool, const FrontDev* fro
                                    (const float2*)linv, piv);
     return;
   }
-  if (prec == 0)
-    k_forward<double2><<<n, SOLVE_THREADS, 0, s>>>((const double2*)pool, (double2*)rpool, fronts, tasks, nrhs, flags,
-                                                   epoch, st, nullptr, piv);
-  else
-    k_forward<float2><<<n, SOLVE_THREADS, 0, s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs, flags,
-                                                  epoch, st, (const float2*)linv, piv);
+  if (prec == 0) {
+    if (fits_one_wave(k_forward<double2, true>, n))
+      k_forward<double2, true><<<n, SOLVE_THREADS, 0, s>>>((const double2*)pool, (double2*)rpool, fronts, tasks, nrhs,
+                                                          flags, epoch, st, nullptr, piv);
+    else
+      k_forward<double2, false><<<n, SOLVE_THREADS, 0, s>>>((const double2*)pool, (double2*)rpool, fronts, tasks,
+                                                           nrhs, flags, epoch, st, nullptr, piv);
+  } else {
+    if (fits_one_wave(k_forward<float2, true>, n))
+      k_forward<float2, true><<<n, SOLVE_THREADS, 0, s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs,
+                                                         flags, epoch, st, (const float2*)linv, piv);
+    else
+      k_forward<float2, false><<<n, SOLVE_THREADS, 0, s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs,
+                                                          flags, epoch, st, (const float2*)linv, piv);
+  }
 }
 
 void launch_backward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const Task* tasks, int n,
@@ -731,13 +832,25 @@ void launch_backward(int prec, const void* pool, void* rpool, const FrontDev* fr
                                     (float2*)lam_work, ld_lam, flags, epoch, st, (const float2*)linv, piv);
     return;
   }
-  if (prec == 0)
-    k_backward<double2><<<n, SOLVE_THREADS, 0, s>>>((const double2*)pool, (double2*)rpool, fronts, tasks, nrhs, upd,
-                                                    sep, (double2*)lam_work, ld_lam, flags, epoch, st, nullptr, piv);
-  else
-    k_backward<float2><<<n, SOLVE_THREADS, 0, s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs, upd, sep,
-                                                   (float2*)lam_work, ld_lam, flags, epoch, st, (const float2*)linv,
-                                                   piv);
+  if (prec == 0) {
+    if (fits_one_wave(k_backward<double2, true>, n))
+      k_backward<double2, true><<<n, SOLVE_THREADS, 0, s>>>((const double2*)pool, (double2*)rpool, fronts, tasks, nrhs,
+                                                           upd, sep, (double2*)lam_work, ld_lam, flags, epoch, st,
+                                                           nullptr, piv);
+    else
+      k_backward<double2, false><<<n, SOLVE_THREADS, 0, s>>>((const double2*)pool, (double2*)rpool, fronts, tasks,
+                                                            nrhs, upd, sep, (double2*)lam_work, ld_lam, flags, epoch,
+                                                            st, nullptr, piv);
+  } else {
+    if (fits_one_wave(k_backward<float2, true>, n))
+      k_backward<float2, true><<<n, SOLVE_THREADS, 0, s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs,
+                                                          upd, sep, (float2*)lam_work, ld_lam, flags, epoch, st,
+                                                          (const float2*)linv, piv);
+    else
+      k_backward<float2, false><<<n, SOLVE_THREADS, 0, s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs,
+                                                           upd, sep, (float2*)lam_work, ld_lam, flags, epoch, st,
+                                                           (const float2*)linv, piv);
+  }
 }
 
 void launch_leaf_out(int prec, const void* rpool, const FrontDev* fronts, const LeafDev* leaves, int n_leaves,
