@@ -64,6 +64,7 @@ struct Level {
   int max_child_nu = 0;
   int64_t fwd_off = 0, bwd_off = 0;   // solve tasks (forward by row tile, backward by column tile)
   int n_fwd = 0, n_bwd = 0;
+  int upd_split = 0;   // separator levels: CTAs per backward task of the split update-row product
 };
 
 struct DeviceArena {
@@ -195,6 +196,7 @@ struct dd_handle {
   }
   void* rpool = nullptr;
   void* lam_work = nullptr;
+  void* upd_part = nullptr;   // update-row partial sums of the backward substitution
   double2 *d_f = nullptr, *d_u = nullptr, *d_r = nullptr, *d_du = nullptr;
   double2 *d_lam = nullptr, *d_dlam = nullptr, *d_g = nullptr;
   std::vector<void*> work_ptrs;
@@ -361,6 +363,26 @@ int ensure_work(dd_handle* h, int nrhs) {
   const size_t nr = (size_t)nrhs;
   DD_CUDA(get(&h->rpool, (size_t)h->rows_total * nr * h->elem));
   DD_CUDA(get(&h->lam_work, (size_t)h->n_dual * nr * h->elem));
+  // separator levels of few tiles (their substitution is a chain whose first
+  // tile waits for its update-row product): split the update rows of each
+  // backward task over enough CTAs to fill the GPU about four times, at least
+  // 128 rows per CTA.  Levels of many tiles keep the product inside the
+  // substitution, where it overlaps the waits.
+  int sms = 1;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  size_t part_el = 0;
+  for (size_t l = 1; l < h->levels.size(); ++l) {
+    Level& L = h->levels[l];
+    int max_nu = 0;
+    for (int32_t f : L.ids) max_nu = std::max(max_nu, h->fronts[f].nu);
+    L.upd_split = 0;
+    if (max_nu == 0 || L.n_bwd == 0) continue;
+    const int by_rows = (max_nu + 127) / 128, by_grid = (4 * sms + L.n_bwd - 1) / L.n_bwd;
+    if (L.n_bwd > 2 * sms || by_rows < 2) continue;
+    L.upd_split = std::min(by_rows, by_grid);
+    part_el = std::max(part_el, (size_t)L.n_bwd * L.upd_split * DD_TILE);
+  }
+  DD_CUDA(get(&h->upd_part, part_el * nr * h->elem));
   DD_CUDA(get((void**)&h->d_f, (size_t)h->n_loc * nr * 16));
   DD_CUDA(get((void**)&h->d_u, (size_t)h->n_loc * nr * 16));
   DD_CUDA(get((void**)&h->d_r, (size_t)h->n_loc * nr * 16));
@@ -412,10 +434,10 @@ void direct_solve(dd_handle* h, int nrhs, const double2* f, int64_t ldf, const d
   for (size_t l = h->levels.size(); l-- > 0;) {
     const Level& L = h->levels[l];
     const bool leaf_sub = sub && l == 0;
-    ddk::launch_backward(p, h->pool, h->rpool, h->d_fronts, leaf_sub ? sub->bwd : h->d_bwd + L.bwd_off,
-                         leaf_sub ? sub->n_bwd : L.n_bwd, nrhs, h->d_upd, h->d_sep, h->lam_work, h->n_dual,
-                         h->d_flag_b, ep, h->d_solve_status, s, h->d_linv, h->d_piv);
-    h->launches += 1;
+    h->launches += ddk::launch_backward(p, h->pool, h->rpool, h->d_fronts, leaf_sub ? sub->bwd : h->d_bwd + L.bwd_off,
+                                        leaf_sub ? sub->n_bwd : L.n_bwd, nrhs, h->d_upd, h->d_sep, h->lam_work,
+                                        h->n_dual, h->d_flag_b, ep, h->d_solve_status, s, h->d_linv, h->d_piv,
+                                        l > 0 && L.upd_split > 0 ? h->upd_part : nullptr, L.upd_split);
   }
   if (sub)
     ddk::launch_leaf_out(p, h->rpool, h->d_fronts, sub->leaves, sub->n_leaves, h->d_perm, u, sub->ldu, nrhs, 0, s);

@@ -132,10 +132,13 @@ void launch_rhs_extend_add(int prec, void* rpool, const FrontDev* fronts, const 
 void launch_forward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const Task* tasks, int n,
                     int nrhs, int32_t* flags, int epoch, DevStatus* st, cudaStream_t s,
                     const void* linv = nullptr, const uint8_t* piv = nullptr);
-void launch_backward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const Task* tasks, int n,
-                     int nrhs, const int32_t* upd, const int32_t* sep, void* lam_work, int64_t ld_lam,
-                     int32_t* flags, int epoch, DevStatus* st, cudaStream_t s, const void* linv = nullptr,
-                     const uint8_t* piv = nullptr);
+// upart (optional, separator levels): scratch for the update-row partial sums
+// (n x nsplit x nrhs x 64 elements); the update-row product then runs as a
+// separate launch split nsplit ways.  Returns the number of kernels launched.
+int launch_backward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const Task* tasks, int n,
+                    int nrhs, const int32_t* upd, const int32_t* sep, void* lam_work, int64_t ld_lam,
+                    int32_t* flags, int epoch, DevStatus* st, cudaStream_t s, const void* linv = nullptr,
+                    const uint8_t* piv = nullptr, void* upart = nullptr, int nsplit = 0);
 void launch_leaf_out(int prec, const void* rpool, const FrontDev* fronts, const LeafDev* leaves,
                      int n_leaves, const int32_t* perm, double2* u, int64_t ldu, int nrhs, int accumulate,
                      cudaStream_t s);

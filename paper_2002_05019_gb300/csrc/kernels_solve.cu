@@ -122,14 +122,13 @@ __device__ __forceinline__ float2 ldcg<float2>(const float2* p) { return __ldcg(
 // block.  Tasks are ordered by tile index, so a CTA only waits on CTAs with a
 // smaller block index.  Update tiles (i >= ne_pad / 64) only accumulate.
 //
-// CHAIN (launches of few tiles, where the substitution is a chain of dependent
-// tiles): everything that does not depend on the tiles being waited for is read
-// before the waits -- the tile's diagonal block (L_ii^{-1} when given) into
-// shared memory, the tile's own right-hand side, and (FP32 form) the L block
-// of the next tile into registers -- so after each wait only the 64 values of
-// the finished tile are read, all issued before the products.  The other
-// launches (many tiles, bandwidth-bound) keep the registers low.
-template <typename S, bool CHAIN>
+// Everything that does not depend on the tiles waited for is read before the
+// waits -- the tile's diagonal block (L_ii^{-1} when given) into shared memory,
+// the tile's own right-hand side and (FP32 form) the L block of the next tile
+// into registers -- so after each wait only the 64 values of the finished tile
+// are read, all issued before the products: the separator fronts' substitution
+// is a chain of dependent tiles, and its step time is this latency.
+template <typename S>
 __global__ void __launch_bounds__(SOLVE_THREADS) k_forward(const S* pool, S* rpool, const FrontDev* fr,
                                                            const Task* tasks, int nrhs, int32_t* flags, int epoch,
                                                            DevStatus* st, const S* linv, const uint8_t* piv) {
@@ -147,12 +146,12 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_forward(const S* pool, S* rpo
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   int32_t* flg = flags + F.tile_off;
   constexpr int RW = T / (SOLVE_THREADS / 32);  // rows per warp
-  constexpr bool kAhead = CHAIN && sizeof(S) == 8;
+  constexpr bool kAhead = sizeof(S) == 8;
   const S* Li = (linv != nullptr && i < nte) ? linv + ((int64_t)F.tile_off + i) * T * T : nullptr;
   // restricted Bunch-Kaufman: the tile's right-hand side is permuted (P_i) before its solve
   const bool pv = piv != nullptr && F.piv != 0 && i < nte;
   if (pv && threadIdx.x < T) perm[threadIdx.x] = piv[((int64_t)F.tile_off + i) * T + threadIdx.x];
-  if (i < nte && (Li == nullptr || CHAIN)) {
+  if (i < nte) {
     for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
       const int rr = idx / T, c = idx % T;
       if (c <= rr) Lt[tri(rr, c)] = Li != nullptr ? Li[rr * T + c] : L[(r0 + rr) * ld + r0 + c];
@@ -163,7 +162,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_forward(const S* pool, S* rpo
 #pragma unroll
     for (int q = 0; q < RW; ++q) {
       acc[q] = czero<S>();
-      if (CHAIN) own[q] = ldcg(z + (int64_t)(r0 + warp * RW + q) * nrhs + j);
+      own[q] = ldcg(z + (int64_t)(r0 + warp * RW + q) * nrhs + j);
     }
     if (kAhead && kmax > 0) {
 #pragma unroll
@@ -174,10 +173,10 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_forward(const S* pool, S* rpo
     for (int k = 0; k < kmax; ++k) {
       if (j == 0 && !wait_ready(flg + k, epoch, st, t.f, k)) return;
       const int c0 = k * T;
-      if (kAhead) {
-        S zc[2];
+      S zc[2];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) zc[h] = ldcg(z + (int64_t)(c0 + lane + 32 * h) * nrhs + j);
+      for (int h = 0; h < 2; ++h) zc[h] = ldcg(z + (int64_t)(c0 + lane + 32 * h) * nrhs + j);
+      if (kAhead) {
 #pragma unroll
         for (int h = 0; h < 2; ++h)
 #pragma unroll
@@ -190,19 +189,15 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_forward(const S* pool, S* rpo
         }
       } else {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int c = c0 + lane + 32 * h;
-          const S zc = ldcg(z + (int64_t)c * nrhs + j);
+        for (int h = 0; h < 2; ++h)
 #pragma unroll
-          for (int q = 0; q < RW; ++q) acc[q] = cfma(L[(r0 + warp * RW + q) * ld + c], zc, acc[q]);
-        }
+          for (int q = 0; q < RW; ++q) acc[q] = cfma(L[(r0 + warp * RW + q) * ld + c0 + lane + 32 * h], zc[h], acc[q]);
       }
     }
 #pragma unroll
     for (int q = 0; q < RW; ++q) {
       const S v = warp_sum(acc[q]);
-      if (lane == 0)
-        zi[warp * RW + q] = csub(CHAIN ? own[q] : ldcg(z + (int64_t)(r0 + warp * RW + q) * nrhs + j), v);
+      if (lane == 0) zi[warp * RW + q] = csub(own[q], v);
     }
     __syncthreads();
     if (pv) {
@@ -219,7 +214,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_forward(const S* pool, S* rpo
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const int c = part * 16 + q;
-        if (c <= row) acc = cfma(CHAIN ? Lt[tri(row, c)] : Li[row * T + c], zi[c], acc);
+        if (c <= row) acc = cfma(Lt[tri(row, c)], zi[c], acc);
       }
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
       acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
@@ -256,19 +251,66 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_forward(const S* pool, S* rpo
   }
 }
 
+// Update-row part of the backward substitution of separator fronts,
+// w_j = L_uj^T x_u for every tile task of a launch, with the nu update rows of
+// a task split over nsplit CTAs (grid n_tasks x nsplit): a front's first tile
+// needs its w before the chain of dependent tiles can start, and one CTA per
+// tile reads its rows at a small fraction of the bandwidth.  Partial sums go to
+// out[((task * nsplit + split) * nrhs + column) * 64 + c]; the backward kernel
+// adds them in split order, so the result does not depend on timing.
+template <typename S>
+__global__ void __launch_bounds__(SOLVE_THREADS) k_bwd_upd(const S* pool, const FrontDev* fr, const Task* tasks,
+                                                           int nrhs, const int32_t* upd, const S* lam,
+                                                           int64_t ld_lam, int nsplit, S* out) {
+  constexpr int NG = SOLVE_THREADS / T;
+  __shared__ S xu[SOLVE_THREADS];
+  __shared__ S part[SOLVE_THREADS];
+  const Task t = tasks[blockIdx.x];
+  const FrontDev F = fr[t.f];
+  const int split = blockIdx.y;
+  const int rows = (F.nu + nsplit - 1) / nsplit;
+  const int u_begin = min(F.nu, split * rows), u_end = min(F.nu, u_begin + rows);
+  const int col = threadIdx.x % T, grp = threadIdx.x / T;
+  const S* L = pool + F.off + (int64_t)F.ne_pad * F.ld + t.i * T + col;
+  for (int jj = 0; jj < nrhs; ++jj) {
+    S acc = czero<S>();
+    for (int u0 = u_begin; u0 < u_end; u0 += SOLVE_THREADS) {
+      const int nuc = min(SOLVE_THREADS, u_end - u0);
+      __syncthreads();
+      if (threadIdx.x < nuc) xu[threadIdx.x] = lam[upd[F.upd_off + u0 + threadIdx.x] + jj * ld_lam];
+      __syncthreads();
+#pragma unroll 8
+      for (int u = grp; u < nuc; u += NG) acc = cfma(L[(int64_t)(u0 + u) * F.ld], xu[u], acc);
+    }
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x < T) {
+      S sum = part[threadIdx.x];
+#pragma unroll
+      for (int g = 1; g < NG; ++g) sum = cadd(sum, part[g * T + threadIdx.x]);
+      out[(((int64_t)blockIdx.x * nsplit + split) * nrhs + jj) * T + threadIdx.x] = sum;
+    }
+    __syncthreads();
+  }
+}
+
 // Backward substitution, one CTA per (front, eliminated column tile j), tasks
 // ordered by decreasing j.  y_j = D_j^{-1} z_j - L_uj^T x_u (update rows: the
 // already solved ancestor duals) - sum_{i>j} L_ij^T x_i (as tiles i finish),
-// then x_j = L_jj^{-T} y_j.  Node fronts publish x into lam.  CHAIN: as in the
-// forward substitution, everything independent of the awaited tiles (the
-// diagonal block or its inverse, the pivots, z_j, the destination indices and,
-// FP32 form, the next L block) is read before the waits.
+// then x_j = L_jj^{-T} y_j.  Node fronts publish x into lam.
+//
+// CHAIN (launches whose tiles all fit on the GPU at once: separator fronts,
+// whose substitution is a chain of dependent tiles): everything independent
+// of the awaited tiles -- the diagonal block or its inverse, the pivots, z_j,
+// the destination indices and (FP32 form) the next L block -- is read before
+// the waits, and each dependency's solution is loaded before its products.
+// The other launches (leaves, bandwidth-bound) keep the registers low.
 template <typename S, bool CHAIN>
 __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rpool, const FrontDev* fr,
                                                             const Task* tasks, int nrhs, const int32_t* upd,
                                                             const int32_t* sep, S* lam, int64_t ld_lam,
                                                             int32_t* flags, int epoch, DevStatus* st, const S* linv,
-                                                            const uint8_t* piv) {
+                                                            const uint8_t* piv, const S* upart, int nsplit) {
   __shared__ S Lt[T * (T + 1) / 2];
   __shared__ S part[SOLVE_THREADS];
   __shared__ S yj[T];
@@ -325,10 +367,16 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rp
 #pragma unroll
       for (int q = 0; q < NQ; ++q) lnext[q] = L[((nte - 1) * T + grp + NG * q) * ld + c0 + col];
     }
-    // update rows: the ancestor duals x_u, final since earlier launches (plain
-    // loads), gathered into shared memory a chunk at a time
+    // update rows: L_uj^T x_u, either summed from the partials of k_bwd_upd (in
+    // split order) or formed here from the ancestor duals x_u, final since
+    // earlier launches (plain loads), gathered into shared memory a chunk at a time
     S acc = czero<S>();
-    for (int u0 = 0; u0 < F.nu; u0 += kUChunk) {
+    if (CHAIN && upart != nullptr) {
+      if (grp == 0)
+        for (int q = 0; q < nsplit; ++q)
+          acc = cadd(acc, upart[(((int64_t)blockIdx.x * nsplit + q) * nrhs + jj) * T + col]);
+    }
+    for (int u0 = 0; !(CHAIN && upart != nullptr) && u0 < F.nu; u0 += kUChunk) {
       const int nuc = min(kUChunk, F.nu - u0);
       __syncthreads();
 #pragma unroll 2
@@ -800,28 +848,19 @@ void launch_forward(int prec, const void* pool, void* rpool, const FrontDev* fro
                                    (const float2*)linv, piv);
     return;
   }
-  if (prec == 0) {
-    if (fits_one_wave(k_forward<double2, true>, n))
-      k_forward<double2, true><<<n, SOLVE_THREADS, 0, s>>>((const double2*)pool, (double2*)rpool, fronts, tasks, nrhs,
-                                                          flags, epoch, st, nullptr, piv);
-    else
-      k_forward<double2, false><<<n, SOLVE_THREADS, 0, s>>>((const double2*)pool, (double2*)rpool, fronts, tasks,
-                                                           nrhs, flags, epoch, st, nullptr, piv);
-  } else {
-    if (fits_one_wave(k_forward<float2, true>, n))
-      k_forward<float2, true><<<n, SOLVE_THREADS, 0, s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs,
-                                                         flags, epoch, st, (const float2*)linv, piv);
-    else
-      k_forward<float2, false><<<n, SOLVE_THREADS, 0, s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs,
-                                                          flags, epoch, st, (const float2*)linv, piv);
-  }
+  if (prec == 0)
+    k_forward<double2><<<n, SOLVE_THREADS, 0, s>>>((const double2*)pool, (double2*)rpool, fronts, tasks, nrhs, flags,
+                                                   epoch, st, nullptr, piv);
+  else
+    k_forward<float2><<<n, SOLVE_THREADS, 0, s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs, flags,
+                                                  epoch, st, (const float2*)linv, piv);
 }
 
-void launch_backward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const Task* tasks, int n,
-                     int nrhs, const int32_t* upd, const int32_t* sep, void* lam_work, int64_t ld_lam,
-                     int32_t* flags, int epoch, DevStatus* st, cudaStream_t s, const void* linv,
-                     const uint8_t* piv) {
-  if (n <= 0) return;
+int launch_backward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const Task* tasks, int n,
+                    int nrhs, const int32_t* upd, const int32_t* sep, void* lam_work, int64_t ld_lam,
+                    int32_t* flags, int epoch, DevStatus* st, cudaStream_t s, const void* linv,
+                    const uint8_t* piv, void* upart, int nsplit) {
+  if (n <= 0) return 0;
   if (prec == 1 && linv != nullptr && nrhs >= 4 && nrhs <= T) {
     static bool attr = false;
     if (!attr) {
@@ -830,27 +869,44 @@ void launch_backward(int prec, const void* pool, void* rpool, const FrontDev* fr
     }
     k_backward_mr<<<n, 256, sizeof(MrSmem), s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs, upd, sep,
                                     (float2*)lam_work, ld_lam, flags, epoch, st, (const float2*)linv, piv);
-    return;
+    return 1;
+  }
+  const bool chain = prec == 0 ? fits_one_wave(k_backward<double2, true>, n) : fits_one_wave(k_backward<float2, true>, n);
+  // the split update-row product serves the chain form only
+  if (!chain || upart == nullptr || nsplit < 1) {
+    upart = nullptr;
+    nsplit = 0;
   }
   if (prec == 0) {
-    if (fits_one_wave(k_backward<double2, true>, n))
+    const double2* up = (const double2*)upart;
+    if (upart)
+      k_bwd_upd<double2><<<dim3(n, nsplit), SOLVE_THREADS, 0, s>>>((const double2*)pool, fronts, tasks, nrhs, upd,
+                                                                   (const double2*)lam_work, ld_lam, nsplit,
+                                                                   (double2*)upart);
+    if (chain)
       k_backward<double2, true><<<n, SOLVE_THREADS, 0, s>>>((const double2*)pool, (double2*)rpool, fronts, tasks, nrhs,
                                                            upd, sep, (double2*)lam_work, ld_lam, flags, epoch, st,
-                                                           nullptr, piv);
+                                                           nullptr, piv, up, nsplit);
     else
       k_backward<double2, false><<<n, SOLVE_THREADS, 0, s>>>((const double2*)pool, (double2*)rpool, fronts, tasks,
                                                             nrhs, upd, sep, (double2*)lam_work, ld_lam, flags, epoch,
-                                                            st, nullptr, piv);
+                                                            st, nullptr, piv, nullptr, 0);
   } else {
-    if (fits_one_wave(k_backward<float2, true>, n))
+    const float2* up = (const float2*)upart;
+    if (upart)
+      k_bwd_upd<float2><<<dim3(n, nsplit), SOLVE_THREADS, 0, s>>>((const float2*)pool, fronts, tasks, nrhs, upd,
+                                                                  (const float2*)lam_work, ld_lam, nsplit,
+                                                                  (float2*)upart);
+    if (chain)
       k_backward<float2, true><<<n, SOLVE_THREADS, 0, s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs,
                                                           upd, sep, (float2*)lam_work, ld_lam, flags, epoch, st,
-                                                          (const float2*)linv, piv);
+                                                          (const float2*)linv, piv, up, nsplit);
     else
       k_backward<float2, false><<<n, SOLVE_THREADS, 0, s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs,
                                                            upd, sep, (float2*)lam_work, ld_lam, flags, epoch, st,
-                                                           (const float2*)linv, piv);
+                                                           (const float2*)linv, piv, nullptr, 0);
   }
+  return upart ? 2 : 1;
 }
 
 void launch_leaf_out(int prec, const void* rpool, const FrontDev* fronts, const LeafDev* leaves, int n_leaves,
