@@ -399,11 +399,14 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rp
           for (int q = 0; q < NQ; ++q) lnext[q] = L[((i - 1) * T + grp + NG * q) * ld + c0 + col];
         }
       } else {
+        // x_i through shared memory (one load per thread), so that the L loads
+        // of the product are plain and all in flight together
+        if (jj > 0) __syncthreads();
+        if (threadIdx.x < T) xu[threadIdx.x] = ldcg(z + (int64_t)(i * T + threadIdx.x) * nrhs + jj);
+        __syncthreads();
+        const S* Li_ = L + (int64_t)(i * T + grp) * ld + c0 + col;
 #pragma unroll
-        for (int rr = grp; rr < T; rr += NG) {
-          const int r = i * T + rr;
-          acc = cfma(L[r * ld + c0 + col], ldcg(z + (int64_t)r * nrhs + jj), acc);
-        }
+        for (int q = 0; q < NQ; ++q) acc = cfma(Li_[(int64_t)q * NG * ld], xu[grp + NG * q], acc);
       }
     }
     part[threadIdx.x] = acc;
