@@ -420,15 +420,21 @@ __global__ void __launch_bounds__(256, 1) k_diag_mx(float2* pool, const FrontDev
   if (pv) inv_unit_lower32(a, 0, li);   // the unpivoted path formed N11 with the factor
   __syncthreads();   // ap (the precision-C block) is dead from here until pivot block 2
   {
-    // X21 = A21 P1^T N11^T: x21[r][c] = sum_{q <= c} A21[r][perm q] N11[c][q]
+    // X21 = A21 P1^T N11^T: x21[r][c] = sum_{q <= c} A21[r][perm q] N11[c][q];
+    // the thread's four columns c = cg + 8 h advance together (four independent
+    // chains), each summed in increasing q
     const int r = threadIdx.x >> 3, cg = threadIdx.x & 7;
+    float2 acc[4];
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      const int c = cg + 8 * h;
-      float2 acc = make_float2(0.f, 0.f);
-      for (int q = 0; q <= c; ++q) acc = cfma(a[tri(PB + r, pv ? perm[q] : q)], li[tri(c, q)], acc);
-      x21[r][c] = acc;
+    for (int h = 0; h < 4; ++h) acc[h] = make_float2(0.f, 0.f);
+    for (int q = 0; q < PB; ++q) {
+      const float2 av = a[tri(PB + r, pv ? perm[q] : q)];
+#pragma unroll
+      for (int h = 0; h < 4; ++h)
+        if (q <= cg + 8 * h) acc[h] = cfma(av, li[tri(cg + 8 * h, q)], acc[h]);
     }
+#pragma unroll
+    for (int h = 0; h < 4; ++h) x21[r][cg + 8 * h] = acc[h];
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < PB * PB; idx += blockDim.x) {
@@ -436,14 +442,26 @@ __global__ void __launch_bounds__(256, 1) k_diag_mx(float2* pool, const FrontDev
     a[tri(PB + rr, c)] = cfma(x21[rr][q1[c]], g1[c], cmul(x21[rr][c], d1inv[c]));   // L21 = X21 D1^{-1}
   }
   __syncthreads();
-  // A22 -= L21 X21^T (lower part)
-  for (int idx = threadIdx.x; idx < PB * PB; idx += blockDim.x) {
-    const int i = idx / PB, c = idx % PB;
-    if (c <= i) {
-      float2 acc = a[tri(PB + i, PB + c)];
-      for (int q = 0; q < PB; ++q) acc = cfms(a[tri(PB + i, q)], x21[c][q], acc);
-      a[tri(PB + i, PB + c)] = acc;
+  // A22 -= L21 X21^T (lower part): rows i0 + 8 k of column c, the four
+  // chains advancing together, each in increasing q
+  {
+    static_assert(PB * PB == 4 * 256, "four A22 elements per thread");
+    const int c = threadIdx.x % PB, i0 = threadIdx.x / PB;
+    float2 acc[4];
+#pragma unroll
+    for (int k4 = 0; k4 < 4; ++k4) {
+      const int i = i0 + 8 * k4;
+      acc[k4] = c <= i ? a[tri(PB + i, PB + c)] : make_float2(0.f, 0.f);
     }
+    for (int q = 0; q < PB; ++q) {
+      const float2 xv = x21[c][q];
+#pragma unroll
+      for (int k4 = 0; k4 < 4; ++k4)
+        if (c <= i0 + 8 * k4) acc[k4] = cfms(a[tri(PB + i0 + 8 * k4, q)], xv, acc[k4]);
+    }
+#pragma unroll
+    for (int k4 = 0; k4 < 4; ++k4)
+      if (c <= i0 + 8 * k4) a[tri(PB + i0 + 8 * k4, PB + c)] = acc[k4];
   }
   __syncthreads();
   if (pv) {
@@ -466,25 +484,34 @@ __global__ void __launch_bounds__(256, 1) k_diag_mx(float2* pool, const FrontDev
   // N22 (formed with the factor when unpivoted), then N21 = -N22 (L21 N11) through x21 = L21 N11
   if (pv) inv_unit_lower32(a, PB, li);
   {
+    // x21 = L21 N11 (four column chains together, each in increasing q)
     const int r = threadIdx.x >> 3, cg = threadIdx.x & 7;
+    float2 acc[4];
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      const int c = cg + 8 * h;
-      float2 acc = make_float2(0.f, 0.f);
-      for (int q = c; q < PB; ++q) acc = cfma(a[tri(PB + r, q)], li[tri(q, c)], acc);
-      x21[r][c] = acc;
+    for (int h = 0; h < 4; ++h) acc[h] = make_float2(0.f, 0.f);
+    for (int q = cg; q < PB; ++q) {
+      const float2 av = a[tri(PB + r, q)];
+#pragma unroll
+      for (int h = 0; h < 4; ++h)
+        if (q >= cg + 8 * h) acc[h] = cfma(av, li[tri(q, cg + 8 * h)], acc[h]);
     }
+#pragma unroll
+    for (int h = 0; h < 4; ++h) x21[r][cg + 8 * h] = acc[h];
   }
   __syncthreads();
   {
+    // N21 = -N22 x21
     const int r = threadIdx.x >> 3, cg = threadIdx.x & 7;
+    float2 acc[4];
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      const int c = cg + 8 * h;
-      float2 acc = make_float2(0.f, 0.f);
-      for (int q = 0; q <= r; ++q) acc = cfma(li[tri(PB + r, PB + q)], x21[q][c], acc);
-      li[tri(PB + r, c)] = make_float2(-acc.x, -acc.y);
+    for (int h = 0; h < 4; ++h) acc[h] = make_float2(0.f, 0.f);
+    for (int q = 0; q <= r; ++q) {
+      const float2 lv = li[tri(PB + r, PB + q)];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) acc[h] = cfma(lv, x21[q][cg + 8 * h], acc[h]);
     }
+#pragma unroll
+    for (int h = 0; h < 4; ++h) li[tri(PB + r, cg + 8 * h)] = make_float2(-acc[h].x, -acc[h].y);
   }
   for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
     const int i = idx / T, c = idx % T;
