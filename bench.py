@@ -332,9 +332,9 @@ def ours_arm(args):
         # tcgen05 kind::tf32: dense TF32 peak = measured bf16 peak x nominal TF32/BF16 ratio (1.1 / 2.25);
         # the 3xTF32 split issues 3 tensor passes per algorithmic product
         tf32 = peaks["bf16_tflops"] * (1.1 / 2.25)
-        kernel = ("k_update_tc2 + k_update_tc (tcgen05 3xTF32, 128x64 complex blocks; two-panel K=128 passes, "
-                  "one-panel passes for the next column)" if args.update_panels == 2 else
-                  "k_update_tc (tcgen05 3xTF32, 128x64 complex blocks, one panel per pass)")
+        kernel = ("k_update_tc (tcgen05 3xTF32, M=128 N=256 MMAs on 64x128 complex blocks; two-panel K=128 "
+                  "passes, one-panel passes for the next column)" if args.update_panels == 2 else
+                  "k_update_tc (tcgen05 3xTF32, M=128 N=256 MMAs on 64x128 complex blocks, one panel per pass)")
         bound, peak = "tensor", tf32 / 3.0
         src = (f"TF32 dense {tf32:.0f} TFLOP/s = measured bf16 {peaks['bf16_tflops']:.0f} x 1.1/2.25 "
                f"({peaks_src}); effective complex64 peak = TF32 / 3 split passes")
