@@ -225,7 +225,8 @@ def backward_error(p, u):
 def time_form(p, precision, args, torch, stream):
     import paper_2002_05019_gb300 as dd
     s = dd.Solver.from_problem(p, precision=precision, stream=stream.cuda_stream, device=torch.cuda.current_device(),
-                               time_kernels=not args.no_kernel_timing, refine_tol=args.refine_tol,
+                               time_kernels={"all": 1, "update": 2, "none": 0}[args.kernel_timing],
+                               refine_tol=args.refine_tol,
                                pivoting=args.pivoting, update_panels=args.update_panels)
     sched = None
     if precision == "mixed" and not args.no_autotune:
@@ -406,8 +407,10 @@ def main():
     ap.add_argument("--update-panels", type=int, default=2, choices=[1, 2],
                     help="mixed form: panels fused per tensor-core trailing-update pass")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default factor schedule")
-    ap.add_argument("--no-kernel-timing", action="store_true",
-                    help="no per-launch CUDA events (no kernel breakdown or roofline)")
+    ap.add_argument("--kernel-timing", default="update", choices=["update", "all", "none"],
+                    help="CUDA events in the timed factorizations: around the trailing-update launches "
+                         "(the roofline kernel; default), around every launch (per-class breakdown, slower), "
+                         "or none (no roofline)")
     ap.add_argument("--refine-tol", type=float, default=1e-11,
                     help="mixed form: stop refinement at this relative correction (1e-11 keeps the error <= 1e-10)")
     args = ap.parse_args()

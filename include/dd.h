@@ -104,7 +104,9 @@ typedef struct {
   void* cuda_stream;        /* cudaStream_t for every device call; NULL = legacy default stream */
   int32_t device;           /* CUDA device ordinal */
   int32_t time_kernels;     /* 1: dd_factor brackets every launch with CUDA events and reports
-                               per-kernel-class device time in dd_stats (slower; default 0) */
+                               per-kernel-class device time in dd_stats (slower; default 0);
+                               2: only the trailing-update launches (DD_K_UPDATE, the dominant
+                               kernel), the other classes reporting 0 */
   int32_t simt_update;      /* MIXED: 1 runs the trailing updates on the FP32 FMA pipes instead of
                                the tensor cores (comparison baseline; default 0) */
   int32_t update_panels;    /* MIXED, tensor cores: panels fused per trailing-update pass, 1 (C read

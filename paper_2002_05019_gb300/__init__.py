@@ -132,7 +132,7 @@ class Solver:
 
     def __init__(self, subdomains, n_dual: int, precision: str = "fp64", refine_tol: float = 1e-13,
                  max_refine: int | None = None, tree_parent=None, centroids=None, stream=None, device: int = 0,
-                 time_kernels: bool = False, simt_update: bool = False, pivoting: int | None = None,
+                 time_kernels: bool | int = False, simt_update: bool = False, pivoting: int | None = None,
                  update_panels: int | None = None):
         lib = load()
         self._keep = []
@@ -169,7 +169,8 @@ class Solver:
         if stream is not None:
             opt.cuda_stream = C.c_void_p(int(stream))
         opt.device = device
-        opt.time_kernels = 1 if time_kernels else 0
+        # True / 1: every launch; 2: the trailing-update launches only
+        opt.time_kernels = 2 if (not isinstance(time_kernels, bool) and time_kernels == 2) else (1 if time_kernels else 0)
         opt.simt_update = 1 if simt_update else 0
         if update_panels is not None:
             opt.update_panels = int(update_panels)   # tensor-core update: 1 or 2 panels per pass

@@ -544,7 +544,7 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
   h->n_sub = n_sub;
   h->n_dual = n_dual;
   h->elem = opt.precision == DD_PREC_FP64 ? 16 : 8;
-  h->time_kernels = opt.time_kernels ? 1 : 0;
+  h->time_kernels = opt.time_kernels == 2 ? 2 : (opt.time_kernels ? 1 : 0);
   h->use_tc = (opt.precision == DD_PREC_MIXED && !opt.simt_update) ? 1 : 0;
   h->pair_panels = h->use_tc && opt.update_panels == 2;
   h->pivoting = opt.pivoting;
@@ -1098,7 +1098,8 @@ int dd_set_values(dd_handle* h, const dd_c128* vals) {
 
 // Enqueues one numeric factorization on stream s (and the look-ahead stream):
 // the same launch sequence every call, so it can be captured once as a CUDA
-// graph.  With time_kernels, event pairs around every launch (not captured).
+// graph.  With time_kernels, event pairs around every launch (1) or around the
+// trailing-update launches only (2).
 static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& nev, std::vector<int>& cls_of) {
   const int p = h->prec == DD_PREC_FP64 ? 0 : 1;
   k_status_init<<<1, 1, 0, s>>>(h->d_status);
@@ -1108,7 +1109,7 @@ static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& n
   nev = 0;
   cls_of.assign(h->time_kernels ? kMaxTimed : 0, 0);
   auto mark_on = [&](int cls, bool begin, cudaStream_t on) -> cudaError_t {
-    if (!h->time_kernels || nev >= 2 * kMaxTimed) return cudaSuccess;
+    if (!h->time_kernels || (h->time_kernels == 2 && cls != DD_K_UPDATE) || nev >= 2 * kMaxTimed) return cudaSuccess;
     if (begin) cls_of[nev / 2] = cls;
     while (h->kev.size() <= nev) {
       cudaEvent_t e;

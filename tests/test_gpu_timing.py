@@ -1,0 +1,30 @@
+"""GPU: per-launch kernel timing of the factorization (dd_options.time_kernels):
+0 none, 1 every launch (a device time per kernel class), 2 the trailing-update
+launches only.  The event nodes change neither the launches nor the result."""
+import numpy as np
+import pytest
+
+import femgen
+import paper_2002_05019_gb300 as dd
+
+pytestmark = pytest.mark.gpu
+
+
+def test_kernel_timing_modes():
+    p = femgen.plain_c1()
+    f = dd.stacked_loads(p)
+    res = {}
+    for mode in (0, 1, 2):
+        s = dd.Solver.from_problem(p, precision="mixed", time_kernels=mode)
+        s.factor()
+        st = s.stats()
+        u, _ = s.solve(f)
+        res[mode] = (st["kernel_ms"], st["kernel_launches"], u)
+        s.free()
+    (km0, kl0, u0), (km1, kl1, u1), (km2, kl2, u2) = res[0], res[1], res[2]
+    assert all(v == 0 for v in km0.values())
+    assert km1["update"] > 0 and km1["diag"] > 0 and km1["trsm"] > 0
+    assert km2["update"] > 0 and km2["diag"] == 0 and km2["trsm"] == 0 and km2["assemble"] == 0
+    assert kl0 == kl1 == kl2
+    for u in (u1, u2):
+        assert np.linalg.norm(u - u0) <= 1e-12 * np.linalg.norm(u0)
