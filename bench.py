@@ -358,6 +358,8 @@ def ours_arm(args):
                    "parallelism": f"replicas x{ws}"},
         "tflops": flops_step / t_step / 1e12,
         "refine_iters": iters, "refine_tol": args.refine_tol, "backward_error": main["backward_error"],
+        # setup (validation, symbolic analysis, device uploads) is outside the timed step
+        "setup_ms": st["t_setup_ms"],
         "roofline": roofline,
         "gpu_launches": main["launches"],
         "clocks": main["clocks"],

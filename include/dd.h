@@ -126,7 +126,8 @@ typedef struct {
   double flops_solve;        /* algorithmic real flops of one direct solve with one right-hand side */
   int64_t bytes_factor;      /* bytes of the stored factors (L, D of every front) */
   int64_t bytes_device;      /* device bytes held by the handle */
-  double t_setup_ms, t_factor_ms, t_solve_ms;   /* last call, device-timed */
+  double t_setup_ms;          /* dd_setup wall time: validation, symbolic analysis, device uploads */
+  double t_factor_ms, t_solve_ms;   /* last call, device-timed */
   double growth;             /* max |L D| entry / max |A| entry over all fronts (pivot growth) */
   double min_pivot;          /* min |d| over all pivots */
   int32_t refine_iters;      /* last dd_solve */

@@ -14,6 +14,7 @@
 //     ancestor duals reached through its subtree's cliques; that structure is
 //     the block fill of the auxiliary factor.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -515,6 +516,7 @@ void dd_free(dd_handle* h) {
 }
 
 int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n_dual, const dd_options* opt_in) {
+  const auto t_begin = std::chrono::steady_clock::now();
   if (!out) return DD_ERR_INVALID_ARG;
   *out = nullptr;
   if (n_sub < 1 || n_dual < 0 || !subs) return DD_ERR_INVALID_ARG;
@@ -1079,6 +1081,7 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
   h->stats.n_primal = h->n_loc;
   h->stats.bytes_factor = bytes_factor;
   h->stats.bytes_device = (int64_t)A.bytes;
+  h->stats.t_setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_begin).count();
   *out = h.release();
   return DD_OK;
 }
