@@ -16,7 +16,11 @@ Routes to the same solution x = A^{-1} b of the assembled FEM system:
                               partial pivoting (inputs whose LDL^T needs pivoting);
   * dense.ldlt_bk_restricted - LDL^T with Bunch-Kaufman pivoting restricted to
                               diagonal blocks (the pivoting rule of Section II);
-  * refine.residual_dd      - double-double residuals for iterative refinement.
+  * refine.residual_dd      - double-double residuals for iterative refinement;
+  * symbolic.fronts_by_elimination / fronts_by_tree - the front tree of the
+                              auxiliary matrix's symbolic factorization
+                              (Section II), by clique-graph elimination and
+                              from the domain tree.
 
 Parity status: pinned by closed forms and library special cases (see the
 tests); the paper prints no numerical values, so no value of the paper pins it.
@@ -25,7 +29,9 @@ from .dense import lu_solve, ldlt, ldlt_solve, ldlt_bk_restricted, ldlt_bk_solve
 from .skyline import BandLDLT, rcm, envelope_entries
 from .dd import DDOracle, subdomain_schur, arrow_residual, local_B, arrow_dense, arrow_solve
 from .refine import residual_dd, refine, backward_error
+from .symbolic import fronts_by_elimination, fronts_by_tree, lca_fronts, dual_domains
 
 __all__ = ["lu_solve", "ldlt", "ldlt_solve", "ldlt_bk_restricted", "ldlt_bk_solve", "BandLDLT", "rcm", "envelope_entries",
            "DDOracle", "subdomain_schur", "arrow_residual", "local_B", "arrow_dense", "arrow_solve",
+           "fronts_by_elimination", "fronts_by_tree", "lca_fronts", "dual_domains",
            "residual_dd", "refine", "backward_error"]

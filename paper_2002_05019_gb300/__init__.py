@@ -72,7 +72,8 @@ class Schedule(C.Structure):
 
 EXPORTS = ["dd_default_options", "dd_setup", "dd_set_values", "dd_factor", "dd_solve", "dd_solve_subset", "dd_get_schur",
            "dd_set_schedule", "dd_autotune",
-           "dd_get_stats", "dd_strerror", "dd_free", "dd_dense_solve_noalloc", "dd_selftest_wait_timeout"]
+           "dd_get_stats", "dd_strerror", "dd_free", "dd_dense_solve_noalloc", "dd_selftest_wait_timeout",
+           "dd_symbolic"]
 
 
 def library_path() -> str:
@@ -107,6 +108,8 @@ def load(build_if_missing: bool = True):
     lib.dd_free.argtypes = [C.c_void_p]
     lib.dd_free.restype = None
     lib.dd_selftest_wait_timeout.argtypes = [C.c_void_p]
+    lib.dd_symbolic.argtypes = [C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
     lib.dd_dense_solve_noalloc.argtypes = [C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64,
                                            C.c_void_p, C.c_int64, C.c_void_p]
     _lib = lib
@@ -127,6 +130,72 @@ def _is_torch(x) -> bool:
     return type(x).__module__.startswith("torch")
 
 
+def _marshal(subdomains, tree_parent=None, centroids=None):
+    """dd_subdomain array and default dd_options for a list of domain dicts;
+    returns (subs, opt, keep), keep holding the arrays the pointers refer to."""
+    lib = load()
+    keep = []
+    subs = (Subdomain * len(subdomains))()
+    for k, s in enumerate(subdomains):
+        rp = np.ascontiguousarray(s["indptr"], dtype=np.int32)
+        ci = np.ascontiguousarray(s["indices"], dtype=np.int32)
+        va = np.ascontiguousarray(s["data"], dtype=np.complex128)
+        bd = np.ascontiguousarray(s["b_dual"], dtype=np.int32)
+        bl = np.ascontiguousarray(s["b_local"], dtype=np.int32)
+        bs = np.ascontiguousarray(s["b_sign"], dtype=np.int8)
+        keep += [rp, ci, va, bd, bl, bs]
+        subs[k] = Subdomain(int(s["n"]), _ptr(rp, C.c_int32), _ptr(ci, C.c_int32), va.ctypes.data, bd.size,
+                            _ptr(bd, C.c_int32), _ptr(bl, C.c_int32), _ptr(bs, C.c_int8))
+    opt = Options()
+    lib.dd_default_options(C.byref(opt))
+    if tree_parent is not None:
+        tp = np.ascontiguousarray(tree_parent, dtype=np.int32)
+        keep.append(tp)
+        opt.tree_parent = _ptr(tp, C.c_int32)
+    if centroids is not None:
+        ce = np.ascontiguousarray(centroids, dtype=np.float64).ravel()
+        keep.append(ce)
+        opt.centroids = _ptr(ce, C.c_double)
+    return subs, opt, keep
+
+
+def _problem_subs(p):
+    return [dict(n=s.n, indptr=s.indptr, indices=s.indices, data=s.data, b_dual=s.b_dual,
+                 b_local=s.b_local, b_sign=s.b_sign) for s in p.subs]
+
+
+def symbolic(subdomains, n_dual: int, tree_parent=None, centroids=None) -> dict:
+    """The front tree of the library's symbolic analysis (dd_symbolic; host only,
+    no GPU): parent, ne, nu per front (domains first, then separator fronts in
+    post-order), the front of every dual, and each front's update-row duals."""
+    lib = load()
+    subs, opt, keep = _marshal(subdomains, tree_parent, centroids)
+    n_sub = len(subdomains)
+    cap = 2 * n_sub + 1
+    nf = C.c_int32(0)
+    parent, ne, nu = (np.zeros(cap, np.int32) for _ in range(3))
+    dual_front = np.zeros(max(n_dual, 1), np.int32)
+    upd_ptr = np.zeros(cap + 1, np.int64)
+    st = lib.dd_symbolic(n_sub, subs, int(n_dual), C.byref(opt), cap, C.byref(nf), parent.ctypes.data,
+                         ne.ctypes.data, nu.ctypes.data, dual_front.ctypes.data, 0, upd_ptr.ctypes.data, None)
+    _check(st, "dd_symbolic")
+    n = nf.value
+    upd_idx = np.zeros(max(int(upd_ptr[n]), 1), np.int32)
+    st = lib.dd_symbolic(n_sub, subs, int(n_dual), C.byref(opt), cap, C.byref(nf), parent.ctypes.data,
+                         ne.ctypes.data, nu.ctypes.data, dual_front.ctypes.data, upd_idx.size, upd_ptr.ctypes.data,
+                         upd_idx.ctypes.data)
+    _check(st, "dd_symbolic")
+    del keep
+    return {"n_front": n, "parent": parent[:n].copy(), "ne": ne[:n].copy(), "nu": nu[:n].copy(),
+            "dual_front": dual_front[:n_dual].copy(),
+            "upd": [upd_idx[upd_ptr[x]:upd_ptr[x + 1]].copy() for x in range(n)]}
+
+
+def symbolic_problem(p) -> dict:
+    """symbolic() for a femgen.Problem, with its domain tree."""
+    return symbolic(_problem_subs(p), p.n_dual, tree_parent=p.rcb.parent)
+
+
 class Solver:
     """One factorization of an arrowhead system on one GPU."""
 
@@ -135,37 +204,15 @@ class Solver:
                  time_kernels: bool | int = False, simt_update: bool = False, pivoting: int | None = None,
                  update_panels: int | None = None):
         lib = load()
-        self._keep = []
-        subs = (Subdomain * len(subdomains))()
+        subs, opt, self._keep = _marshal(subdomains, tree_parent, centroids)
         self.n = [int(s["n"]) for s in subdomains]
         self.n_loc = int(sum(self.n))
         self.n_dual = int(n_dual)
-        self.nnz = []
-        for k, s in enumerate(subdomains):
-            rp = np.ascontiguousarray(s["indptr"], dtype=np.int32)
-            ci = np.ascontiguousarray(s["indices"], dtype=np.int32)
-            va = np.ascontiguousarray(s["data"], dtype=np.complex128)
-            bd = np.ascontiguousarray(s["b_dual"], dtype=np.int32)
-            bl = np.ascontiguousarray(s["b_local"], dtype=np.int32)
-            bs = np.ascontiguousarray(s["b_sign"], dtype=np.int8)
-            self._keep += [rp, ci, va, bd, bl, bs]
-            subs[k] = Subdomain(int(s["n"]), _ptr(rp, C.c_int32), _ptr(ci, C.c_int32), va.ctypes.data, bd.size,
-                                _ptr(bd, C.c_int32), _ptr(bl, C.c_int32), _ptr(bs, C.c_int8))
-            self.nnz.append(int(ci.size))
-        opt = Options()
-        lib.dd_default_options(C.byref(opt))
+        self.nnz = [int(np.size(s["indices"])) for s in subdomains]
         opt.precision = PRECISION[precision]
         opt.refine_tol = refine_tol
         if max_refine is not None:
             opt.max_refine = int(max_refine)
-        if tree_parent is not None:
-            tp = np.ascontiguousarray(tree_parent, dtype=np.int32)
-            self._keep.append(tp)
-            opt.tree_parent = _ptr(tp, C.c_int32)
-        if centroids is not None:
-            ce = np.ascontiguousarray(centroids, dtype=np.float64).ravel()
-            self._keep.append(ce)
-            opt.centroids = _ptr(ce, C.c_double)
         if stream is not None:
             opt.cuda_stream = C.c_void_p(int(stream))
         opt.device = device
@@ -185,10 +232,8 @@ class Solver:
     @classmethod
     def from_problem(cls, p, **kw):
         """Build from a femgen.Problem (domain CSRs, B entries and the domain tree)."""
-        subs = [dict(n=s.n, indptr=s.indptr, indices=s.indices, data=s.data, b_dual=s.b_dual,
-                     b_local=s.b_local, b_sign=s.b_sign) for s in p.subs]
         kw.setdefault("tree_parent", p.rcb.parent)
-        return cls(subs, p.n_dual, **kw)
+        return cls(_problem_subs(p), p.n_dual, **kw)
 
     def set_values(self, vals):
         """New values for every A_i (same patterns), domain after domain: host array or CUDA tensor."""
@@ -306,4 +351,5 @@ def unstack(problem, u: np.ndarray):
     return [u[offs[k]:offs[k + 1]] for k in range(problem.n_sub)]
 
 
-__all__ = ["Solver", "DDError", "load", "library_path", "stacked_loads", "unstack", "EXPORTS", "PRECISION"]
+__all__ = ["Solver", "DDError", "load", "library_path", "stacked_loads", "unstack", "symbolic", "symbolic_problem",
+           "EXPORTS", "PRECISION"]

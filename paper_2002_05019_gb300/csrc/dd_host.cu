@@ -515,7 +515,26 @@ void dd_free(dd_handle* h) {
   cudaSetDevice(cur);
 }
 
-int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n_dual, const dd_options* opt_in) {
+}  // extern "C"
+
+namespace {
+// Front tree of the symbolic analysis, for dd_symbolic (host only)
+struct SymbolicOut {
+  int32_t max_fronts;
+  int32_t* n_front;
+  int32_t* parent;
+  int32_t* ne;
+  int32_t* nu;
+  int32_t* dual_front;
+  int64_t upd_cap;
+  int64_t* upd_ptr;
+  int32_t* upd_idx;
+};
+
+// dd_setup; with sym, only its host-side validation and symbolic analysis,
+// whose front tree is written to sym (no device is touched)
+int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n_dual, const dd_options* opt_in,
+               const SymbolicOut* sym) {
   const auto t_begin = std::chrono::steady_clock::now();
   if (!out) return DD_ERR_INVALID_ARG;
   *out = nullptr;
@@ -996,6 +1015,28 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
     L.n_bwd = (int)((int64_t)h_bwd.size() - L.bwd_off);
   }
 
+  if (sym) {
+    *sym->n_front = n_front;
+    if (sym->max_fronts < n_front) return DD_ERR_INVALID_ARG;
+    int64_t tot = 0;
+    for (int x = 0; x < n_front; ++x) {
+      sym->parent[x] = par[x];
+      sym->ne[x] = h->fronts[x].ne;
+      sym->nu[x] = h->fronts[x].nu;
+      if (sym->upd_ptr) sym->upd_ptr[x] = tot;
+      tot += (int64_t)upd[x].size();
+    }
+    if (sym->upd_ptr) sym->upd_ptr[n_front] = tot;
+    for (int d = 0; d < n_dual; ++d) sym->dual_front[d] = dual_node[d];
+    if (sym->upd_idx) {
+      if (sym->upd_cap < tot) return DD_ERR_INVALID_ARG;
+      int64_t q = 0;
+      for (int x = 0; x < n_front; ++x)
+        for (int32_t d : upd[x]) sym->upd_idx[q++] = d;
+    }
+    return DD_OK;
+  }
+
   // ---- upload (everything above is host-only validation and analysis) -------------
   int ndev = 0;
   if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -1084,6 +1125,22 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
   h->stats.t_setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_begin).count();
   *out = h.release();
   return DD_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n_dual, const dd_options* opt_in) {
+  return setup_impl(out, n_sub, subs, n_dual, opt_in, nullptr);
+}
+
+int dd_symbolic(int32_t n_sub, const dd_subdomain* subs, int32_t n_dual, const dd_options* opt, int32_t max_fronts,
+                int32_t* n_front, int32_t* parent, int32_t* ne, int32_t* nu, int32_t* dual_front, int64_t upd_cap,
+                int64_t* upd_ptr, int32_t* upd_idx) {
+  if (!n_front || !parent || !ne || !nu || (n_dual > 0 && !dual_front) || (upd_idx && !upd_ptr)) return DD_ERR_INVALID_ARG;
+  const SymbolicOut sym{max_fronts, n_front, parent, ne, nu, dual_front, upd_cap, upd_ptr, upd_idx};
+  dd_handle* unused = nullptr;
+  return setup_impl(&unused, n_sub, subs, n_dual, opt, &sym);
 }
 
 int dd_set_values(dd_handle* h, const dd_c128* vals) {

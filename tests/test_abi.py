@@ -64,6 +64,31 @@ def test_null_handles_are_rejected():
     assert lib.dd_autotune(None, 1, None) == 1
     assert lib.dd_set_schedule(None, None) == 1
     assert lib.dd_get_stats(None, None) == 1
+    # dd_symbolic: NULL outputs
+    assert lib.dd_symbolic(1, None, 0, None, 4, None, None, None, None, None, 0, None, None) == 1
+
+
+def test_symbolic_output_limits():
+    """dd_symbolic reports the front count when max_fronts is too small, and
+    rejects an update-row buffer that cannot hold the rows."""
+    import ctypes as C
+    lib = dd.load()
+    p = femgen.tiny(2, 2)
+    subs, opt, keep = dd._marshal(dd._problem_subs(p), tree_parent=p.rcb.parent)
+    nf = C.c_int32(0)
+    small = np.zeros(2, np.int32)
+    dual_front = np.zeros(p.n_dual, np.int32)
+    st = lib.dd_symbolic(p.n_sub, subs, p.n_dual, C.byref(opt), 2, C.byref(nf), small.ctypes.data, small.ctypes.data,
+                         small.ctypes.data, dual_front.ctypes.data, 0, None, None)
+    assert st == 1 and nf.value == 2 * p.n_sub - 1
+    cap = nf.value
+    par, ne, nu = (np.zeros(cap, np.int32) for _ in range(3))
+    ptr = np.zeros(cap + 1, np.int64)
+    idx = np.zeros(1, np.int32)
+    st = lib.dd_symbolic(p.n_sub, subs, p.n_dual, C.byref(opt), cap, C.byref(nf), par.ctypes.data, ne.ctypes.data,
+                         nu.ctypes.data, dual_front.ctypes.data, 1, ptr.ctypes.data, idx.ctypes.data)
+    assert st == 1 and ptr[cap] > 1
+    del keep
 
 
 def _subs(p):
