@@ -6,8 +6,8 @@ of the solver's arithmetic, and both the CPU oracle and the GPU library take
 their inputs from it.
 """
 from .mesh import Mesh, box_mesh, kuhn_edge_count, boundary_edge_mask
-from .problems import (Problem, Subdomain, build_problem, plain_c1, batched_c2, medium, large_c4,
+from .problems import (Problem, Subdomain, build_problem, plain_c1, batched_c2, medium, big_domains, large_c4,
                        multi_rhs_c5, tiny, K0)
 
 __all__ = ["Mesh", "box_mesh", "kuhn_edge_count", "boundary_edge_mask", "Problem", "Subdomain",
-           "build_problem", "plain_c1", "batched_c2", "medium", "large_c4", "multi_rhs_c5", "tiny", "K0"]
+           "build_problem", "plain_c1", "batched_c2", "medium", "big_domains", "large_c4", "multi_rhs_c5", "tiny", "K0"]

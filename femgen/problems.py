@@ -304,6 +304,13 @@ def medium(rhs="edge", **kw) -> Problem:
                          eps="random", rhs=rhs, **kw)
 
 
+def big_domains(n: int = 24, rhs="edge", **kw) -> Problem:
+    """8 equal domains (2x2x2) of an n^3 mesh: 13,428 edges each at n = 24
+    (102,024 DoFs), 2,863 at n = 14 -- domains above the dense-front range,
+    for the sparse-domain route."""
+    return build_problem(f"big-n{n}-s8", n, 3, rhs=rhs, **kw)
+
+
 def large_c4(rhs="edge", **kw) -> Problem:
     """n = 65, 2048 jittered-bisection domains of 500..2500 edges: 1,960,595 DoFs."""
     return build_problem("large-n65-s2048", 65, 11, split_range=(0.37, 0.63), size_range=(500, 2500),

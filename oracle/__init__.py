@@ -12,6 +12,8 @@ Routes to the same solution x = A^{-1} b of the assembled FEM system:
   * dd.DDOracle             - the paper's decomposition route (Section II):
                               per-domain LDL^T, F = sum B_i A_i^{-1} B_i^T,
                               F lambda = d, primal recovery;
+  * dd.SparseDDOracle       - the same route with sparse (SuperLU) domain
+                              factorizations, for domains beyond the dense reach;
   * dd.arrow_solve          - the arrowhead system solved undecomposed by LU with
                               partial pivoting (inputs whose LDL^T needs pivoting);
   * dense.ldlt_bk_restricted - LDL^T with Bunch-Kaufman pivoting restricted to
@@ -27,11 +29,11 @@ tests); the paper prints no numerical values, so no value of the paper pins it.
 """
 from .dense import lu_solve, ldlt, ldlt_solve, ldlt_bk_restricted, ldlt_bk_solve
 from .skyline import BandLDLT, rcm, envelope_entries
-from .dd import DDOracle, subdomain_schur, arrow_residual, local_B, arrow_dense, arrow_solve
+from .dd import DDOracle, SparseDDOracle, gather_copies, subdomain_schur, arrow_residual, local_B, arrow_dense, arrow_solve
 from .refine import residual_dd, refine, backward_error
 from .symbolic import fronts_by_elimination, fronts_by_tree, lca_fronts, dual_domains
 
 __all__ = ["lu_solve", "ldlt", "ldlt_solve", "ldlt_bk_restricted", "ldlt_bk_solve", "BandLDLT", "rcm", "envelope_entries",
-           "DDOracle", "subdomain_schur", "arrow_residual", "local_B", "arrow_dense", "arrow_solve",
+           "DDOracle", "SparseDDOracle", "gather_copies", "subdomain_schur", "arrow_residual", "local_B", "arrow_dense", "arrow_solve",
            "fronts_by_elimination", "fronts_by_tree", "lca_fronts", "dual_domains",
            "residual_dd", "refine", "backward_error"]
