@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rp
   __shared__ S yj[T];
   __shared__ S dv[T];            // the pivots d when Lt holds L_jj^{-1}
   constexpr int kUChunk = sizeof(S) == 8 ? 512 : 256;
-  __shared__ S xu[kUChunk];      // gathered ancestor duals of the update rows
+  __shared__ S xu[kUChunk];      // gathered ancestor duals of the update rows; then each awaited tile's x_i (non-read-ahead form)
   __shared__ S g0s[T], g1s[T];   // D_j^{-1} coefficients when the tile pivoted
   __shared__ int qs[T], perm[T];
   const Task t = tasks[blockIdx.x];
