@@ -46,6 +46,33 @@ int dd_symbolic(int32_t n_sub, const dd_subdomain* subs, int32_t n_dual, const d
                 int32_t max_fronts, int32_t* n_front, int32_t* parent, int32_t* ne, int32_t* nu,
                 int32_t* dual_front, int64_t upd_cap, int64_t* upd_ptr, int32_t* upd_idx);
 
+/* Nested-dissection symbolic analysis of one domain matrix, for domains
+ * beyond the dense-front range (Section II factors each domain with a sparse
+ * direct solver); host only, touching no device, and not yet used by
+ * dd_factor (whose domain fronts are dense).  The rows flagged in is_last (the
+ * interface rows that B couples to the duals; NULL: none) are eliminated last,
+ * in the root front; the others by nested dissection -- separators are middle
+ * levels of breadth-first level structures from pseudo-peripheral vertices --
+ * down to leaves of at most leaf_max rows.
+ *
+ * Input: the n x n pattern in CSR (rowptr[n + 1], colind; 0-based, symmetric,
+ * the diagonal optional).  Outputs, caller-allocated:
+ *   n_front              fronts of the tree (also written when max_fronts is too small)
+ *   parent[max_fronts]   parent front, -1 at the root; children precede parents
+ *   ne[max_fronts]       rows eliminated in the front
+ *   nu[max_fronts]       its update rows (later rows coupled to it or its subtree)
+ *   order[n]             elimination order (row eliminated at position k)
+ *   front_of[n]          front eliminating each row
+ *   stored               entries of the fronts' strictly lower L: sum ne(ne-1)/2 + ne nu
+ *   upd_ptr[max_fronts + 1], upd_idx[upd_cap] (optional, NULL to skip): the
+ *                        update rows of front x, ascending
+ * Returns DD_OK, DD_ERR_NOT_SYMMETRIC (pattern), or DD_ERR_INVALID_ARG (bad
+ * sizes or indices, a NULL output, max_fronts or upd_cap too small). */
+int dd_domain_symbolic(int32_t n, const int32_t* rowptr, const int32_t* colind, const int8_t* is_last,
+                       int32_t leaf_max, int32_t max_fronts, int32_t* n_front, int32_t* parent, int32_t* ne,
+                       int32_t* nu, int32_t* order, int32_t* front_of, int64_t* stored, int64_t upd_cap,
+                       int64_t* upd_ptr, int32_t* upd_idx);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,7 +22,10 @@ Routes to the same solution x = A^{-1} b of the assembled FEM system:
   * symbolic.fronts_by_elimination / fronts_by_tree - the front tree of the
                               auxiliary matrix's symbolic factorization
                               (Section II), by clique-graph elimination and
-                              from the domain tree.
+                              from the domain tree;
+  * domain_symbolic          - validity of a nested dissection of one domain
+                              and its front structure, by row-by-row graph
+                              elimination and by reach.
 
 Parity status: pinned by closed forms and library special cases (see the
 tests); the paper prints no numerical values, so no value of the paper pins it.
@@ -32,8 +35,9 @@ from .skyline import BandLDLT, rcm, envelope_entries
 from .dd import DDOracle, SparseDDOracle, gather_copies, subdomain_schur, arrow_residual, local_B, arrow_dense, arrow_solve
 from .refine import residual_dd, refine, backward_error
 from .symbolic import fronts_by_elimination, fronts_by_tree, lca_fronts, dual_domains
+from . import domain_symbolic
 
 __all__ = ["lu_solve", "ldlt", "ldlt_solve", "ldlt_bk_restricted", "ldlt_bk_solve", "BandLDLT", "rcm", "envelope_entries",
            "DDOracle", "SparseDDOracle", "gather_copies", "subdomain_schur", "arrow_residual", "local_B", "arrow_dense", "arrow_solve",
-           "fronts_by_elimination", "fronts_by_tree", "lca_fronts", "dual_domains",
+           "fronts_by_elimination", "fronts_by_tree", "lca_fronts", "dual_domains", "domain_symbolic",
            "residual_dd", "refine", "backward_error"]

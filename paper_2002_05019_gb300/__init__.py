@@ -73,7 +73,7 @@ class Schedule(C.Structure):
 EXPORTS = ["dd_default_options", "dd_setup", "dd_set_values", "dd_factor", "dd_solve", "dd_solve_subset", "dd_get_schur",
            "dd_set_schedule", "dd_autotune",
            "dd_get_stats", "dd_strerror", "dd_free", "dd_dense_solve_noalloc", "dd_selftest_wait_timeout",
-           "dd_symbolic"]
+           "dd_symbolic", "dd_domain_symbolic"]
 
 
 def library_path() -> str:
@@ -108,6 +108,9 @@ def load(build_if_missing: bool = True):
     lib.dd_free.argtypes = [C.c_void_p]
     lib.dd_free.restype = None
     lib.dd_selftest_wait_timeout.argtypes = [C.c_void_p]
+    lib.dd_domain_symbolic.argtypes = [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
+                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
     lib.dd_symbolic.argtypes = [C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
     lib.dd_dense_solve_noalloc.argtypes = [C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64,
@@ -189,6 +192,32 @@ def symbolic(subdomains, n_dual: int, tree_parent=None, centroids=None) -> dict:
     return {"n_front": n, "parent": parent[:n].copy(), "ne": ne[:n].copy(), "nu": nu[:n].copy(),
             "dual_front": dual_front[:n_dual].copy(),
             "upd": [upd_idx[upd_ptr[x]:upd_ptr[x + 1]].copy() for x in range(n)]}
+
+
+def domain_symbolic(indptr, indices, is_last=None, leaf_max: int = 256) -> dict:
+    """Nested-dissection front tree of one domain matrix (dd_domain_symbolic;
+    host only): rows flagged in is_last are eliminated last, in the root."""
+    lib = load()
+    rp = np.ascontiguousarray(indptr, dtype=np.int32)
+    ci = np.ascontiguousarray(indices, dtype=np.int32)
+    n = rp.size - 1
+    il = None if is_last is None else np.ascontiguousarray(is_last, dtype=np.int8)
+    cap = max(2 * n + 1, 1)
+    nf = C.c_int32(0)
+    stored = C.c_int64(0)
+    parent, ne, nu = (np.zeros(cap, np.int32) for _ in range(3))
+    order, front_of = np.zeros(max(n, 1), np.int32), np.zeros(max(n, 1), np.int32)
+    upd_ptr = np.zeros(cap + 1, np.int64)
+    args = (n, rp.ctypes.data, ci.ctypes.data, None if il is None else il.ctypes.data, int(leaf_max), cap,
+            C.byref(nf), parent.ctypes.data, ne.ctypes.data, nu.ctypes.data, order.ctypes.data,
+            front_of.ctypes.data, C.byref(stored))
+    _check(lib.dd_domain_symbolic(*args, 0, upd_ptr.ctypes.data, None), "dd_domain_symbolic")
+    k = nf.value
+    upd_idx = np.zeros(max(int(upd_ptr[k]), 1), np.int32)
+    _check(lib.dd_domain_symbolic(*args, upd_idx.size, upd_ptr.ctypes.data, upd_idx.ctypes.data), "dd_domain_symbolic")
+    return {"n_front": k, "parent": parent[:k].copy(), "ne": ne[:k].copy(), "nu": nu[:k].copy(),
+            "order": order[:n].copy(), "front_of": front_of[:n].copy(), "stored": stored.value,
+            "upd": [upd_idx[upd_ptr[x]:upd_ptr[x + 1]].copy() for x in range(k)]}
 
 
 def symbolic_problem(p) -> dict:
@@ -352,4 +381,5 @@ def unstack(problem, u: np.ndarray):
 
 
 __all__ = ["Solver", "DDError", "load", "library_path", "stacked_loads", "unstack", "symbolic", "symbolic_problem",
+           "domain_symbolic",
            "EXPORTS", "PRECISION"]
