@@ -73,6 +73,26 @@ int dd_domain_symbolic(int32_t n, const int32_t* rowptr, const int32_t* colind, 
                        int32_t* nu, int32_t* order, int32_t* front_of, int64_t* stored, int64_t upd_cap,
                        int64_t* upd_ptr, int32_t* upd_idx);
 
+/* The assembly maps of the same analysis, for a multifrontal factorization
+ * of the domain over its front tree.  Front x holds rows[rows_ptr[x] ..
+ * rows_ptr[x + 1]): its ne[x] own rows, then its update rows, both in
+ * elimination order.  Outputs, caller-allocated (call once with rows = NULL
+ * for the sizes: n_front, parent, ne and rows_ptr are then written):
+ *   parent[max_fronts], ne[max_fronts], rows_ptr[max_fronts + 1]
+ *   rows[rows_cap]     the domain row of every front row
+ *   ea_map[rows_cap]   for an update row of a front, its row in the parent
+ *                      front (extend-add); -1 for own rows and at the root
+ *   a_front[nnz], a_row[nnz], a_col[nnz]  for CSR entry q = (r, c): the front
+ *                      and the (row, column) there that receive a_rc, column
+ *                      r being an own row of that front; -1 for the entries
+ *                      left to their mirror (c eliminated before r)
+ * Returns as dd_domain_symbolic (DD_ERR_INVALID_ARG also for rows_cap too
+ * small or a NULL map with rows given). */
+int dd_domain_assembly(int32_t n, const int32_t* rowptr, const int32_t* colind, const int8_t* is_last,
+                       int32_t leaf_max, int32_t max_fronts, int32_t* n_front, int32_t* parent, int32_t* ne,
+                       int64_t rows_cap, int64_t* rows_ptr, int32_t* rows, int32_t* ea_map, int32_t* a_front,
+                       int32_t* a_row, int32_t* a_col);
+
 #ifdef __cplusplus
 }
 #endif

@@ -73,7 +73,7 @@ class Schedule(C.Structure):
 EXPORTS = ["dd_default_options", "dd_setup", "dd_set_values", "dd_factor", "dd_solve", "dd_solve_subset", "dd_get_schur",
            "dd_set_schedule", "dd_autotune",
            "dd_get_stats", "dd_strerror", "dd_free", "dd_dense_solve_noalloc", "dd_selftest_wait_timeout",
-           "dd_symbolic", "dd_domain_symbolic"]
+           "dd_symbolic", "dd_domain_symbolic", "dd_domain_assembly"]
 
 
 def library_path() -> str:
@@ -111,6 +111,9 @@ def load(build_if_missing: bool = True):
     lib.dd_domain_symbolic.argtypes = [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
+    lib.dd_domain_assembly.argtypes = [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
+                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.dd_symbolic.argtypes = [C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
     lib.dd_dense_solve_noalloc.argtypes = [C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64,
@@ -218,6 +221,34 @@ def domain_symbolic(indptr, indices, is_last=None, leaf_max: int = 256) -> dict:
     return {"n_front": k, "parent": parent[:k].copy(), "ne": ne[:k].copy(), "nu": nu[:k].copy(),
             "order": order[:n].copy(), "front_of": front_of[:n].copy(), "stored": stored.value,
             "upd": [upd_idx[upd_ptr[x]:upd_ptr[x + 1]].copy() for x in range(k)]}
+
+
+def domain_assembly(indptr, indices, is_last=None, leaf_max: int = 256) -> dict:
+    """Assembly maps of the domain's front tree (dd_domain_assembly; host only):
+    every front's rows, the extend-add map of its update rows into its parent,
+    and the front position of every CSR entry of A_i."""
+    lib = load()
+    rp = np.ascontiguousarray(indptr, dtype=np.int32)
+    ci = np.ascontiguousarray(indices, dtype=np.int32)
+    n = rp.size - 1
+    il = None if is_last is None else np.ascontiguousarray(is_last, dtype=np.int8)
+    cap = max(2 * n + 1, 1)
+    nf = C.c_int32(0)
+    parent, ne = np.zeros(cap, np.int32), np.zeros(cap, np.int32)
+    rows_ptr = np.zeros(cap + 1, np.int64)
+    head = (n, rp.ctypes.data, ci.ctypes.data, None if il is None else il.ctypes.data, int(leaf_max), cap,
+            C.byref(nf), parent.ctypes.data, ne.ctypes.data)
+    _check(lib.dd_domain_assembly(*head, 0, rows_ptr.ctypes.data, None, None, None, None, None), "dd_domain_assembly")
+    k = nf.value
+    m = int(rows_ptr[k])
+    rows, ea = np.zeros(max(m, 1), np.int32), np.zeros(max(m, 1), np.int32)
+    nnz = int(rp[-1]) if n else 0
+    af, ar, ac = (np.zeros(max(nnz, 1), np.int32) for _ in range(3))
+    _check(lib.dd_domain_assembly(*head, rows.size, rows_ptr.ctypes.data, rows.ctypes.data, ea.ctypes.data,
+                                  af.ctypes.data, ar.ctypes.data, ac.ctypes.data), "dd_domain_assembly")
+    return {"n_front": k, "parent": parent[:k].copy(), "ne": ne[:k].copy(), "rows_ptr": rows_ptr[:k + 1].copy(),
+            "rows": rows[:m].copy(), "ea_map": ea[:m].copy(), "a_front": af[:nnz].copy(), "a_row": ar[:nnz].copy(),
+            "a_col": ac[:nnz].copy()}
 
 
 def symbolic_problem(p) -> dict:
@@ -381,5 +412,5 @@ def unstack(problem, u: np.ndarray):
 
 
 __all__ = ["Solver", "DDError", "load", "library_path", "stacked_loads", "unstack", "symbolic", "symbolic_problem",
-           "domain_symbolic",
+           "domain_symbolic", "domain_assembly",
            "EXPORTS", "PRECISION"]

@@ -160,14 +160,18 @@ struct DomainNd {
   }
 };
 
-}  // namespace
+// The analysis of one domain: its dissection tree and every front's rows.
+struct DomainFronts {
+  int32_t nf = 0;
+  std::vector<int32_t> parent, fof, pos;          // per front; per row: front, elimination position
+  std::vector<std::vector<int32_t>> elim, upd;    // per front: own rows (by position), update rows (by index)
+  int64_t stored = 0;
+};
 
-extern "C" int dd_domain_symbolic(int32_t n, const int32_t* rowptr, const int32_t* colind, const int8_t* is_last,
-                                  int32_t leaf_max, int32_t max_fronts, int32_t* n_front, int32_t* parent,
-                                  int32_t* ne, int32_t* nu, int32_t* order, int32_t* front_of, int64_t* stored,
-                                  int64_t upd_cap, int64_t* upd_ptr, int32_t* upd_idx) {
-  if (n < 0 || leaf_max < 1 || !n_front || !parent || !ne || !nu || !stored || (upd_idx && !upd_ptr)) return DD_ERR_INVALID_ARG;
-  if (n > 0 && (!rowptr || !colind || !order || !front_of)) return DD_ERR_INVALID_ARG;
+int analyse_domain(int32_t n, const int32_t* rowptr, const int32_t* colind, const int8_t* is_last, int32_t leaf_max,
+                   DomainFronts& out) {
+  if (n < 0 || leaf_max < 1) return DD_ERR_INVALID_ARG;
+  if (n > 0 && (!rowptr || !colind)) return DD_ERR_INVALID_ARG;
   if (n > 0 && rowptr[0] != 0) return DD_ERR_INVALID_ARG;
   std::vector<std::vector<int32_t>> adj(n);
   for (int32_t i = 0; i < n; ++i) {
@@ -196,16 +200,13 @@ extern "C" int dd_domain_symbolic(int32_t n, const int32_t* rowptr, const int32_
     nd.new_node(iface);
   }
   const int32_t nf = (int32_t)nd.elim.size();
-  *n_front = nf;
-  if (max_fronts < nf) return DD_ERR_INVALID_ARG;
-
   // elimination order (nodes in creation order: children before parents) and
   // the depth of every node, for the ancestor test
-  std::vector<int32_t> fof(n, -1), depth(nf, 0);
+  std::vector<int32_t> fof(n, -1), pos(n, -1), depth(nf, 0);
   int32_t k = 0;
   for (int32_t x = 0; x < nf; ++x)
     for (int32_t v : nd.elim[x]) {
-      order[k++] = v;
+      pos[v] = k++;
       fof[v] = x;
     }
   for (int32_t x = nf - 1; x >= 0; --x) depth[x] = nd.parent[x] < 0 ? 0 : depth[nd.parent[x]] + 1;
@@ -215,11 +216,10 @@ extern "C" int dd_domain_symbolic(int32_t n, const int32_t* rowptr, const int32_
   };
   // update rows: unknowns of proper ancestors adjacent to this front's own
   // unknowns, or passed up by its children
-  std::vector<std::vector<int32_t>> upd(nf);
-  std::vector<std::vector<int32_t>> children(nf);
+  std::vector<std::vector<int32_t>> upd(nf), children(nf);
   for (int32_t x = 0; x < nf; ++x)
     if (nd.parent[x] >= 0) children[nd.parent[x]].push_back(x);
-  int64_t total = 0, st = 0;
+  int64_t st = 0;
   for (int32_t x = 0; x < nf; ++x) {
     std::vector<int32_t> u;
     for (int32_t v : nd.elim[x])
@@ -233,28 +233,123 @@ extern "C" int dd_domain_symbolic(int32_t n, const int32_t* rowptr, const int32_
     upd[x] = std::move(u);
     const int64_t e = (int64_t)nd.elim[x].size(), a = (int64_t)upd[x].size();
     st += e * (e - 1) / 2 + e * a;
-    total += a;
   }
-  for (int32_t x = 0; x < nf; ++x) {
-    parent[x] = nd.parent[x];
-    ne[x] = (int32_t)nd.elim[x].size();
-    nu[x] = (int32_t)upd[x].size();
+  out.nf = nf;
+  out.parent = nd.parent;
+  out.fof = std::move(fof);
+  out.pos = std::move(pos);
+  out.elim = std::move(nd.elim);
+  out.upd = std::move(upd);
+  out.stored = st;
+  return DD_OK;
+}
+
+}  // namespace
+
+extern "C" int dd_domain_symbolic(int32_t n, const int32_t* rowptr, const int32_t* colind, const int8_t* is_last,
+                                  int32_t leaf_max, int32_t max_fronts, int32_t* n_front, int32_t* parent,
+                                  int32_t* ne, int32_t* nu, int32_t* order, int32_t* front_of, int64_t* stored,
+                                  int64_t upd_cap, int64_t* upd_ptr, int32_t* upd_idx) {
+  if (!n_front || !parent || !ne || !nu || !stored || (upd_idx && !upd_ptr)) return DD_ERR_INVALID_ARG;
+  if (n > 0 && (!order || !front_of)) return DD_ERR_INVALID_ARG;
+  DomainFronts d;
+  const int status = analyse_domain(n, rowptr, colind, is_last, leaf_max, d);
+  if (status != DD_OK) return status;
+  *n_front = d.nf;
+  if (max_fronts < d.nf) return DD_ERR_INVALID_ARG;
+  int64_t total = 0;
+  for (int32_t x = 0; x < d.nf; ++x) {
+    parent[x] = d.parent[x];
+    ne[x] = (int32_t)d.elim[x].size();
+    nu[x] = (int32_t)d.upd[x].size();
+    total += nu[x];
   }
-  for (int32_t v = 0; v < n; ++v) front_of[v] = fof[v];
-  *stored = st;
+  for (int32_t v = 0; v < n; ++v) {
+    order[d.pos[v]] = v;
+    front_of[v] = d.fof[v];
+  }
+  *stored = d.stored;
   if (upd_ptr) {
     int64_t q = 0;
-    for (int32_t x = 0; x < nf; ++x) {
+    for (int32_t x = 0; x < d.nf; ++x) {
       upd_ptr[x] = q;
-      q += (int64_t)upd[x].size();
+      q += (int64_t)d.upd[x].size();
     }
-    upd_ptr[nf] = q;
+    upd_ptr[d.nf] = q;
     if (upd_idx) {
       if (upd_cap < total) return DD_ERR_INVALID_ARG;
       q = 0;
-      for (int32_t x = 0; x < nf; ++x)
-        for (int32_t w : upd[x]) upd_idx[q++] = w;
+      for (int32_t x = 0; x < d.nf; ++x)
+        for (int32_t w : d.upd[x]) upd_idx[q++] = w;
     }
+  }
+  return DD_OK;
+}
+
+extern "C" int dd_domain_assembly(int32_t n, const int32_t* rowptr, const int32_t* colind, const int8_t* is_last,
+                                  int32_t leaf_max, int32_t max_fronts, int32_t* n_front, int32_t* parent,
+                                  int32_t* ne, int64_t rows_cap, int64_t* rows_ptr, int32_t* rows,
+                                  int32_t* ea_map, int32_t* a_front, int32_t* a_row, int32_t* a_col) {
+  if (!n_front || !parent || !ne || !rows_ptr) return DD_ERR_INVALID_ARG;
+  DomainFronts d;
+  const int status = analyse_domain(n, rowptr, colind, is_last, leaf_max, d);
+  if (status != DD_OK) return status;
+  *n_front = d.nf;
+  if (max_fronts < d.nf) return DD_ERR_INVALID_ARG;
+  // a front's rows: its own rows, then its update rows, both in elimination
+  // order (so every child's update rows land in increasing parent rows)
+  for (auto& u : d.upd) std::sort(u.begin(), u.end(), [&](int32_t a, int32_t b) { return d.pos[a] < d.pos[b]; });
+  int64_t q = 0;
+  for (int32_t x = 0; x < d.nf; ++x) {
+    parent[x] = d.parent[x];
+    ne[x] = (int32_t)d.elim[x].size();
+    rows_ptr[x] = q;
+    q += (int64_t)(d.elim[x].size() + d.upd[x].size());
+  }
+  rows_ptr[d.nf] = q;
+  if (!rows) return DD_OK;   // sizes only
+  if (rows_cap < q || !ea_map || (n > 0 && (!a_front || !a_row || !a_col))) return DD_ERR_INVALID_ARG;
+  std::vector<int32_t> loc(n, -1);   // row -> index in the front being filled
+  for (int32_t x = 0; x < d.nf; ++x) {
+    int32_t* rx = rows + rows_ptr[x];
+    int32_t r = 0;
+    for (int32_t v : d.elim[x]) rx[r++] = v;
+    for (int32_t v : d.upd[x]) rx[r++] = v;
+  }
+  // extend-add: each update row of a front, its row in the parent front
+  for (int32_t x = 0; x < d.nf; ++x) {
+    const int32_t p = d.parent[x];
+    const int64_t b = rows_ptr[x];
+    const int32_t e = (int32_t)d.elim[x].size(), m = (int32_t)(rows_ptr[x + 1] - b);
+    for (int32_t r = 0; r < m; ++r) ea_map[b + r] = -1;
+    if (p < 0) continue;
+    const int64_t bp = rows_ptr[p];
+    for (int32_t r = 0; r < (int32_t)(rows_ptr[p + 1] - bp); ++r) loc[rows[bp + r]] = r;
+    for (int32_t r = e; r < m; ++r) ea_map[b + r] = loc[rows[b + r]];
+    for (int32_t r = 0; r < (int32_t)(rows_ptr[p + 1] - bp); ++r) loc[rows[bp + r]] = -1;
+  }
+  // entries of A (symmetric): CSR row r supplies column r of its front; the
+  // entry (r, c) with c eliminated no earlier than r goes to r's front at
+  // (row of c, row of r), the other entries of the row are left to their
+  // mirrors (a_front = -1)
+  for (int32_t x = 0; x < d.nf; ++x) {
+    const int64_t b = rows_ptr[x];
+    for (int64_t r = b; r < rows_ptr[x + 1]; ++r) loc[rows[r]] = (int32_t)(r - b);
+    int bad = 0;
+    for (int32_t r : d.elim[x])
+      for (int32_t qq = rowptr[r]; qq < rowptr[r + 1]; ++qq) {
+        const int32_t c = colind[qq];
+        if (d.pos[c] < d.pos[r]) {
+          a_front[qq] = a_row[qq] = a_col[qq] = -1;
+        } else {
+          a_front[qq] = x;
+          a_row[qq] = loc[c];
+          a_col[qq] = loc[r];
+          bad |= loc[c] < 0;
+        }
+      }
+    for (int64_t r = b; r < rows_ptr[x + 1]; ++r) loc[rows[r]] = -1;
+    if (bad) return DD_ERR_INVALID_ARG;   // not reached for a valid analysis
   }
   return DD_OK;
 }

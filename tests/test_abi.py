@@ -68,6 +68,8 @@ def test_null_handles_are_rejected():
     assert lib.dd_symbolic(1, None, 0, None, 4, None, None, None, None, None, 0, None, None) == 1
     assert lib.dd_domain_symbolic(4, None, None, None, 16, 8, None, None, None, None, None, None, None, 0, None,
                                   None) == 1
+    assert lib.dd_domain_assembly(4, None, None, None, 16, 8, None, None, None, 0, None, None, None, None, None,
+                                  None) == 1
 
 
 def test_symbolic_output_limits():

@@ -87,3 +87,73 @@ def test_planted_mistakes_are_caught():
         adj_only.append(sorted(u))
     el = ods.fronts_by_elimination(s.indptr, s.indices, t["order"], t["front_of"], t["parent"])
     assert adj_only != el["upd"]
+
+
+def _multifrontal_solve(s, mp, b):
+    """Unpivoted multifrontal LDL^T of A_i over the library's front tree, driven
+    only by its assembly maps (entries scattered to fronts, update blocks
+    extend-added into parents), then the forward, diagonal and backward
+    substitutions over the same tree."""
+    nf, parent, ne = mp["n_front"], mp["parent"], mp["ne"]
+    rp, rows, ea = mp["rows_ptr"], mp["rows"], mp["ea_map"]
+    rowid = np.repeat(np.arange(s.n), np.diff(s.indptr))
+    fronts, upd_blocks, facs = [], [None] * nf, [None] * nf
+    for x in range(nf):
+        m = int(rp[x + 1] - rp[x])
+        fronts.append(np.zeros((m, m), dtype=np.complex128))
+    for q in np.flatnonzero(mp["a_front"] >= 0):
+        x, r, c = mp["a_front"][q], mp["a_row"][q], mp["a_col"][q]
+        assert r >= c
+        fronts[x][r, c] += s.data[q]
+    for x in range(nf):
+        Fm = fronts[x]
+        for c in range(x):
+            if parent[c] == x and upd_blocks[c] is not None:
+                idx = ea[rp[c] + ne[c]:rp[c + 1]]
+                assert (idx >= 0).all() and (np.diff(idx) > 0).all()   # increasing rows of the parent
+                Fm[np.ix_(idx, idx)] += upd_blocks[c]
+        Fm = np.tril(Fm) + np.tril(Fm, -1).T
+        e = ne[x]
+        L = np.eye(e, dtype=np.complex128)
+        d = np.zeros(e, dtype=np.complex128)
+        A11 = Fm[:e, :e].copy()
+        for j in range(e):          # unpivoted LDL^T of the own block
+            d[j] = A11[j, j]
+            L[j + 1:, j] = A11[j + 1:, j] / d[j]
+            A11[j + 1:, j + 1:] -= np.outer(L[j + 1:, j], A11[j, j + 1:])
+        L21 = np.linalg.solve(L, Fm[e:, :e].T).T / d       # F21 L11^{-T} D^{-1}
+        upd_blocks[x] = np.tril(Fm[e:, e:] - (L21 * d) @ L21.T)
+        facs[x] = (L, d, L21)
+    y = b.astype(np.complex128).copy()
+    for x in range(nf):             # forward
+        L, d, L21 = facs[x]
+        r = rows[rp[x]:rp[x + 1]]
+        w = np.linalg.solve(L, y[r[:ne[x]]])
+        y[r[:ne[x]]] = w
+        y[r[ne[x]:]] -= L21 @ w
+    for x in range(nf):
+        y[rows[rp[x]:rp[x] + ne[x]]] /= facs[x][1][:, None]
+    for x in range(nf - 1, -1, -1):  # backward
+        L, d, L21 = facs[x]
+        r = rows[rp[x]:rp[x + 1]]
+        y[r[:ne[x]]] = np.linalg.solve(L.T, y[r[:ne[x]]] - L21.T @ y[r[ne[x]:]])
+    return y
+
+
+@pytest.mark.parametrize("name,make,leaf_max", CASES)
+def test_assembly_maps_drive_a_correct_factorization(name, make, leaf_max):
+    s = make()
+    il = _iface(s)
+    mp = dd.domain_assembly(s.indptr, s.indices, il, leaf_max=leaf_max)
+    t = dd.domain_symbolic(s.indptr, s.indices, il, leaf_max=leaf_max)
+    assert np.array_equal(mp["parent"], t["parent"]) and np.array_equal(mp["ne"], t["ne"])
+    # every front's rows: its own rows in elimination order, then its update rows
+    for x in range(mp["n_front"]):
+        r = mp["rows"][mp["rows_ptr"][x]:mp["rows_ptr"][x + 1]]
+        assert np.array_equal(np.sort(r[mp["ne"][x]:]), np.sort(t["upd"][x]))
+    # each unordered entry pair assembled exactly once
+    assert int((mp["a_front"] >= 0).sum()) == (s.indices.size + s.n) // 2
+    b = np.random.default_rng(3).standard_normal((s.n, 2)) + 0j
+    x = _multifrontal_solve(s, mp, b)
+    ref = np.linalg.solve(s.dense(), b)
+    assert np.linalg.norm(x - ref) <= 1e-10 * np.linalg.norm(ref)
