@@ -12,8 +12,7 @@
  *   - the primal unknowns are eliminated by many independent factorizations
  *     A_i = L_i D_i L_i^T;
  *   - the resulting auxiliary matrix F = sum_i B_i A_i^{-1} B_i^T is symmetric,
- *     much smaller, and block-wise sparse (a sparse collection of dense
- *     blocks); its block structure is found by a symbolic step on the clique
+ *     much smaller, and sparse at the level of dense blocks; its block structure is found by a symbolic step on the clique
  *     graph of the domains and it is factored by a block LDL^T;
  *   - the primal unknowns are recovered by many small forward/backward
  *     substitutions, one per domain.
@@ -54,8 +53,8 @@ typedef enum {
 
 typedef enum { DD_PREC_FP64 = 0, DD_PREC_MIXED = 1 } dd_precision;
 
-/* One domain of the arrowhead system (Section II: "primal DoFs in domain
- * volumes and dual DoF on domain interfaces").
+/* One domain of the arrowhead system (Section II: primal unknowns live in
+ * the domain volumes, dual unknowns on the domain interfaces).
  *   n        local primal unknowns (rows of A_i), n >= 1
  *   rowptr   n+1 entries, 0-based CSR row pointers of A_i
  *   colind   rowptr[n] column indices, sorted and unique within each row
@@ -154,7 +153,7 @@ typedef struct {
 int dd_default_options(dd_options* opt);
 
 /* Analyse and upload the arrowhead system (Section II: decomposed BVP with
- * primal and dual unknowns; the "symbolic factorization" on the clique graph
+ * primal and dual unknowns; the symbolic factorization on the clique graph
  * of the block-wise sparse auxiliary matrix).  Validates every input, orders
  * each domain's unknowns interior-first / interface-last, builds the
  * separator tree of the dual unknowns from the domain tree, computes the
@@ -244,10 +243,12 @@ void dd_free(dd_handle* h);
  * Solves A X = B for one dense complex-symmetric A (A = A^T, lower triangle
  * read, unpivoted LDL^T in FP64 with the same kernels as dd_factor/dd_solve).
  *   n      1..DD_NOALLOC_MAX_N;  nrhs  1..DD_NOALLOC_MAX_NRHS
- *   A      DEVICE memory, n x n column-major, leading dimension lda >= n
- *   b      DEVICE memory, n x nrhs column-major (ldb >= n)
- *   x      DEVICE memory, n x nrhs column-major (ldx >= n), written
+ *   A      device memory, n x n column-major, leading dimension lda >= n
+ *   b      device memory, n x nrhs column-major (ldb >= n)
+ *   x      device memory, n x nrhs column-major (ldx >= n), written
  *   cuda_stream  stream for all work (NULL = legacy default stream)
+ * A, b and x must be device memory of the CURRENT device (or managed memory);
+ * host memory and device memory of another GPU are refused. 
  * Allocates nothing: all scratch is one static device array of about 4.3 MB
  * that every GPU loading this library holds until the process exits.  The
  * first call on a device looks up that array's device address; make that
@@ -255,7 +256,8 @@ void dd_free(dd_handle* h);
  * at zero, but all calls share the one array: calls that overlap on the GPU
  * (other streams, other host threads) race and must be serialised by the
  * caller.  Returns after the stream has finished the solve.  Errors:
- * DD_ERR_INVALID_ARG (sizes beyond the limits, NULL or host pointers),
+ * DD_ERR_INVALID_ARG (sizes beyond the limits, NULL pointers, host memory or
+ * another device's memory),
  * DD_ERR_SINGULAR_PIVOT, DD_ERR_TIMEOUT, DD_ERR_CUDA.
  * ------------------------------------------------------------------------- */
 #define DD_NOALLOC_MAX_N 512

@@ -2,8 +2,8 @@
 // include/dd.h, input validation, the symbolic analysis of the arrowhead
 // system, device memory, and the launch schedule of factor and solve.
 //
-// Symbolic analysis (Section II, "symbolic factorization step ... attributed
-// clique graph of the block-wise sparse matrix"):
+// Symbolic analysis (Section II: the block structure of the auxiliary factor
+// comes from a symbolic factorization over the clique graph of its blocks):
 //   * each domain's unknowns are ordered interior first, interface last, so
 //     that the rows of B_i only meet the last n_Gamma columns of L_i;
 //   * every domain is a clique over the duals it touches; a dual coupling a set

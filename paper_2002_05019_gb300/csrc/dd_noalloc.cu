@@ -9,6 +9,7 @@
 // LDL^T, then the tile-parallel substitution) and allocates nothing: every
 // byte of scratch lives in the file-scope array below, which each GPU that
 // loads this library holds until the process exits.
+#include <atomic>
 #include <cstring>
 
 #include "../../include/dd.h"
@@ -102,17 +103,20 @@ __global__ void k_plan(unsigned char* scratch, int n, int nt) {
   st->min_abs_d = 0x7FF0000000000000ull;
 }
 
-// front <- lower triangle of A (column-major, lda), identity padding; the rest
-// of the front was cleared by the caller
+// front (ld x ld, row-major) <- lower triangle of A (column-major, lda) with
+// identity padding; the strictly upper triangle is written with zeros, so no
+// value of an earlier call (of another size or ld) survives anywhere in the
+// front, although the factor and solve kernels read the lower triangle only
 __global__ void k_load_matrix(unsigned char* scratch, int n, int ld, const double2* A, int64_t lda) {
   double2* front = reinterpret_cast<double2*>(scratch + kOffFront);
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)ld * ld;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int r = (int)(e / ld), c = (int)(e % ld);
-    if (c > r) continue;
     double2 v = make_double2(0.0, 0.0);
-    if (r < n) v = A[r + (int64_t)c * lda];
-    else if (r == c) v = make_double2(1.0, 0.0);
+    if (c <= r) {
+      if (r < n) v = A[r + (int64_t)c * lda];
+      else if (r == c) v = make_double2(1.0, 0.0);
+    }
     front[e] = v;
   }
 }
@@ -134,28 +138,37 @@ __global__ void k_store_x(const unsigned char* scratch, int n, int nrhs, double2
   }
 }
 
-bool is_device(const void* p) {
+// True for memory the kernels of device `dev` may read and write: device
+// memory of that same device, or managed memory.  Device memory of another
+// GPU is refused (without peer access a kernel touching it would fault).
+bool is_device_of(const void* p, int dev) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 constexpr int kMaxDevices = 64;
-unsigned char* g_scratch_addr[kMaxDevices] = {};
+// Per-device cache of the scratch's device address.  Two host threads making
+// their first call at once may both look it up; both store the same value,
+// and the atomics keep that a well-defined race.
+std::atomic<unsigned char*> g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the scratch on the current device (looked up once per device).
-int scratch_address(unsigned char** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DD_ERR_CUDA;
-  if (!g_scratch_addr[dev]) {
+// Device address of the scratch on device `dev`, the current device (looked
+// up once per device).
+int scratch_address(int dev, unsigned char** out) {
+  if (dev < 0 || dev >= kMaxDevices) return DD_ERR_CUDA;
+  unsigned char* a = g_scratch_addr[dev].load(std::memory_order_relaxed);
+  if (!a) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return DD_ERR_CUDA;
-    g_scratch_addr[dev] = static_cast<unsigned char*>(p);
+    a = static_cast<unsigned char*>(p);
+    g_scratch_addr[dev].store(a, std::memory_order_relaxed);
   }
-  *out = g_scratch_addr[dev];
+  *out = a;
   return DD_OK;
 }
 
@@ -165,9 +178,11 @@ extern "C" int dd_dense_solve_noalloc(int32_t n, const dd_c128* A, int64_t lda, 
                                       int64_t ldb, dd_c128* x, int64_t ldx, void* cuda_stream) {
   if (n < 1 || n > kMaxN || nrhs < 1 || nrhs > kMaxRhs) return DD_ERR_INVALID_ARG;
   if (!A || !b || !x || lda < n || ldb < n || ldx < n) return DD_ERR_INVALID_ARG;
-  if (!is_device(A) || !is_device(b) || !is_device(x)) return DD_ERR_INVALID_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return DD_ERR_CUDA;
+  if (!is_device_of(A, dev) || !is_device_of(b, dev) || !is_device_of(x, dev)) return DD_ERR_INVALID_ARG;
   unsigned char* sc = nullptr;
-  int st = scratch_address(&sc);
+  int st = scratch_address(dev, &sc);
   if (st != DD_OK) return st;
   cudaStream_t s = (cudaStream_t)cuda_stream;
   const Layout Lo = make_layout(n, nrhs);

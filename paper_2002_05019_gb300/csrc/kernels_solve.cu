@@ -1,6 +1,6 @@
-// Forward / backward substitution over the front tree (Section II: "the
-// solution of all ... primal unknowns are recovered ... via many smaller size
-// sparse forward backward substitutions", after the auxiliary solve), and the
+// Forward / backward substitution over the front tree (Section II: after the
+// auxiliary solve, the primal unknowns of every domain, or of a chosen subset,
+// follow from many small independent substitutions), and the
 // FP64 residual of the arrowhead system used by iterative refinement.
 //
 // Right-hand sides live in a per-front block z (ld rows x nrhs, row-major).

@@ -5,7 +5,8 @@ are running (an application whose allocator owns all device memory, or a loop
 that cannot afford cudaMalloc's synchronisation or failure); its scratch is a
 static device array.  The test checks it against the allocating entry points
 (dd_setup / dd_factor / dd_solve on the same system as a single domain) within
-the FP64 tolerance, on two calls in a row with different systems, and checks
+the FP64 tolerance, on calls in a row with different systems (small, the
+largest, small again), and checks
 that sizes beyond its limit and host pointers are rejected.  It sits in its own
 file, collected last, and passes alone or after the other tests.
 """
@@ -60,13 +61,17 @@ def rel(a, b):
 
 
 def test_noalloc_matches_allocating_path_twice():
-    # call 1: a FEM domain matrix (ragged size), call 2: the maximum size
+    # a FEM domain matrix (ragged size), then the maximum size, then a smaller
+    # system again: the shared scratch still holds the large call's front and
+    # right-hand sides (another padded order), which must not leak into it
     p = femgen.tiny(3, 1)
     A1 = p.subs[0].dense()
     B1 = np.random.default_rng(1).normal(size=(A1.shape[0], 3)) + 0j
     A2 = _lossy_symmetric(512, seed=2)
     B2 = np.random.default_rng(3).normal(size=(512, 16)) + 1j * np.random.default_rng(4).normal(size=(512, 16))
-    for A, B in ((A1, B1), (A2, B2)):
+    A3 = _lossy_symmetric(77, seed=5)
+    B3 = np.random.default_rng(6).normal(size=(77, 2)) + 0j
+    for A, B in ((A1, B1), (A2, B2), (A3, B3)):
         code, X = _noalloc_solve(A, B)
         assert code == 0
         Xref = _allocating_solve(A, B)
