@@ -7,7 +7,7 @@ their inputs from it.
 """
 from .mesh import Mesh, box_mesh, kuhn_edge_count, boundary_edge_mask
 from .problems import (Problem, Subdomain, build_problem, plain_c1, batched_c2, medium, big_domains, large_c4,
-                       multi_rhs_c5, tiny, K0)
+                       multi_rhs_c5, tiny, linear_field_loads, K0)
 
 __all__ = ["Mesh", "box_mesh", "kuhn_edge_count", "boundary_edge_mask", "Problem", "Subdomain",
-           "build_problem", "plain_c1", "batched_c2", "medium", "big_domains", "large_c4", "multi_rhs_c5", "tiny", "K0"]
+           "build_problem", "plain_c1", "batched_c2", "medium", "big_domains", "large_c4", "multi_rhs_c5", "tiny", "linear_field_loads", "K0"]

@@ -221,17 +221,8 @@ def build_problem(name: str, n: int, levels: int, *, jitter=0.15, mesh_seed=0,
         for c, fl in enumerate(wave_loads):
             b[:, rhs_edges.size + c] = _assemble_load(te[:0], np.zeros((0, 6)), feid, fl, nE)
     elif rhs == "linear":
-        r = np.random.default_rng(field_seed)
-        a = r.normal(size=3) + 1j * r.normal(size=3)
-        bb = r.normal(size=3) + 1j * r.normal(size=3)
-        E = linear_field(a, bb)
-        # curl curl E = 0, so F = -k0^2 eps_r E with each tetrahedron's own eps_r
-        elem_load = volume_load(mesh, E, s=1) * (-(k0 ** 2) * eps_tet[:, None])
-        U = _abc_data(E, lambda x: np.broadcast_to(2.0 * bb, x.shape).astype(complex), k0)
-        fl, _ = face_load(mesh, U, s=1)
-        face_ld = -fl
+        elem_load, face_ld, x_exact = _linear_pieces(mesh, eps_tet, k0, field_seed)
         b = _assemble_load(te, elem_load, feid, face_ld, nE)[:, None]
-        x_exact = interpolate(mesh, E)[:, None]
     elif rhs == "sine":
         E, curlE = sine_field()
         elem_load = volume_load(mesh, E, s=3) * ((2 * np.pi ** 2) - (k0 ** 2) * eps_tet[:, None])
@@ -269,6 +260,40 @@ def build_problem(name: str, n: int, levels: int, *, jitter=0.15, mesh_seed=0,
     return Problem(name=name, mesh=mesh, k0=k0, eps_tet=eps_tet, tet_sub=tet_sub, rcb=rcb,
                    tearing=tr, A_indptr=A_indptr, A_indices=A_indices, A_data=A_data, b=b,
                    subs=subs, x_exact=x_exact, rhs_edges=rhs_edges)
+
+
+def _linear_pieces(mesh: Mesh, eps_tet, k0, field_seed):
+    """Element and face loads of the linear field E = a + b x r (seeded a, b)
+    and its edge interpolant, the exact discrete solution."""
+    r = np.random.default_rng(field_seed)
+    a = r.normal(size=3) + 1j * r.normal(size=3)
+    bb = r.normal(size=3) + 1j * r.normal(size=3)
+    E = linear_field(a, bb)
+    # curl curl E = 0, so F = -k0^2 eps_r E with each tetrahedron's own eps_r
+    elem_load = volume_load(mesh, E, s=1) * (-(k0 ** 2) * eps_tet[:, None])
+    U = _abc_data(E, lambda x: np.broadcast_to(2.0 * bb, x.shape).astype(complex), k0)
+    fl, _ = face_load(mesh, U, s=1)
+    return elem_load, -fl, interpolate(mesh, E)[:, None]
+
+
+def linear_field_loads(p: Problem, field_seed=5):
+    """Local loads f_i (list of (n_i, 1)) and the exact solution (n, 1) of the
+    linear-field problem on p's mesh, materials and partition: the same A_i
+    as p, so one factorization of p serves both.  Equal to the loads of
+    build_problem(..., rhs="linear") with the same seeds."""
+    mesh = p.mesh
+    elem_load, face_ld, x_exact = _linear_pieces(mesh, p.eps_tet, p.k0, field_seed)
+    _, feid = face_matrices(mesh)
+    te = mesh.tet_edges
+    f = []
+    for s, sub in enumerate(p.subs):
+        g = sub.l2g
+        tmask = p.tet_sub == s
+        fmask = p.tet_sub[mesh.bface_tet] == s
+        lt = np.searchsorted(g, te[tmask])
+        lf = np.searchsorted(g, feid[fmask])
+        f.append(_assemble_load(lt, elem_load[tmask], lf, face_ld[fmask], g.size)[:, None])
+    return f, x_exact
 
 
 def _lowest_owner(tr: Tearing, e: int, s: int) -> int:

@@ -14,6 +14,10 @@ Routes to the same solution x = A^{-1} b of the assembled FEM system:
                               F lambda = d, primal recovery;
   * dd.SparseDDOracle       - the same route with sparse (SuperLU) domain
                               factorizations, for domains beyond the dense reach;
+  * tree.TreeDDOracle       - the same route with F eliminated block by block
+                              over the domain tree (nested dissection): the
+                              route that reaches the 512- and 2048-domain
+                              workloads, and a subtree of one as a timed sample;
   * dd.arrow_solve          - the arrowhead system solved undecomposed by LU with
                               partial pivoting (inputs whose LDL^T needs pivoting);
   * dense.ldlt_bk_restricted - LDL^T with Bunch-Kaufman pivoting restricted to
@@ -34,10 +38,11 @@ from .dense import lu_solve, ldlt, ldlt_solve, ldlt_bk_restricted, ldlt_bk_solve
 from .skyline import BandLDLT, rcm, envelope_entries
 from .dd import DDOracle, SparseDDOracle, gather_copies, subdomain_schur, arrow_residual, local_B, arrow_dense, arrow_solve
 from .refine import residual_dd, refine, backward_error
+from .tree import TreeDDOracle, subtree_nodes
 from .symbolic import fronts_by_elimination, fronts_by_tree, lca_fronts, dual_domains
 from . import domain_symbolic
 
 __all__ = ["lu_solve", "ldlt", "ldlt_solve", "ldlt_bk_restricted", "ldlt_bk_solve", "BandLDLT", "rcm", "envelope_entries",
-           "DDOracle", "SparseDDOracle", "gather_copies", "subdomain_schur", "arrow_residual", "local_B", "arrow_dense", "arrow_solve",
+           "DDOracle", "SparseDDOracle", "TreeDDOracle", "subtree_nodes", "gather_copies", "subdomain_schur", "arrow_residual", "local_B", "arrow_dense", "arrow_solve",
            "fronts_by_elimination", "fronts_by_tree", "lca_fronts", "dual_domains", "domain_symbolic",
            "residual_dd", "refine", "backward_error"]

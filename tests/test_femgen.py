@@ -195,3 +195,15 @@ def test_plane_wave_curl_and_boundary_load():
     f = np.concatenate([s.f for s in p.subs])
     assert np.abs(R.T @ f - p.b).max() <= 1e-15 * np.abs(p.b).max()
     assert np.all(np.abs(p.b[:, 56:]).max(axis=0) > 0.1)
+
+
+def test_linear_field_loads_match_the_linear_problem():
+    """linear_field_loads on an edge-current problem gives the loads and exact
+    solution of the same mesh built with rhs="linear" (same matrices)."""
+    a = femgen.tiny(4, 3, jittered=True, eps="random", rhs="linear")
+    b = femgen.tiny(4, 3, jittered=True, eps="random")
+    f, x = femgen.linear_field_loads(b)
+    for sa, sb, fb in zip(a.subs, b.subs, f):
+        assert np.array_equal(sa.data, sb.data)
+        assert np.array_equal(sa.f, fb)
+    assert np.array_equal(a.x_exact, x)
