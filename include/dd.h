@@ -135,7 +135,8 @@ typedef struct {
   int32_t launches_solve;    /* kernels launched by the last dd_solve */
   double kernel_ms[DD_K_NCLASS];        /* time_kernels: summed device time per class, last dd_factor */
   int32_t kernel_launches[DD_K_NCLASS]; /* launches per class in one dd_factor */
-  double kernel_flops[DD_K_NCLASS];     /* algorithmic real flops per class in one dd_factor */
+  double kernel_flops[DD_K_NCLASS];     /* algorithmic real flops per class in one dd_factor, counted on
+                                           the fronts' exact sizes (tile padding not counted) */
   int64_t interchanges;      /* pivoting: symmetric interchanges in the last dd_factor */
   int64_t pivots_2x2;        /* pivoting: 2 x 2 pivot blocks in the last dd_factor */
 } dd_stats;

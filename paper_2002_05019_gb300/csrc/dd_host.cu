@@ -902,7 +902,7 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
       R.upd_off = (int64_t)h_updt.size();
       R.tc_off = (int64_t)h_tc.size();
       std::vector<Task> upd_next, upd_rest, tc_next, tc_rest;
-      double upd_flops = 0.0;
+      double upd_flops = 0.0, trsm_flops = 0.0, diag_flops = 0.0;
       for (int f : L.ids) {
         const FrontDev& F = h->fronts[f];
         const int nte = F.ne_pad / T, nt = F.ld / T;
@@ -912,14 +912,25 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
         auto zero_tile = [&](int i) { return F.kind == 0 && i >= nte && (k + 1) * T <= F.n_int; };
         for (int i = k + 1; i < nt; ++i)
           if (!zero_tile(i)) h_trsm.push_back(Task{f, i, k, 0});
-        // algorithmic trailing-update work of this step (64 x 64 tiles, lower part)
         for (int j = k + 1; j < nt; ++j) {
           if (zero_tile(j)) continue;
           for (int i = j; i < nt; ++i) {
             if (zero_tile(i)) continue;
-            upd_flops += 8.0 * T * (i == j ? T * (T + 1) / 2 : T * T);
             if (!h->use_tc) (j == k + 1 ? upd_next : upd_rest).push_back(Task{f, i, j, 0});
           }
+        }
+        // algorithmic work of this step on the front's exact sizes (no tile
+        // padding; 8 real flops per complex multiply-add): the panel's w real
+        // columns, the r real rows below it (later eliminated rows, and the
+        // update rows unless B vanishes on the panel); the trailing update
+        // covers the lower triangle of the r x r block
+        {
+          const double w = std::min(T, F.ne - k * T);
+          const double e = std::max(0, F.ne - (k + 1) * T);
+          const double r = e + (zero_tile(nte) ? 0 : F.nu);
+          diag_flops += 8.0 * w * (w - 1) * (w + 1) / 6.0;
+          trsm_flops += 8.0 * r * w * (w - 1) / 2.0;
+          upd_flops += 8.0 * w * r * (r + 1) / 2.0;
         }
         // tensor-core tasks: row tile i x column tiles (j, j + 1); column pairs
         // never straddle the first update-row tile, so both columns of a task
@@ -947,8 +958,8 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
       h_tc.insert(h_tc.end(), tc_rest.begin(), tc_rest.end());
       R.n_diag = (int)((int64_t)h_diag.size() - R.diag_off);
       h->stats.kernel_flops[DD_K_UPDATE] += upd_flops;
-      h->stats.kernel_flops[DD_K_TRSM] += 8.0 * ((int64_t)h_trsm.size() - R.trsm_off) * T * T * (T - 1) / 2.0;
-      h->stats.kernel_flops[DD_K_DIAG] += 8.0 * ((int64_t)h_diag.size() - R.diag_off) * (double)T * T * T / 6.0;
+      h->stats.kernel_flops[DD_K_TRSM] += trsm_flops;
+      h->stats.kernel_flops[DD_K_DIAG] += diag_flops;
       R.n_trsm = (int)((int64_t)h_trsm.size() - R.trsm_off);
       R.n_upd = (int)((int64_t)h_updt.size() - R.upd_off);
       R.n_tc = (int)((int64_t)h_tc.size() - R.tc_off);

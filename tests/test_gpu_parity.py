@@ -15,16 +15,31 @@ import paper_2002_05019_gb300 as dd
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-12, "mixed": 1e-10}
-# F_i itself is not refined: in the mixed form it carries the complex64 LDL^T
-# error, about cond(A_i) * u with cond(A_i) <~ 1e3.  The tensor-core products
-# are 3xTF32: a = hi + lo with lo rounded to tf32, so each product carries
-# about 2^-21 (the dropped lo lo' term and the rounding of lo, each 2^-22
-# relative) instead of FP32's 2^-24: u ~ 5e-7, cond * u ~ 5e-4
-TOL_F = {"fp64": 1e-12, "mixed": 5e-4}
+# F_i = B_i A_i^{-1} B_i^T itself is not refined.  In the mixed form its
+# factors are complex64 with 3xTF32 tensor-core products: a = hi + lo with lo
+# rounded to tf32, so each product carries about 2^-21 relative error (the
+# dropped lo lo' term and the rounding of lo, each 2^-22) instead of FP32's
+# 2^-24.  A relative perturbation eps of A_i moves A_i^{-1}, and so F_i, by
+# about cond(A_i) eps (first order), so the tolerance of domain i is
+# cond_2(A_i) * 2^-21, with cond_2(A_i) computed here from the dense A_i
+# (about 60..140 on the 98-unknown tiny domains, 330..460 on the 604-unknown
+# domains of the 8-domain mesh, 4e3..1e4 on the 512-domain mesh).
+U_TC = 2.0 ** -21
+
+
+def tol_f(precision, sub):
+    if precision == "fp64":
+        return 1e-12
+    return float(np.linalg.cond(sub.dense())) * U_TC
 
 
 def rel(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300))
+
+
+def maxrel(ref, a):
+    """Largest entry error over every local copy, relative to the largest entry."""
+    return float(np.abs(np.asarray(a) - ref).max() / np.abs(ref).max())
 
 
 def gather(p, u):
@@ -68,15 +83,15 @@ def test_tiny_against_oracle(precision, n, levels, jit):
     xo, _ = o.gather(uo)
     s, u, lam = run(p, precision)
     assert rel(gather(p, u), xo) <= TOL[precision]
+    assert maxrel(np.concatenate(uo), u) <= TOL[precision]
     assert rel(lam, lo) <= TOL[precision] * 10
     assert copy_mismatch(p, u) <= TOL[precision] * np.abs(xo).max()
     # F_i of every domain (first-step parity: domain LDL^T + Schur contribution)
-    if precision == "fp64":
-        for i, sub in enumerate(p.subs):
-            Fi, duals = s.schur(i)
-            Fo, do = oracle.subdomain_schur(sub, o.facs[i])
-            assert np.array_equal(duals, do)
-            assert rel(Fi, Fo) <= 1e-12
+    for i, sub in enumerate(p.subs):
+        Fi, duals = s.schur(i)
+        Fo, do = oracle.subdomain_schur(sub, o.facs[i])
+        assert np.array_equal(duals, do)
+        assert rel(Fi, Fo) <= tol_f(precision, sub)
     s.free()
 
 
@@ -88,6 +103,7 @@ def test_plain_8_domains_against_oracle(c1, precision):
     s, u, lam = run(c1, precision)
     x = gather(c1, u)
     assert rel(x, xo) <= TOL[precision]
+    assert maxrel(np.concatenate(uo), u) <= TOL[precision]
     assert rel(lam, lo) <= TOL[precision] * 10
     assert oracle.backward_error(c1.A_indptr, c1.A_indices, c1.A_data, x, c1.b) < (1e-15 if precision == "fp64" else 1e-13)
     st = s.stats()
@@ -98,7 +114,7 @@ def test_plain_8_domains_against_oracle(c1, precision):
     for i in (0, 7):
         Fi, _ = s.schur(i)
         Fo, _ = oracle.subdomain_schur(c1.subs[i], o.facs[i])
-        assert rel(Fi, Fo) <= TOL_F[precision]
+        assert rel(Fi, Fo) <= tol_f(precision, c1.subs[i])
     s.free()
 
 
@@ -176,7 +192,7 @@ def test_batched_512_domains_full_size(c2_linear, precision):
         Fi, duals = s.schur(i)
         Fo, do = oracle.subdomain_schur(p.subs[i])
         assert np.array_equal(duals, do)
-        assert rel(Fi, Fo) <= TOL_F[precision]
+        assert rel(Fi, Fo) <= tol_f(precision, p.subs[i])
     s.free()
 
 
@@ -184,7 +200,8 @@ def test_batched_512_domains_full_size(c2_linear, precision):
 def test_tensor_core_update_matches_simt_update(c1, p_name):
     """The tcgen05 3xTF32 trailing update, one or two panels per pass, and the
     FP32 FMA-pipe update give the same F_i to the accuracy of 3xTF32 products
-    (cond(A_i) <~ 1e3 times 2^-21) and all refine to the mixed tolerance."""
+    (two independent errors of cond(A_i) 2^-21 each) and all refine to the
+    mixed tolerance."""
     p = c1 if p_name == "c1" else femgen.medium()
     o = oracle.DDOracle(p) if p_name == "c1" else None
     xo = o.gather(o.solve([s.f for s in p.subs])[0])[0] if o else None
@@ -198,9 +215,10 @@ def test_tensor_core_update_matches_simt_update(c1, p_name):
             assert rel(gather(p, u), xo) <= TOL["mixed"]
         res[mode] = ([s.schur(i)[0] for i in range(0, p.n_sub, max(1, p.n_sub // 8))], u)
         s.free()
+    tols = [2 * tol_f("mixed", p.subs[i]) for i in range(0, p.n_sub, max(1, p.n_sub // 8))]
     for mode in ("tc1", "simt"):
-        for a, b in zip(res["tc2"][0], res[mode][0]):
-            assert rel(a, b) <= 5e-4
+        for a, b, t in zip(res["tc2"][0], res[mode][0], tols):
+            assert rel(a, b) <= t
         assert rel(res["tc2"][1], res[mode][1]) <= TOL["mixed"] * 10
 
 

@@ -7,6 +7,8 @@ memory report.
   domains are simply not back-substituted), on 8 and 512 domains;
 * mixed form (refined on every domain): the listed rows of the full refined
   solution;
+* both forms against the oracle (DDOracle) on the 8-domain mesh, element by
+  element (the 512-domain comparison is in test_gpu_parity_c2.py);
 * bad, repeated and out-of-range ids are rejected;
 * factor memory: dd_stats.bytes_factor against the skyline (envelope) factor
   of the undecomposed RCM-ordered system (the oracle's O2), reported.
@@ -52,6 +54,22 @@ def test_mixed_subset_is_the_refined_solution():
     rows = _rows(p, ids)
     assert np.linalg.norm(us - u[rows]) <= 1e-14 * np.linalg.norm(u[rows])
     assert np.linalg.norm(ls - lam) <= 1e-14 * np.linalg.norm(lam)
+    s.free()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_subset_against_oracle_8_domains(c1, precision):
+    o = oracle.DDOracle(c1)
+    uo, lo = o.solve([s.f for s in c1.subs])
+    s = dd.Solver.from_problem(c1, precision=precision)
+    s.factor()
+    ids = [6, 1, 3]
+    us, ls = s.solve_subset(dd.stacked_loads(c1), ids)
+    ref = np.concatenate([uo[i] for i in ids], axis=0)
+    tol = 1e-12 if precision == "fp64" else 1e-10
+    scale = max(np.abs(u).max() for u in uo)
+    assert np.abs(us - ref).max() <= tol * scale
+    assert np.linalg.norm(ls - lo) <= 10 * tol * np.linalg.norm(lo)
     s.free()
 
 

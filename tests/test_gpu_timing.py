@@ -30,3 +30,20 @@ def test_kernel_timing_modes():
     assert kl0 == kl1 == kl2
     for u in (u1, u2):
         assert np.linalg.norm(u - u0) <= 1e-12 * np.linalg.norm(u0)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_class_flops_add_up_to_the_factor_count(precision):
+    """The per-class algorithmic flops (diagonal blocks, panels, trailing
+    updates; exact front sizes, no tile padding) add up to the factorization's
+    algorithmic count (4/3 n^3 per elimination plus the Schur terms), within
+    the interior columns that share a tile with interface columns."""
+    p = femgen.medium()
+    s = dd.Solver.from_problem(p, precision=precision)
+    s.factor()
+    st = s.stats()
+    kf = st["kernel_flops"]
+    total = kf["diag"] + kf["trsm"] + kf["update"]
+    assert kf["update"] > 0.9 * total
+    assert abs(total - st["flops_factor"]) <= 0.03 * st["flops_factor"]
+    s.free()
