@@ -135,6 +135,27 @@ def pick_subtree(parent, n_sub: int, n_domains: int) -> int:
     return int(cand[np.argmin(count[cand])])
 
 
+def skyline_worker(workload: str, out_path: str, repeats: int = 1):
+    """Time the oracle's undecomposed route O2 (RCM + band LDL^T of the global
+    system, then the solve) on the whole workload, `repeats` times."""
+    import femgen
+    import oracle
+    p = getattr(femgen, WORKLOADS[workload][0])()
+    runs = []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        o = oracle.BandLDLT(p.A_indptr, p.A_indices, p.A_data).factor()
+        t1 = time.perf_counter()
+        o.solve(p.b)
+        t2 = time.perf_counter()
+        runs.append((t2 - t0, t1 - t0, t2 - t1))
+    sec, fac, sol = runs[-1]
+    with open(out_path, "w") as fh:
+        json.dump({"seconds": sec, "factor_s": fac, "solve_s": sol, "runs": [r[0] for r in runs],
+                   "domains": p.n_sub, "fronts": 0, "n_global": p.n, "n_sub": p.n_sub, "dofs": p.n,
+                   "value": p.n / sec, "skyline_entries": None, "route": "skyline"}, fh)
+
+
 def oracle_sample_worker(workload: str, n_domains: int, out_path: str, with_skyline: bool = False,
                          repeats: int = 1):
     """Time the oracle's complete DD route (oracle.TreeDDOracle: domain LU,
@@ -162,15 +183,20 @@ def oracle_sample_worker(workload: str, n_domains: int, out_path: str, with_skyl
                    "dofs": dofs, "value": dofs / sec, "skyline_entries": sky}, fh)
 
 
-def run_oracle_sample(workload: str, n_domains: int, threads: int, with_skyline: bool = False, repeats: int = 1):
-    """Run oracle_sample_worker in a fresh interpreter with `threads` BLAS threads."""
+def run_oracle_sample(workload: str, n_domains: int, threads: int, with_skyline: bool = False, repeats: int = 1,
+                      route: str = "tree"):
+    """Run oracle_sample_worker (or skyline_worker) in a fresh interpreter with `threads` BLAS threads."""
     import tempfile
     fd, path = tempfile.mkstemp(suffix=".json")
     os.close(fd)
     t = str(threads)
     env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t)
-    code = ("import sys; sys.path.insert(0, %r); import bench; bench.oracle_sample_worker(%r, %r, %r, %r, %r)"
-            % (ROOT, workload, n_domains, path, with_skyline, repeats))
+    if route == "skyline":
+        code = ("import sys; sys.path.insert(0, %r); import bench; bench.skyline_worker(%r, %r, %r)"
+                % (ROOT, workload, path, repeats))
+    else:
+        code = ("import sys; sys.path.insert(0, %r); import bench; bench.oracle_sample_worker(%r, %r, %r, %r, %r)"
+                % (ROOT, workload, n_domains, path, with_skyline, repeats))
     subprocess.run([sys.executable, "-c", code], env=env, check=True)
     with open(path) as fh:
         r = json.load(fh)
@@ -187,13 +213,20 @@ def host_cores() -> int:
 
 
 def cpu_baseline_entry(r, workload):
+    if r.get("route") == "skyline":
+        return {"value": r["value"], "unit": "DoF/s", "cores": r["threads"], "kind": "oracle",
+                "sample": (f"oracle undecomposed route O2 (RCM + band LDL^T of the global system, solve) on the "
+                           f"whole {workload} workload ({r['dofs']} DoFs): {r['seconds']:.1f} s (factor "
+                           f"{r['factor_s']:.1f} s, solve {r['solve_s']:.2f} s) on {r['threads']} host threads "
+                           f"of {host_cores()}")}
     return {"value": r["value"], "unit": "DoF/s", "cores": r["threads"], "kind": "oracle",
             "sample": (f"oracle tree route (domain LU, F_i, block elimination of F over the domain tree, "
                        f"forward/backward substitution, primal recovery) on the {r['domains']} domains and "
                        f"{r['fronts']} separator fronts of one subtree of the {workload} workload "
                        f"({r['dofs']} distinct DoFs of {r['n_global']}), timed in full: {r['seconds']:.1f} s "
                        f"(factor {r['factor_s']:.1f} s, solve {r['solve_s']:.2f} s) on {r['threads']} host "
-                       f"threads of {host_cores()}; the separators above the subtree are not in the sample")}
+                       f"threads of {host_cores()}" + ("; the whole workload" if r["domains"] == r["n_sub"] else
+                                                          "; the separators above the subtree are not in the sample"))}
 
 
 # ---------------------------------------------------------------------------
@@ -223,9 +256,10 @@ def reference_arm(args):
     ws, rank, local = dist_env()
     if rank != 0:
         return 0
-    threads = host_cores()
+    threads = args.ref_threads or host_cores()
     t_run = time.perf_counter()
-    r = run_oracle_sample(args.workload, args.ref_domains, threads, repeats=args.warmup + args.steps)
+    r = run_oracle_sample(args.workload, args.ref_domains, threads, repeats=args.warmup + args.steps,
+                          route=args.ref_route)
     secs = r["runs"][args.warmup:]
     log(f"[bench] reference arm: {args.warmup + args.steps} oracle runs in {time.perf_counter() - t_run:.1f} s")
     v = r["dofs"] / float(np.mean(secs))
@@ -518,6 +552,10 @@ def main():
                     help="domains in the subtree sample the CPU oracle baseline solves")
     ap.add_argument("--ref-domains", type=int, default=8,
                     help="domains in the subtree sample of each reference-arm step")
+    ap.add_argument("--ref-route", default="tree", choices=["tree", "skyline"],
+                    help="reference arm: the oracle's DD tree route on a subtree sample, or its undecomposed "
+                         "skyline route on the whole workload")
+    ap.add_argument("--ref-threads", type=int, default=0, help="reference arm: host threads (0: all)")
     ap.add_argument("--pivoting", type=int, default=0, choices=[0, 1, 2],
                     help="restricted Bunch-Kaufman: 0 none, 1 auxiliary fronts, 2 every front")
     ap.add_argument("--update-panels", type=int, default=2, choices=[1, 2],

@@ -111,6 +111,13 @@ typedef struct {
   int32_t update_panels;    /* MIXED, tensor cores: panels fused per trailing-update pass, 1 (C read
                                and written after every 64-wide panel) or 2 (after every pair of
                                panels, K = 128; default); other values: DD_ERR_INVALID_ARG */
+  int32_t sparse_min;       /* Section II factors each domain with a sparse direct solver: domains of
+                               at least sparse_min unknowns are split into a tree of fronts by nested
+                               dissection of their matrix graph (interface unknowns last, in the
+                               domain's root front, whose update rows are the domain's duals), the
+                               others stay one dense front.  0 (default): every domain is one dense
+                               front; negative: DD_ERR_INVALID_ARG */
+  int32_t sparse_leaf;      /* largest leaf front of that dissection (0: 256); negative: DD_ERR_INVALID_ARG */
 } dd_options;
 
 /* Kernel classes of dd_stats.kernel_ms / kernel_launches / kernel_flops. */

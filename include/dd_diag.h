@@ -29,8 +29,13 @@ int dd_selftest_wait_timeout(void* cuda_stream);
  * validation as dd_setup (the same error codes for bad inputs).
  *
  * Fronts: 0 .. n_sub-1 are the domains (front i eliminates the n_i unknowns of
- * domain i), n_sub .. n_front-1 the separator fronts of the domain tree in
- * post-order (children before parents).  Outputs, all caller-allocated:
+ * domain i), n_sub .. n_sub+n_sep-1 the separator fronts of the domain tree in
+ * post-order (children before parents).  With opt->sparse_min > 0, front i of
+ * a domain of at least sparse_min unknowns is the root of its nested-dissection
+ * tree (it eliminates the interface unknowns) and the tree's other fronts
+ * follow the separator fronts, domain after domain, children before parents;
+ * their rows are given by row ids n_dual + (the row's index in the stacked
+ * primal vector).  Outputs, all caller-allocated:
  *   n_front            number of fronts (also written when max_fronts is too small)
  *   parent[max_fronts] parent front, -1 at the root
  *   ne[max_fronts]     unknowns eliminated in the front (domain size, or separator duals)
@@ -38,8 +43,8 @@ int dd_selftest_wait_timeout(void* cuda_stream);
  *   dual_front[n_dual] front that eliminates each dual (the lowest common
  *                      ancestor of the domains it touches)
  *   upd_ptr[max_fronts + 1], upd_idx[upd_cap] (optional, NULL to skip): the
- *                      update-row duals of front x are upd_idx[upd_ptr[x] ..
- *                      upd_ptr[x + 1]), in the library's row order
+ *                      update-row duals (or row ids) of front x are
+ *                      upd_idx[upd_ptr[x] .. upd_ptr[x + 1]), in the library's row order
  * Returns DD_OK, DD_ERR_INVALID_ARG (bad inputs, a NULL output, max_fronts <
  * n_front or upd_cap too small), or dd_setup's other validation codes. */
 int dd_symbolic(int32_t n_sub, const dd_subdomain* subs, int32_t n_dual, const dd_options* opt,
@@ -48,8 +53,8 @@ int dd_symbolic(int32_t n_sub, const dd_subdomain* subs, int32_t n_dual, const d
 
 /* Nested-dissection symbolic analysis of one domain matrix, for domains
  * beyond the dense-front range (Section II factors each domain with a sparse
- * direct solver); host only, touching no device, and not yet used by
- * dd_factor (whose domain fronts are dense).  The rows flagged in is_last (the
+ * direct solver); host only, touching no device.  dd_setup uses the same
+ * analysis for the domains selected by dd_options.sparse_min.  The rows flagged in is_last (the
  * interface rows that B couples to the duals; NULL: none) are eliminated last,
  * in the root front; the others by nested dissection -- separators are middle
  * levels of breadth-first level structures from pseudo-peripheral vertices --

@@ -49,7 +49,8 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("refine_tol", C.c_double), ("max_refine", C.c_int32),
                 ("pivoting", C.c_int32), ("tree_parent", C.POINTER(C.c_int32)),
                 ("centroids", C.POINTER(C.c_double)), ("cuda_stream", C.c_void_p), ("device", C.c_int32),
-                ("time_kernels", C.c_int32), ("simt_update", C.c_int32), ("update_panels", C.c_int32)]
+                ("time_kernels", C.c_int32), ("simt_update", C.c_int32), ("update_panels", C.c_int32),
+                ("sparse_min", C.c_int32), ("sparse_leaf", C.c_int32)]
 
 KERNEL_CLASSES = ["diag", "trsm", "update", "assemble", "init"]
 
@@ -262,7 +263,7 @@ class Solver:
     def __init__(self, subdomains, n_dual: int, precision: str = "fp64", refine_tol: float = 1e-13,
                  max_refine: int | None = None, tree_parent=None, centroids=None, stream=None, device: int = 0,
                  time_kernels: bool | int = False, simt_update: bool = False, pivoting: int | None = None,
-                 update_panels: int | None = None):
+                 update_panels: int | None = None, sparse_min: int | None = None, sparse_leaf: int | None = None):
         lib = load()
         subs, opt, self._keep = _marshal(subdomains, tree_parent, centroids)
         self.n = [int(s["n"]) for s in subdomains]
@@ -283,6 +284,10 @@ class Solver:
             opt.update_panels = int(update_panels)   # tensor-core update: 1 or 2 panels per pass
         if pivoting is not None:
             opt.pivoting = int(pivoting)   # 0 none, 1 auxiliary fronts, 2 every front (restricted Bunch-Kaufman)
+        if sparse_min is not None:
+            opt.sparse_min = int(sparse_min)   # domains of >= sparse_min unknowns: nested-dissection front trees
+        if sparse_leaf is not None:
+            opt.sparse_leaf = int(sparse_leaf)
         self.precision = precision
         h = C.c_void_p()
         _check(lib.dd_setup(C.byref(h), len(subdomains), subs, self.n_dual, C.byref(opt)), "dd_setup")

@@ -36,6 +36,16 @@ constexpr int kNormBlocks = 16;   // reduction blocks per column for the refinem
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+// Front tree of one sparse domain (dd_domain_assembly): local fronts 0..nf-1,
+// children before parents; gid maps them to the handle's fronts (root -> the
+// domain id).  nf == 0: the domain is one dense front.
+struct SparseDomain {
+  int nf = 0, root = -1;
+  int64_t vec_off = 0;                 // the domain's first row in the stacked primal vector
+  std::vector<int32_t> parent, ne, rows, a_front, gid;
+  std::vector<int64_t> rows_ptr;
+};
+
 struct StepRange {
   int k;
   int64_t diag_off, trsm_off, upd_off, tc_off;
@@ -66,6 +76,7 @@ struct Level {
   int64_t fwd_off = 0, bwd_off = 0;   // solve tasks (forward by row tile, backward by column tile)
   int n_fwd = 0, n_bwd = 0;
   int upd_split = 0;   // separator levels: CTAs per backward task of the split update-row product
+  int n_aux = 0;       // separator fronts of the auxiliary matrix here (the others eliminate domain unknowns)
 };
 
 struct DeviceArena {
@@ -114,6 +125,13 @@ struct dd_handle {
   double refine_tol = 1e-13;
   int max_refine = 0;
   int n_sub = 0, n_dual = 0;
+  int n_sparse = 0;        // domains factored as nested-dissection front trees
+  int64_t ld_lam = 0;      // rows of the solve's row-id vector: n_dual, + n_loc with sparse domains
+  int64_t n_scatter = 0;   // entries of the sparse domains' front initialisation
+  int64_t* d_sp_dst = nullptr;
+  int32_t* d_sp_src = nullptr;
+  int32_t* d_lvl0_sparse = nullptr;   // sparse-domain fronts of tree level 0
+  int n_lvl0_sparse = 0;
   int64_t n_loc = 0, nnz_total = 0;
   size_t elem = 16;  // bytes per stored complex
 
@@ -363,7 +381,7 @@ int ensure_work(dd_handle* h, int nrhs) {
   };
   const size_t nr = (size_t)nrhs;
   DD_CUDA(get(&h->rpool, (size_t)h->rows_total * nr * h->elem));
-  DD_CUDA(get(&h->lam_work, (size_t)h->n_dual * nr * h->elem));
+  DD_CUDA(get(&h->lam_work, (size_t)h->ld_lam * nr * h->elem));
   // separator levels of few tiles (their substitution is a chain whose first
   // tile waits for its update-row product): split the update rows of each
   // backward task over enough CTAs to fill the GPU about four times, at least
@@ -418,18 +436,23 @@ void direct_solve(dd_handle* h, int nrhs, const double2* f, int64_t ldf, const d
   const int ep = 1;
   ddk::launch_rhs_leaf(p, h->rpool, h->d_fronts, h->d_leaves, h->n_sub, h->d_perm, f, ldf, nrhs, s);
   h->launches += 1;
+  if (h->n_lvl0_sparse) {   // sparse-domain fronts without children
+    ddk::launch_rhs_node(p, h->rpool, h->d_fronts, h->d_lvl0_sparse, h->n_lvl0_sparse, h->d_sep, g, h->n_dual, f,
+                         ldf, h->n_dual, nrhs, s);
+    h->launches += 1;
+  }
   for (size_t l = 0; l < h->levels.size(); ++l) {
     const Level& L = h->levels[l];
     const int32_t* ids = h->d_level_ids + L.ids_off;
     const int n = (int)L.ids.size();
     if (l > 0) {
-      ddk::launch_rhs_node(p, h->rpool, h->d_fronts, ids, n, h->d_sep, g, h->n_dual, nrhs, s);
+      ddk::launch_rhs_node(p, h->rpool, h->d_fronts, ids, n, h->d_sep, g, h->n_dual, f, ldf, h->n_dual, nrhs, s);
       ddk::launch_rhs_extend_add(p, h->rpool, h->d_fronts, ids, n, 0, h->d_maps, nrhs, s);
       ddk::launch_rhs_extend_add(p, h->rpool, h->d_fronts, ids, n, 1, h->d_maps, nrhs, s);
       h->launches += 3;
     }
     ddk::launch_forward(p, h->pool, h->rpool, h->d_fronts, h->d_fwd + L.fwd_off, L.n_fwd, nrhs, h->d_flag_f, ep,
-                        h->d_solve_status, s, h->d_linv, h->d_piv);
+                        h->d_solve_status, s, h->d_linv, h->d_piv, h->use_tc);
     h->launches += 1;
   }
   for (size_t l = h->levels.size(); l-- > 0;) {
@@ -437,14 +460,17 @@ void direct_solve(dd_handle* h, int nrhs, const double2* f, int64_t ldf, const d
     const bool leaf_sub = sub && l == 0;
     h->launches += ddk::launch_backward(p, h->pool, h->rpool, h->d_fronts, leaf_sub ? sub->bwd : h->d_bwd + L.bwd_off,
                                         leaf_sub ? sub->n_bwd : L.n_bwd, nrhs, h->d_upd, h->d_sep, h->lam_work,
-                                        h->n_dual, h->d_flag_b, ep, h->d_solve_status, s, h->d_linv, h->d_piv,
-                                        l > 0 && L.upd_split > 0 ? h->upd_part : nullptr, L.upd_split);
+                                        h->ld_lam, h->d_flag_b, ep, h->d_solve_status, s, h->d_linv, h->d_piv,
+                                        l > 0 && L.upd_split > 0 ? h->upd_part : nullptr, L.upd_split,
+                                        h->use_tc);
   }
   if (sub)
-    ddk::launch_leaf_out(p, h->rpool, h->d_fronts, sub->leaves, sub->n_leaves, h->d_perm, u, sub->ldu, nrhs, 0, s);
+    ddk::launch_leaf_out(p, h->rpool, h->d_fronts, sub->leaves, sub->n_leaves, h->d_perm, u, sub->ldu, nrhs, 0, s,
+                         h->lam_work, h->ld_lam, h->n_dual);
   else
-    ddk::launch_leaf_out(p, h->rpool, h->d_fronts, h->d_leaves, h->n_sub, h->d_perm, u, h->n_loc, nrhs, 0, s);
-  ddk::launch_lam_out(p, h->lam_work, h->n_dual, h->n_dual, nrhs, lam, h->n_dual, 0, s);
+    ddk::launch_leaf_out(p, h->rpool, h->d_fronts, h->d_leaves, h->n_sub, h->d_perm, u, h->n_loc, nrhs, 0, s,
+                         h->lam_work, h->ld_lam, h->n_dual);
+  ddk::launch_lam_out(p, h->lam_work, h->ld_lam, h->n_dual, nrhs, lam, h->n_dual, 0, s);
   h->launches += 2;
 }
 
@@ -546,6 +572,7 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
   if (opt.pivoting < 0 || opt.pivoting > 2 || opt.max_refine < 0 || !(opt.refine_tol >= 0))
     return DD_ERR_INVALID_ARG;
   if (opt.update_panels != 1 && opt.update_panels != 2) return DD_ERR_INVALID_ARG;
+  if (opt.sparse_min < 0 || opt.sparse_leaf < 0) return DD_ERR_INVALID_ARG;
   if (opt.device < 0) return DD_ERR_INVALID_ARG;
 
   double amax = 0.0;
@@ -608,13 +635,85 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
     if (dual_node[d] < 0) return DD_ERR_INVALID_ARG;
   }
 
+  // ---- sparse domains (Section II: sparse direct factorizations of the domains):
+  // a domain of at least sparse_min unknowns becomes a tree of fronts, ordered
+  // by nested dissection with its interface unknowns last (dd_domain_assembly).
+  // The tree's root is front i (its update rows are the domain's duals, as for
+  // a dense domain front); the other fronts get ids after the separator fronts.
+  // Rows of these fronts carry "row ids": n_dual + the row's index in the
+  // stacked primal vector, beside the dual ids of the update rows of the root.
+  const int32_t sp_leaf = opt.sparse_leaf > 0 ? opt.sparse_leaf : 256;
+  std::vector<SparseDomain> spd(n_sub);
+  int n_extra = 0;
+  {
+    int64_t voff = 0;
+    for (int i = 0; i < n_sub; ++i) {
+      const dd_subdomain& sd = subs[i];
+      SparseDomain& D = spd[i];
+      D.vec_off = voff;
+      voff += sd.n;
+      if (opt.sparse_min <= 0 || sd.n < opt.sparse_min) continue;
+      std::vector<int8_t> is_last(sd.n, 0);
+      for (int q = 0; q < sd.nb; ++q) is_last[sd.b_local[q]] = 1;
+      const int cap = 2 * sd.n + 1;
+      D.parent.assign(cap, -1);
+      D.ne.assign(cap, 0);
+      D.rows_ptr.assign(cap + 1, 0);
+      int32_t nf = 0;
+      int st2 = dd_domain_assembly(sd.n, sd.rowptr, sd.colind, is_last.data(), sp_leaf, cap, &nf, D.parent.data(),
+                                   D.ne.data(), 0, D.rows_ptr.data(), nullptr, nullptr, nullptr, nullptr, nullptr);
+      if (st2 != DD_OK) return st2;
+      const int64_t nrows = D.rows_ptr[nf];
+      const int64_t nnz = sd.rowptr[sd.n];
+      D.rows.assign(std::max<int64_t>(nrows, 1), 0);
+      std::vector<int32_t> ea(D.rows.size()), arow(std::max<int64_t>(nnz, 1)), acol(arow.size());
+      D.a_front.assign(arow.size(), -1);
+      st2 = dd_domain_assembly(sd.n, sd.rowptr, sd.colind, is_last.data(), sp_leaf, cap, &nf, D.parent.data(),
+                               D.ne.data(), (int64_t)D.rows.size(), D.rows_ptr.data(), D.rows.data(), ea.data(),
+                               D.a_front.data(), arow.data(), acol.data());
+      if (st2 != DD_OK) return st2;
+      D.nf = nf;
+      for (int x = 0; x < nf; ++x)
+        if (D.parent[x] < 0) {
+          if (D.root >= 0) return DD_ERR_INVALID_ARG;   // one tree per domain
+          D.root = x;
+        }
+      // the interface rows must all be eliminated in the root front
+      int n_if = 0;
+      for (int r = 0; r < sd.n; ++r) n_if += is_last[r];
+      if (D.root < 0 || D.ne[D.root] != n_if || D.rows_ptr[D.root + 1] - D.rows_ptr[D.root] != n_if)
+        return DD_ERR_INVALID_ARG;
+      n_extra += nf - 1;
+    }
+  }
+  const int n_front_dense = n_front;   // domains and separator fronts
+  {
+    int next = n_front_dense;
+    for (int i = 0; i < n_sub; ++i) {
+      SparseDomain& D = spd[i];
+      D.gid.assign(D.nf, -1);
+      for (int x = 0; x < D.nf; ++x) D.gid[x] = x == D.root ? i : next++;
+    }
+  }
+  const int n_front_all = n_front_dense + n_extra;
+  h->n_sparse = 0;
+  for (int i = 0; i < n_sub; ++i) h->n_sparse += spd[i].nf > 0 ? 1 : 0;
+  par.resize(n_front_all, -1);
+  for (int i = 0; i < n_sub; ++i)
+    for (int x = 0; x < spd[i].nf; ++x)
+      if (x != spd[i].root) par[spd[i].gid[x]] = spd[i].gid[spd[i].parent[x]];
+  // row id of stacked primal row r (rows of sparse-domain fronts)
+  auto vid = [&](int i, int r) -> int32_t { return (int32_t)(n_dual + spd[i].vec_off + r); };
+  if (h->n_sparse && (int64_t)n_dual + spd[n_sub - 1].vec_off + subs[n_sub - 1].n > INT32_MAX) return DD_ERR_INVALID_ARG;
+
   // ---- leaf structures --------------------------------------------------------
-  h->fronts.assign(n_front, FrontDev{});
+  h->fronts.assign(n_front_all, FrontDev{});
   std::vector<int32_t> h_rowptr, h_colind, h_iperm, h_perm, h_brow, h_blocal, h_blptr, h_bldual;
   std::vector<int8_t> h_bsign, h_blsign;
   std::vector<double2> h_val;
   std::vector<LeafDev> h_leaves(n_sub);
   std::vector<int32_t> h_upd, h_sep, h_maps;
+  std::vector<std::vector<int32_t>> sp_sep(n_front_all), sp_upd(n_front_all);   // sparse-domain fronts
   h->leaf_duals.resize(n_sub);
   h->leaf_vec_off.resize(n_sub);
   int64_t vec_off = 0, csr_off = 0;
@@ -662,6 +761,28 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
     F.sep_off = 0;
     F.child[0] = F.child[1] = -1;
     h_upd.insert(h_upd.end(), duals.begin(), duals.end());
+    const SparseDomain& D = spd[i];
+    for (int x = 0; x < D.nf; ++x) {
+      // a front of the domain's tree: its own rows, then its update rows (the
+      // domain's duals at the root), all given by row ids
+      FrontDev& G = h->fronts[D.gid[x]];
+      G.piv = h->pivoting == 2 ? 1 : 0;
+      G.kind = 2;
+      G.sub = i;
+      G.ne = D.ne[x];
+      G.ne_pad = (int32_t)round_up(G.ne, T);
+      G.nu = x == D.root ? (int32_t)duals.size() : (int32_t)(D.rows_ptr[x + 1] - D.rows_ptr[x] - D.ne[x]);
+      G.ld = G.ne_pad + (int32_t)round_up(G.nu, T);
+      G.n_int = 0;
+      G.child[0] = G.child[1] = -1;
+      std::vector<int32_t>& own = sp_sep[D.gid[x]];
+      for (int64_t q = D.rows_ptr[x]; q < D.rows_ptr[x] + D.ne[x]; ++q) own.push_back(vid(i, D.rows[q]));
+      if (x != D.root) {
+        std::vector<int32_t>& up = sp_upd[D.gid[x]];
+        for (int64_t q = D.rows_ptr[x] + D.ne[x]; q < D.rows_ptr[x + 1]; ++q) up.push_back(vid(i, D.rows[q]));
+      }
+      add_flops(h.get(), G.ne, G.nu, 0, false);
+    }
 
     const int nnz = sd.rowptr[sd.n];
     h_rowptr.insert(h_rowptr.end(), sd.rowptr, sd.rowptr + sd.n + 1);
@@ -691,7 +812,7 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
     rp_off += sd.n + 1;
     b_off += sd.nb;
     const double ng = (double)(sd.n - n_int);
-    add_flops(h.get(), sd.n, F.nu, ng, true);
+    if (!D.nf) add_flops(h.get(), sd.n, F.nu, ng, true);
   }
   h->n_loc = vec_off;
   h->nnz_total = csr_off;
@@ -715,13 +836,26 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
   }
 
   // ---- node fronts (post-order: children before parents) ----------------------
-  std::vector<std::vector<int32_t>> sep(n_front), upd(n_front);
+  std::vector<std::vector<int32_t>> sep(n_front_all), upd(n_front_all);
   for (int d = 0; d < n_dual; ++d) sep[dual_node[d]].push_back(d);
   for (int i = 0; i < n_sub; ++i) upd[i] = h->leaf_duals[i];
-  std::vector<std::vector<int32_t>> children(n_front);
-  for (int x = 0; x < n_front; ++x)
+  std::vector<std::vector<int32_t>> children(n_front_all);
+  for (int x = 0; x < n_front_all; ++x)
     if (par[x] >= 0) children[par[x]].push_back(x);
-  std::vector<int> height(n_front, 0);
+  std::vector<int> height(n_front_all, 0);
+  // sparse-domain fronts: rows, separator ids and heights (children first)
+  for (int i = 0; i < n_sub; ++i) {
+    const SparseDomain& D = spd[i];
+    for (int x = 0; x < D.nf; ++x) {
+      const int g = D.gid[x];
+      sep[g] = sp_sep[g];
+      if (x != D.root) upd[g] = sp_upd[g];
+      if (children[g].size() > 2) return DD_ERR_INVALID_ARG;   // the dissection is binary
+      int hgt = 0;
+      for (int c : children[g]) hgt = std::max(hgt, height[c] + 1);
+      height[g] = hgt;
+    }
+  }
   for (int v = n_sub; v < n_front; ++v) {
     FrontDev& F = h->fronts[v];
     F.kind = 1;
@@ -767,19 +901,29 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
     add_flops(h.get(), F.ne, F.nu, 0, false);
     h->stats.max_front = std::max(h->stats.max_front, F.ld);
   }
+  for (int g = n_front; g < n_front_all; ++g) h->stats.max_front = std::max(h->stats.max_front, h->fronts[g].ld);
+  // sparse-domain fronts: separator ids, children (the extend-add maps follow below)
+  for (int i = 0; i < n_sub; ++i)
+    for (int g : spd[i].gid) {
+      FrontDev& G = h->fronts[g];
+      G.sep_off = (int32_t)h_sep.size();
+      h_sep.insert(h_sep.end(), sep[g].begin(), sep[g].end());
+      for (size_t slot = 0; slot < children[g].size(); ++slot) G.child[slot] = children[g][slot];
+    }
 
   // ---- update-row order: every front's update rows follow its parent's row
   // order, so each extend-add map is increasing and a child's block lands in
   // its parent row by row, in order (coalesced, never transposed) ----------------
   {
-    std::vector<int32_t> rowpos(std::max(n_dual, 1), -1);
+    const int64_t n_ids = (int64_t)n_dual + (h->n_sparse ? vec_off : 0);
+    std::vector<int32_t> rowpos(std::max<int64_t>(n_ids, 1), -1);
     std::vector<int> order;   // parents before children
-    for (int x = 0; x < n_front; ++x)
+    for (int x = 0; x < n_front_all; ++x)
       if (par[x] < 0) order.push_back(x);
     for (size_t q = 0; q < order.size(); ++q)
       for (int c : children[order[q]]) order.push_back(c);
     for (int v : order) {
-      if (v < n_sub) continue;
+      if (h->fronts[v].kind == 0) continue;
       const FrontDev& F = h->fronts[v];
       for (size_t r = 0; r < sep[v].size(); ++r) rowpos[sep[v][r]] = (int32_t)r;
       for (size_t r = 0; r < upd[v].size(); ++r) rowpos[upd[v][r]] = F.ne_pad + (int32_t)r;
@@ -789,12 +933,13 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
       for (int d : upd[v]) rowpos[d] = -1;
     }
     h_upd.clear();
-    for (int x = 0; x < n_front; ++x) {
+    for (int x = 0; x < n_front_all; ++x) {
       h->fronts[x].upd_off = (int32_t)h_upd.size();
       h_upd.insert(h_upd.end(), upd[x].begin(), upd[x].end());
     }
     h_maps.clear();
-    for (int v = n_sub; v < n_front; ++v) {
+    for (int v = 0; v < n_front_all; ++v) {
+      if (h->fronts[v].kind == 0) continue;
       FrontDev& F = h->fronts[v];
       for (size_t r = 0; r < sep[v].size(); ++r) rowpos[sep[v][r]] = (int32_t)r;
       for (size_t r = 0; r < upd[v].size(); ++r) rowpos[upd[v][r]] = F.ne_pad + (int32_t)r;
@@ -822,7 +967,7 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
   // ---- offsets, levels, task lists ----------------------------------------------
   int64_t off = 0, roff = 0, toff = 0;
   int64_t bytes_factor = 0;
-  for (int x = 0; x < n_front; ++x) {
+  for (int x = 0; x < n_front_all; ++x) {
     FrontDev& F = h->fronts[x];
     F.off = off;
     F.roff = roff;
@@ -836,10 +981,13 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
   h->rows_total = roff;
   h->n_tiles = toff;
   int max_h = 0;
-  for (int x = 0; x < n_front; ++x) max_h = std::max(max_h, height[x]);
+  for (int x = 0; x < n_front_all; ++x) max_h = std::max(max_h, height[x]);
   h->levels.assign(max_h + 1, Level{});
-  for (int x = 0; x < n_front; ++x)
-    if (h->fronts[x].ld > 0 || x < n_sub) h->levels[height[x]].ids.push_back(x);
+  for (int x = 0; x < n_front_all; ++x)
+    if (h->fronts[x].ld > 0 || x < n_sub) {
+      h->levels[height[x]].ids.push_back(x);
+      if (h->fronts[x].kind == 1) h->levels[height[x]].n_aux++;
+    }
   // mixed form: panel image workspace, reused level after level
   if (h->use_tc) {
     // slots 0 and 1 hold the images of even / odd panels of every level; the
@@ -1027,26 +1175,82 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
   }
 
   if (sym) {
-    *sym->n_front = n_front;
-    if (sym->max_fronts < n_front) return DD_ERR_INVALID_ARG;
+    *sym->n_front = n_front_all;
+    if (sym->max_fronts < n_front_all) return DD_ERR_INVALID_ARG;
     int64_t tot = 0;
-    for (int x = 0; x < n_front; ++x) {
+    for (int x = 0; x < n_front_all; ++x) {
       sym->parent[x] = par[x];
       sym->ne[x] = h->fronts[x].ne;
       sym->nu[x] = h->fronts[x].nu;
       if (sym->upd_ptr) sym->upd_ptr[x] = tot;
       tot += (int64_t)upd[x].size();
     }
-    if (sym->upd_ptr) sym->upd_ptr[n_front] = tot;
+    if (sym->upd_ptr) sym->upd_ptr[n_front_all] = tot;
     for (int d = 0; d < n_dual; ++d) sym->dual_front[d] = dual_node[d];
     if (sym->upd_idx) {
       if (sym->upd_cap < tot) return DD_ERR_INVALID_ARG;
       int64_t q = 0;
-      for (int x = 0; x < n_front; ++x)
+      for (int x = 0; x < n_front_all; ++x)
         for (int32_t d : upd[x]) sym->upd_idx[q++] = d;
     }
     return DD_OK;
   }
+
+  // ---- sparse domains: the front position of every A_i entry (the front
+  // eliminating the earlier of its row and column), of every B_i entry (the
+  // root's update rows) and of the padding diagonals, for the initialisation
+  std::vector<int64_t> h_sp_dst;
+  std::vector<int32_t> h_sp_src;   // >= 0: index into the stacked CSR values; -1: +1; -2: -1
+  std::vector<int32_t> h_lvl0;
+  h->ld_lam = n_dual;
+  if (h->n_sparse) {
+    h->ld_lam = (int64_t)n_dual + h->n_loc;
+    std::vector<int32_t> rowpos((size_t)h->ld_lam, -1);
+    int64_t csr0 = 0, b0 = 0;
+    for (int i = 0; i < n_sub; ++i) {
+      const SparseDomain& D = spd[i];
+      const dd_subdomain& sd = subs[i];
+      const int64_t nnz = sd.rowptr[sd.n];
+      if (D.nf) {
+        std::vector<std::vector<std::pair<int32_t, int32_t>>> by_front(D.nf);   // (CSR entry, its row)
+        for (int r = 0; r < sd.n; ++r)
+          for (int q = sd.rowptr[r]; q < sd.rowptr[r + 1]; ++q)
+            if (D.a_front[q] >= 0) by_front[D.a_front[q]].push_back({q, r});
+        for (int x = 0; x < D.nf; ++x) {
+          const int g = D.gid[x];
+          const FrontDev& G = h->fronts[g];
+          for (size_t r = 0; r < sep[g].size(); ++r) rowpos[sep[g][r]] = (int32_t)r;
+          if (x != D.root)
+            for (size_t r = 0; r < upd[g].size(); ++r) rowpos[upd[g][r]] = G.ne_pad + (int32_t)r;
+          for (auto [q, r] : by_front[x]) {
+            const int pc = rowpos[vid(i, r)], pr = rowpos[vid(i, sd.colind[q])];
+            if (pc < 0 || pc >= G.ne || pr < pc) return DD_ERR_INVALID_ARG;
+            h_sp_dst.push_back(G.off + (int64_t)pr * G.ld + pc);
+            h_sp_src.push_back((int32_t)(csr0 + q));
+          }
+          for (int r = G.ne; r < G.ne_pad; ++r) {
+            h_sp_dst.push_back(G.off + (int64_t)r * G.ld + r);
+            h_sp_src.push_back(-1);
+          }
+          if (x == D.root)
+            for (int k = 0; k < sd.nb; ++k) {
+              const int pc = rowpos[vid(i, sd.b_local[k])];
+              if (pc < 0 || pc >= G.ne) return DD_ERR_INVALID_ARG;
+              h_sp_dst.push_back(G.off + (int64_t)(G.ne_pad + h_brow[b0 + k]) * G.ld + pc);
+              h_sp_src.push_back(sd.b_sign[k] > 0 ? -1 : -2);
+            }
+          for (int32_t id : sep[g]) rowpos[id] = -1;
+          if (x != D.root)
+            for (int32_t id : upd[g]) rowpos[id] = -1;
+          if (height[g] == 0) h_lvl0.push_back(g);
+        }
+      }
+      csr0 += nnz;
+      b0 += sd.nb;
+    }
+  }
+  h->n_scatter = (int64_t)h_sp_dst.size();
+  h->n_lvl0_sparse = (int)h_lvl0.size();
 
   // ---- upload (everything above is host-only validation and analysis) -------------
   int ndev = 0;
@@ -1088,6 +1292,11 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
   DD_CUDA(A.upload(&h->d_tc, h_tc, s));
   DD_CUDA(A.upload(&h->d_tc2, h_tc2, s));
   DD_CUDA(A.upload(&h->d_grp, h_grp, s));
+  if (h->n_sparse) {
+    DD_CUDA(A.upload(&h->d_sp_dst, h_sp_dst, s));
+    DD_CUDA(A.upload(&h->d_sp_src, h_sp_src, s));
+    DD_CUDA(A.upload(&h->d_lvl0_sparse, h_lvl0, s));
+  }
   {
     int nl = 0;
     for (auto& L : h->levels) nl += 2 * (int)L.steps.size();
@@ -1128,7 +1337,7 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
 
   h->stats.n_sub = n_sub;
   h->stats.n_dual = n_dual;
-  h->stats.n_fronts = n_front;
+  h->stats.n_fronts = n_front_all;
   h->stats.n_levels = (int)h->levels.size();
   h->stats.n_primal = h->n_loc;
   h->stats.bytes_factor = bytes_factor;
@@ -1208,8 +1417,10 @@ static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& n
   DD_CUDA(mark(DD_K_INIT, true));
   ddk::launch_leaf_init(p, h->pool, h->d_fronts, h->d_leaves, h->n_sub, h->d_rowptr, h->d_colind, h->d_val,
                         h->d_iperm, h->d_brow, h->d_blocal, h->d_bsign, s);
+  ddk::launch_sparse_init(p, h->pool, h->d_sp_dst, h->d_sp_src, h->n_scatter, h->d_val, s);
   DD_CUDA(mark(DD_K_INIT, false));
   count(DD_K_INIT, 1);
+  count(DD_K_INIT, h->n_scatter > 0 ? 1 : 0);
   for (size_t l = 0; l < h->levels.size(); ++l) {
     const Level& L = h->levels[l];
     const int32_t* ids = h->d_level_ids + L.ids_off;
@@ -1224,7 +1435,9 @@ static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& n
       count(DD_K_ASSEMBLE, n);
       count(DD_K_ASSEMBLE, n);
     }
-    const int diag64 = (l > 0) ? 1 : 0;  // mixed form: FP64 pivot blocks of the auxiliary matrix
+    // mixed form: FP64 pivot blocks for the auxiliary matrix's separator fronts,
+    // FP32 for the fronts that eliminate domain unknowns
+    const int diag64 = L.n_aux == 0 ? 0 : (L.n_aux == (int)L.ids.size() ? 1 : 2);
     // one-step look-ahead on levels with few fronts: the main stream updates
     // only the next panel columns and factors those panels, while the second
     // stream applies the rest of the trailing update
@@ -1249,8 +1462,9 @@ static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& n
                          h->d_piv);
       else
         ddk::launch_trsm_mx(h->pool, h->d_fronts, h->d_trsm + R.trsm_off, R.n_trsm, R.k, h->d_status, h->d_linv, ws,
-                            s, h->d_piv);
+                            s, h->d_piv, h->use_tc);
       count(DD_K_DIAG, R.n_diag);
+      if (p == 1 && diag64 == 2) count(DD_K_DIAG, R.n_diag);
       count(DD_K_TRSM, R.n_trsm);
       return mark(DD_K_TRSM, false);
     };
@@ -1550,7 +1764,10 @@ int dd_solve_subset(dd_handle* h, int32_t nrhs, const dd_c128* f, int64_t ldf, i
   std::vector<Task> sb;
   for (const Task& t : h->h_bwd_leaf)
     if (front_listed[t.f]) sb.push_back(t);
-  const bool refined = h->max_refine > 0;
+  // the full solve, then the listed rows: with refinement (the FP64 residual
+  // needs every domain) and with sparse domains (whose backward substitution
+  // runs over trees of fronts)
+  const bool refined = h->max_refine > 0 || h->n_sparse > 0;
   const bool u_dev = n_rows > 0 && is_device_ptr(u);
   const int32_t chunk = std::min<int32_t>(kSolveBlock, nrhs);
   auto al = [](size_t b) { return (b + 255) / 256 * 256; };
@@ -1583,7 +1800,6 @@ int dd_solve_subset(dd_handle* h, int32_t nrhs, const dd_c128* f, int64_t ldf, i
     double2* out = u_dev ? reinterpret_cast<double2*>(u + (size_t)c0 * ldu) : d_usub;
     const int64_t ldo = u_dev ? ldu : n_rows;
     if (refined) {
-      // the FP64 residual needs every domain: full refined solve, then the listed rows
       const int st = solve_block(h, nb, fc, ldf, nullptr, 0, lc, ldl);
       if (st != DD_OK && st != DD_ERR_NOT_CONVERGED) return st;
       if (st == DD_ERR_NOT_CONVERGED) status = st;

@@ -29,10 +29,12 @@ struct FrontDev {
   int32_t ne_pad;    // eliminated unknowns padded to DD_TILE (identity padding)
   int32_t nu;        // update (trailing) rows, unpadded
   int32_t n_int;     // leaf: number of interior unknowns (B rows vanish before it); node: 0
-  int32_t kind;      // 0 leaf, 1 node
-  int32_t sub;       // leaf: domain id; node: -1
+  int32_t kind;      // 0 dense domain front, 1 separator front of the auxiliary matrix, 2 front of a
+                     // sparse domain's nested-dissection tree (rows given by row ids; the root,
+                     // front i of domain i, has the domain's duals as update rows)
+  int32_t sub;       // leaf and sparse-domain fronts: domain id; node: -1
   int32_t upd_off;   // offset of the nu dual ids of the update rows
-  int32_t sep_off;   // node: offset of the ne dual ids of the separator rows
+  int32_t sep_off;   // node / sparse-domain front: offset of the ne row ids of its own rows
   int32_t child[2];  // node: child fronts (-1 if absent)
   int32_t map_off[2];// node: offsets of the extend-add maps (child update row -> row here)
   int32_t tile_off;  // offset of this front's per-tile ready flags (ld / DD_TILE of them)
@@ -42,19 +44,16 @@ struct FrontDev {
 };
 
 // Panel operand images for the tensor-core trailing update (mixed form), one
-// per trailing 64-row tile t of a panel step, 64B-swizzled K-major, in pieces
-// of 128 rows x one K atom (16 tf32, 64 B a row) = 8 KB, indexed (split
-// hi/lo, atom 0..3):
+// per trailing 64-row tile t of a panel step, 128B-swizzled K-major, in pieces
+// of 128 rows x one K atom (32 tf32) = 16 KB, indexed (split hi/lo, atom):
 //   A image (rows of L): within a piece, for each group of 16 tile rows, their
 //     real parts then their imaginary parts (piece row 32 (r / 16) + r % 16 and
 //     + 16), so the two parts of a row land in one TMEM sub-partition;
 //   B image (rows of W = L D): within a piece, the 64 real rows then the 64
 //     imaginary rows.
-#define DD_TC_KATOM 16
-#define DD_TC_NATOM (DD_TILE / DD_TC_KATOM)
-#define DD_TC_ATOM 8192
-#define DD_TC_ATILE (2 * DD_TC_NATOM * DD_TC_ATOM)
-#define DD_TC_BTILE (2 * DD_TC_NATOM * DD_TC_ATOM)
+#define DD_TC_ATOM 16384
+#define DD_TC_ATILE (2 * 2 * DD_TC_ATOM)
+#define DD_TC_BTILE (2 * 2 * DD_TC_ATOM)
 
 struct LeafDev {
   int64_t csr_off;   // offset of the domain's nonzeros in the concatenated CSR arrays
@@ -93,6 +92,9 @@ void launch_leaf_init(int prec, void* pool, const FrontDev* fronts, const LeafDe
                       const int8_t* b_sign, cudaStream_t s);
 void launch_node_init(int prec, void* pool, const FrontDev* fronts, const int32_t* node_ids, int n,
                       cudaStream_t s);
+// sparse-domain fronts: pool[dst[e]] = val[src[e]] (src -1: +1, -2: -1)
+void launch_sparse_init(int prec, void* pool, const int64_t* dst, const int32_t* src, int64_t n, const double2* val,
+                        cudaStream_t s);
 // piv (optional): one byte per pivot position of every diagonal tile (index
 // (tile_off + tile) * 64 + c), the permutation of the restricted Bunch-Kaufman
 // pivoting of the fronts with FrontDev::piv set; nullptr: no front pivots
@@ -101,12 +103,15 @@ void launch_diag(int prec, int diag_fp64, void* pool, const FrontDev* fronts, co
                  int k, DevStatus* st, cudaStream_t s, uint8_t* piv = nullptr);
 void launch_trsm(int prec, void* pool, const FrontDev* fronts, const Task* tasks, int n, int k,
                  DevStatus* st, cudaStream_t s, unsigned char* ws = nullptr, const uint8_t* piv = nullptr);
-// mixed form: 64 x 64 diagonal tile with 32 x 32 pivot blocks (FP64 if
-// diag_fp64) and L_kk^{-1} (FP32, 64 x 64 per front id) for the panel product
+// mixed form: 64 x 64 diagonal tile with 32 x 32 pivot blocks (diag_fp64: 0
+// FP32, 1 FP64, 2 FP64 for separator fronts and FP32 for domain fronts) and
+// L_kk^{-1} (FP32, 64 x 64 per front id) for the panel product
 void launch_diag_mx(int diag_fp64, void* pool, const FrontDev* fronts, const int32_t* fids, int n, int k,
                     DevStatus* st, void* linv, cudaStream_t s, uint8_t* piv = nullptr);
+// tensor != 0: the product with L_kk^{-1} on the tensor cores (tcgen05 3xTF32), else on the FP32 FMA pipes
 void launch_trsm_mx(void* pool, const FrontDev* fronts, const Task* tasks, int n, int k, DevStatus* st,
-                    const void* linv, unsigned char* ws, cudaStream_t s, const uint8_t* piv = nullptr);
+                    const void* linv, unsigned char* ws, cudaStream_t s, const uint8_t* piv = nullptr,
+                    int tensor = 0);
 // tensor-core trailing update (mixed form): task (front, row tile i, column
 // tile j); .pad bits 0 / 1 store column tiles j / j + 1, bits 2 / 3 add the
 // products of panel k (images in ws0) / panel k + 1 (images in ws1).
@@ -123,27 +128,34 @@ void launch_extend_add(int prec, void* pool, const FrontDev* fronts, const int32
 // ---- solve --------------------------------------------------------------------
 void launch_rhs_leaf(int prec, void* rpool, const FrontDev* fronts, const LeafDev* leaves, int n_leaves,
                      const int32_t* perm, const double2* f, int64_t ldf, int nrhs, cudaStream_t s);
+// separator fronts: own rows <- g (NULL: zero); sparse-domain fronts: own rows <- f
+// by row id (n_dual + stacked row); dense domain fronts are left alone
 void launch_rhs_node(int prec, void* rpool, const FrontDev* fronts, const int32_t* node_ids, int n,
-                     const int32_t* sep, const double2* g, int64_t ldg, int nrhs, cudaStream_t s);
+                     const int32_t* sep, const double2* g, int64_t ldg, const double2* f, int64_t ldf, int n_dual,
+                     int nrhs, cudaStream_t s);
 void launch_rhs_extend_add(int prec, void* rpool, const FrontDev* fronts, const int32_t* node_ids, int n,
                            int slot, const int32_t* maps, int nrhs, cudaStream_t s);
 // tile-parallel substitution: one CTA per (front, tile) task of a level; a
 // CTA waits (bounded) on the ready flags of the tiles it depends on
 // linv (mixed form, optional): FP32 inverses of the unit-lower diagonal tiles,
 // index tile_off + tile; when given, the in-tile triangular solves are products
+// tensor != 0 (mixed form, 4..64 right-hand sides): the tile products on the
+// tensor cores (tcgen05 3xTF32), else on the FP32 FMA pipes
 void launch_forward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const Task* tasks, int n,
                     int nrhs, int32_t* flags, int epoch, DevStatus* st, cudaStream_t s,
-                    const void* linv = nullptr, const uint8_t* piv = nullptr);
+                    const void* linv = nullptr, const uint8_t* piv = nullptr, int tensor = 0);
 // upart (optional, separator levels): scratch for the update-row partial sums
 // (n x nsplit x nrhs x 64 elements); the update-row product then runs as a
 // separate launch split nsplit ways.  Returns the number of kernels launched.
 int launch_backward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const Task* tasks, int n,
                     int nrhs, const int32_t* upd, const int32_t* sep, void* lam_work, int64_t ld_lam,
                     int32_t* flags, int epoch, DevStatus* st, cudaStream_t s, const void* linv = nullptr,
-                    const uint8_t* piv = nullptr, void* upart = nullptr, int nsplit = 0);
+                    const uint8_t* piv = nullptr, void* upart = nullptr, int nsplit = 0, int tensor = 0);
+// u of every listed domain: from its dense front (rows through perm) or, for a
+// sparse domain, from the row-id vector lam (ld_lam, rows n_dual + stacked row)
 void launch_leaf_out(int prec, const void* rpool, const FrontDev* fronts, const LeafDev* leaves,
                      int n_leaves, const int32_t* perm, double2* u, int64_t ldu, int nrhs, int accumulate,
-                     cudaStream_t s);
+                     cudaStream_t s, const void* lam, int64_t ld_lam, int n_dual);
 void launch_lam_out(int prec, const void* lam_work, int64_t ld_work, int n_dual, int nrhs, double2* lam,
                     int64_t ldl, int accumulate, cudaStream_t s);
 

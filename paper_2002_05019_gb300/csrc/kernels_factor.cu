@@ -12,6 +12,7 @@
 #include "dd_complex.cuh"
 #include "dd_internal.h"
 #include "dd_pivot.cuh"
+#include "dd_tc.cuh"
 
 namespace ddk {
 
@@ -21,23 +22,10 @@ constexpr int T = DD_TILE;
 
 __device__ __forceinline__ int tri(int i, int c) { return (i * (i + 1)) / 2 + c; }
 
-// byte offset of element (row, k), k in 0..15, in a 64B-swizzled K-major atom
-// (8-row groups of 512 B; the 16-byte chunk index is XORed with address bits
-// 7-8, i.e. with (row / 2) % 4)
-__device__ __forceinline__ int swz64(int row, int k) {
-  return (row >> 3) * 512 + (row & 7) * 64 + ((((k >> 2) ^ ((row >> 1) & 3))) << 4) + (k & 3) * 4;
-}
-// x = hi + lo with hi, lo representable in tf32 (round to nearest, ties away)
-__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
-  uint32_t h, l;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-  const float r = x - __uint_as_float(h);
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(r));
-  hi = __uint_as_float(h);
-  lo = __uint_as_float(l);
-}
+using tc::split_tf32;
+using tc::swz128;
 __device__ __forceinline__ void put_img(unsigned char* base, int row, int k, float v) {
-  *reinterpret_cast<float*>(base + swz64(row, k)) = v;
+  *reinterpret_cast<float*>(base + swz128(row, k)) = v;
 }
 
 template <typename S>
@@ -47,23 +35,23 @@ template <>
 __device__ __forceinline__ void write_images<float2>(unsigned char* ws, const FrontDev& F, int ti, int rc, float2 L,
                                                      float2 W) {
   const int r = rc >> 6, p = rc & 63;              // row of the tile, K index
-  const int a = p / DD_TC_KATOM, kk = p % DD_TC_KATOM;
+  const int a = p >> 5, kk = p & 31;
   const int ra = (r >> 4) * 32 + (r & 15);         // A piece row of the real part (imaginary: + 16)
   unsigned char* Ab = ws + F.ws_off + (int64_t)ti * DD_TC_ATILE;
   unsigned char* Bb = ws + F.ws_boff + (int64_t)ti * DD_TC_BTILE;
   float h, l;
   split_tf32(L.x, h, l);
-  put_img(Ab + (0 * DD_TC_NATOM + a) * DD_TC_ATOM, ra, kk, h);
-  put_img(Ab + (1 * DD_TC_NATOM + a) * DD_TC_ATOM, ra, kk, l);
+  put_img(Ab + (0 * 2 + a) * DD_TC_ATOM, ra, kk, h);
+  put_img(Ab + (1 * 2 + a) * DD_TC_ATOM, ra, kk, l);
   split_tf32(L.y, h, l);
-  put_img(Ab + (0 * DD_TC_NATOM + a) * DD_TC_ATOM, ra + 16, kk, h);
-  put_img(Ab + (1 * DD_TC_NATOM + a) * DD_TC_ATOM, ra + 16, kk, l);
+  put_img(Ab + (0 * 2 + a) * DD_TC_ATOM, ra + 16, kk, h);
+  put_img(Ab + (1 * 2 + a) * DD_TC_ATOM, ra + 16, kk, l);
   split_tf32(W.x, h, l);
-  put_img(Bb + (0 * DD_TC_NATOM + a) * DD_TC_ATOM, r, kk, h);
-  put_img(Bb + (1 * DD_TC_NATOM + a) * DD_TC_ATOM, r, kk, l);
+  put_img(Bb + (0 * 2 + a) * DD_TC_ATOM, r, kk, h);
+  put_img(Bb + (1 * 2 + a) * DD_TC_ATOM, r, kk, l);
   split_tf32(W.y, h, l);
-  put_img(Bb + (0 * DD_TC_NATOM + a) * DD_TC_ATOM, r + 64, kk, h);
-  put_img(Bb + (1 * DD_TC_NATOM + a) * DD_TC_ATOM, r + 64, kk, l);
+  put_img(Bb + (0 * 2 + a) * DD_TC_ATOM, r + 64, kk, h);
+  put_img(Bb + (1 * 2 + a) * DD_TC_ATOM, r + 64, kk, l);
 }
 
 __device__ void status_pivot(DevStatus* st, int front, int row) {
@@ -89,6 +77,7 @@ __global__ void k_leaf_init(S* pool, const FrontDev* fr, const LeafDev* lv, cons
                             const int32_t* b_row, const int32_t* b_local, const int8_t* b_sign) {
   const LeafDev L = lv[blockIdx.x];
   const FrontDev F = fr[L.front];
+  if (F.kind != 0) return;   // a sparse domain: its fronts are filled by k_sparse_init
   S* A = pool + F.off;
   const int32_t* rp = rowptr + L.rowptr_off;
   const int32_t* ip = iperm + L.perm_off;
@@ -107,6 +96,16 @@ __global__ void k_leaf_init(S* pool, const FrontDev* fr, const LeafDev* lv, cons
     const int row = F.ne_pad + b_row[L.b_off + q];
     const int col = ip[b_local[L.b_off + q]];
     A[(int64_t)row * F.ld + col] = cmake<S>((float)b_sign[L.b_off + q], 0);
+  }
+}
+
+// fronts of sparse domains: every A_i entry, B_i entry and padding diagonal
+// goes to its precomputed pool position (src >= 0: a CSR value; -1: +1; -2: -1)
+template <typename S>
+__global__ void k_sparse_init(S* pool, const int64_t* dst, const int32_t* src, int64_t n, const double2* val) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t q = src[e];
+    pool[dst[e]] = q >= 0 ? cconv<S>(val[q]) : cmake<S>(q == -1 ? 1 : -1, 0);
   }
 }
 
@@ -365,7 +364,7 @@ __device__ void inv_unit_lower32(const float2* a, int jb, float2* li) {
 
 template <typename C>
 __global__ void __launch_bounds__(256, 1) k_diag_mx(float2* pool, const FrontDev* fr, const int32_t* fids, int k,
-                                                 DevStatus* st, float2* linv, uint8_t* piv) {
+                                                 DevStatus* st, float2* linv, uint8_t* piv, int sel) {
   __shared__ float2 a[T * (T + 1) / 2];
   __shared__ float2 li[T * (T + 1) / 2];   // L_kk^{-1}, packed lower
   // the precision-C pivot block, and between the two block factorizations the
@@ -387,6 +386,8 @@ __global__ void __launch_bounds__(256, 1) k_diag_mx(float2* pool, const FrontDev
   __shared__ int cnt[2];
   const int f = fids[blockIdx.x];
   const FrontDev F = fr[f];
+  // sel 1: separator fronts of the auxiliary matrix only, 2: domain fronts only
+  if ((sel == 1 && F.kind != 1) || (sel == 2 && F.kind == 1)) return;
   const bool pv = piv != nullptr && F.piv != 0;
   float2* base = pool + F.off + (int64_t)(k * T) * F.ld + k * T;
   for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
@@ -627,6 +628,106 @@ __global__ void __launch_bounds__(256) k_trsm_mx(float2* pool, const FrontDev* f
   if ((threadIdx.x & 31) == 0 && mx > 0.f && isfinite(mx)) atomic_max_pos(&st->max_abs_l, sqrt((double)mx));
 }
 
+// mixed form panel on the tensor cores: X = A_ik P_k^T L_kk^{-T} as one 3xTF32
+// tcgen05 product with the stored inverse (M = 128: real and imaginary rows
+// of A_ik, N = 128: real and imaginary rows of L_kk^{-1}, K = 64), the
+// accumulator in TMEM; then L_ik = X D_k^{-1} and the operand images of the
+// trailing update, as k_trsm_mx.  256 threads; warps 0-3 drain TMEM.
+constexpr int kTrsmTcSmem = 2 * tc::kImage + 1024;   // A and B images (later X), 1024-aligned
+__global__ void __launch_bounds__(256, 1) k_trsm_tc(float2* pool, const FrontDev* fr, const Task* tasks, int k,
+                                                    DevStatus* st, const float2* linv, unsigned char* ws,
+                                                    const uint8_t* piv) {
+  extern __shared__ __align__(1024) unsigned char tc_raw[];
+  unsigned char* smem = tc_raw + ((1024u - (tc::smem_u32(tc_raw) & 1023u)) & 1023u);
+  unsigned char* imgA = smem;
+  unsigned char* imgB = smem + tc::kImage;
+  float2 (*Xs)[T + 1] = reinterpret_cast<float2 (*)[T + 1]>(smem);   // after the product
+  __shared__ float2 rinv[T];
+  __shared__ float2 g1[T];
+  __shared__ int qc[T];
+  __shared__ int perm[T];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int ok_s;
+  const Task t = tasks[blockIdx.x];
+  const FrontDev F = fr[t.f];
+  const bool pv = piv != nullptr && F.piv != 0;
+  const int64_t ld = F.ld;
+  float2* Aik = pool + F.off + (int64_t)(t.i * T) * ld + k * T;
+  const float2* Dk = pool + F.off + (int64_t)(k * T) * ld + k * T;
+  const float2* Li = linv + ((int64_t)F.tile_off + k) * T * T;
+  const int warp = threadIdx.x >> 5;
+  const uint32_t b = tc::smem_u32(&bar);
+  if (threadIdx.x == 0) {
+    tc::mbar_init(b, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&tmem_slot)),
+                 "r"(128));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x < T) {
+    const int p = threadIdx.x;
+    if (pv) {
+      float2 g0, gg;
+      int q;
+      dinv_col(Dk, ld, p, g0, gg, q);
+      rinv[p] = g0;
+      g1[p] = gg;
+      qc[p] = q;
+      perm[p] = piv[((int64_t)F.tile_off + k) * T + p];
+    } else {
+      rinv[p] = cdiv(make_float2(1.f, 0.f), Dk[(int64_t)p * (ld + 1)]);
+      perm[p] = p;
+    }
+  }
+  __syncthreads();
+  // operand images: A = A_ik P_k^T (rows r, K index q), B = L_kk^{-1} (rows p, K index q)
+  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+    const int r = idx / T, q = idx % T;
+    tc::put_a(imgA, r, q, Aik[(int64_t)r * ld + perm[q]]);
+    tc::put_b(imgB, r, q, Li[idx]);
+  }
+  asm volatile("fence.proxy.async.shared::cta;");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+  if (threadIdx.x == 0) {
+    tc::mma_tile(tmem, tc::smem_u32(imgA), tc::smem_u32(imgB), false);
+    tc::mma_commit(b);
+  }
+  if (threadIdx.x == 0) ok_s = tc::mbar_wait(b, 0) ? 1 : 0;
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const bool ok = ok_s != 0;
+  if (ok && warp < 4) tc::read_tile(tmem, [&](int r, int c, float2 v) { Xs[r][c] = v; });
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+  if (!ok) {
+    if (threadIdx.x == 0 && atomicCAS(&st->code, 0, 8) == 0) {
+      st->front = t.f;
+      st->row = k;
+    }
+    return;
+  }
+  // L_ik = X D_k^{-1}; growth statistic in FP32: max |l d|^2
+  float mx = 0.f;
+  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+    const int rr = idx / T, p = idx % T;
+    const float2 x = Xs[rr][p];
+    mx = fmaxf(mx, x.x * x.x + x.y * x.y);
+    const float2 lv = pv ? cfma(Xs[rr][qc[p]], g1[p], cmul(x, rinv[p])) : cmul(x, rinv[p]);
+    Aik[(int64_t)rr * ld + p] = lv;
+    if (ws) write_images<float2>(ws, F, t.i - k - 1, idx, lv, x);
+  }
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0 && mx > 0.f && isfinite(mx)) atomic_max_pos(&st->max_abs_l, sqrt((double)mx));
+}
+
 // ---------------------------------------------------------------------------
 // panel: X = A_ik L_kk^{-T} (= L_ik D_k), then L_ik = X D_k^{-1}
 // dynamic shared memory: Lt[64][64] (Lt[j][p] = L_kk[p][j]) + X[64][65] + d[64]
@@ -819,6 +920,14 @@ void launch_leaf_init(int prec, void* pool, const FrontDev* fronts, const LeafDe
                                                  b_row, b_local, b_sign);
 }
 
+void launch_sparse_init(int prec, void* pool, const int64_t* dst, const int32_t* src, int64_t n, const double2* val,
+                        cudaStream_t s) {
+  if (n <= 0) return;
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 4096);
+  if (prec == 0) k_sparse_init<double2><<<grid, 256, 0, s>>>((double2*)pool, dst, src, n, val);
+  else k_sparse_init<float2><<<grid, 256, 0, s>>>((float2*)pool, dst, src, n, val);
+}
+
 void launch_node_init(int prec, void* pool, const FrontDev* fronts, const int32_t* ids, int n, cudaStream_t s) {
   if (n <= 0) return;
   if (prec == 0) k_node_init<double2><<<n, 64, 0, s>>>((double2*)pool, fronts, ids);
@@ -835,14 +944,27 @@ void launch_diag(int prec, int diag_fp64, void* pool, const FrontDev* fronts, co
 void launch_diag_mx(int diag_fp64, void* pool, const FrontDev* fronts, const int32_t* fids, int n, int k,
                     DevStatus* st, void* linv, cudaStream_t s, uint8_t* piv) {
   if (n <= 0) return;
-  if (diag_fp64) k_diag_mx<double2><<<n, 256, 0, s>>>((float2*)pool, fronts, fids, k, st, (float2*)linv, piv);
-  else k_diag_mx<float2><<<n, 256, 0, s>>>((float2*)pool, fronts, fids, k, st, (float2*)linv, piv);
+  // diag_fp64: 0 FP32 pivot blocks, 1 FP64, 2 by front: FP64 for the auxiliary
+  // matrix's separator fronts, FP32 for domain fronts (two launches)
+  if (diag_fp64 == 1 || diag_fp64 == 2)
+    k_diag_mx<double2><<<n, 256, 0, s>>>((float2*)pool, fronts, fids, k, st, (float2*)linv, piv, diag_fp64 == 2 ? 1 : 0);
+  if (diag_fp64 == 0 || diag_fp64 == 2)
+    k_diag_mx<float2><<<n, 256, 0, s>>>((float2*)pool, fronts, fids, k, st, (float2*)linv, piv, diag_fp64 == 2 ? 2 : 0);
 }
 
 void launch_trsm_mx(void* pool, const FrontDev* fronts, const Task* tasks, int n, int k, DevStatus* st,
-                    const void* linv, unsigned char* ws, cudaStream_t s, const uint8_t* piv) {
+                    const void* linv, unsigned char* ws, cudaStream_t s, const uint8_t* piv, int tensor) {
   if (n <= 0) return;
-  k_trsm_mx<<<n, 256, 0, s>>>((float2*)pool, fronts, tasks, k, st, (const float2*)linv, ws, piv);
+  if (tensor) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_trsm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTrsmTcSmem);
+      attr = true;
+    }
+    k_trsm_tc<<<n, 256, kTrsmTcSmem, s>>>((float2*)pool, fronts, tasks, k, st, (const float2*)linv, ws, piv);
+  } else {
+    k_trsm_mx<<<n, 256, 0, s>>>((float2*)pool, fronts, tasks, k, st, (const float2*)linv, ws, piv);
+  }
 }
 
 void launch_trsm(int prec, void* pool, const FrontDev* fronts, const Task* tasks, int n, int k, DevStatus* st,

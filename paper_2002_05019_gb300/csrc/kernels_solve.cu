@@ -12,6 +12,7 @@
 #include "dd_complex.cuh"
 #include "dd_internal.h"
 #include "dd_pivot.cuh"
+#include "dd_tc.cuh"
 
 namespace ddk {
 
@@ -35,6 +36,7 @@ __global__ void k_rhs_leaf(S* rpool, const FrontDev* fr, const LeafDev* lv, cons
                            int64_t ldf, int nrhs) {
   const LeafDev L = lv[blockIdx.x];
   const FrontDev F = fr[L.front];
+  if (F.kind != 0) return;   // a sparse domain: its fronts load f by row id (k_rhs_node)
   S* z = rpool + F.roff * nrhs;
   const int32_t* pm = perm + L.perm_off;
   for (int64_t e = threadIdx.x; e < (int64_t)F.ld * nrhs; e += blockDim.x) {
@@ -43,14 +45,24 @@ __global__ void k_rhs_leaf(S* rpool, const FrontDev* fr, const LeafDev* lv, cons
   }
 }
 
+// the right-hand side of a separator front (its own rows: the dual load g,
+// zero when g is NULL) or of a sparse-domain front (its own rows: the primal
+// loads f, row id n_dual + stacked row); update rows start at zero
 template <typename S>
 __global__ void k_rhs_node(S* rpool, const FrontDev* fr, const int32_t* ids, const int32_t* sep, const double2* g,
-                           int64_t ldg, int nrhs) {
+                           int64_t ldg, const double2* f, int64_t ldf, int n_dual, int nrhs) {
   const FrontDev F = fr[ids[blockIdx.x]];
+  if (F.kind == 0) return;
   S* z = rpool + F.roff * nrhs;
   for (int64_t e = threadIdx.x; e < (int64_t)F.ld * nrhs; e += blockDim.x) {
     const int r = (int)(e / nrhs), j = (int)(e % nrhs);
-    z[e] = (g != nullptr && r < F.ne) ? cconv<S>(g[sep[F.sep_off + r] + j * ldg]) : czero<S>();
+    S v = czero<S>();
+    if (r < F.ne) {
+      const int id = sep[F.sep_off + r];
+      if (F.kind == 2) v = cconv<S>(f[(id - n_dual) + j * ldf]);
+      else if (g != nullptr) v = cconv<S>(g[id + j * ldg]);
+    }
+    z[e] = v;
   }
 }
 
@@ -354,7 +366,7 @@ __global__ void __launch_bounds__(SOLVE_THREADS) k_backward(const S* pool, S* rp
   int xrow = 0, xdual = -1;
   if (threadIdx.x < T) {
     xrow = c0 + (pv ? perm[threadIdx.x] : threadIdx.x);
-    if (F.kind == 1 && xrow < F.ne) xdual = sep[F.sep_off + xrow];
+    if (F.kind != 0 && xrow < F.ne) xdual = sep[F.sep_off + xrow];
   }
   for (int jj = 0; jj < nrhs; ++jj) {
     S zc = czero<S>(), zq = czero<S>();
@@ -694,7 +706,265 @@ __global__ void __launch_bounds__(256) k_backward_mr(const float2* pool, float2*
     const float2 v = sm.X[cc][col];
     const int r = c0 + perm[cc];   // X_j = P_j^T (L_jj^{-T} Y)
     z[(int64_t)r * nrhs + col] = v;
-    if (F.kind == 1 && r < F.ne) lam[sep[F.sep_off + r] + col * ld_lam] = v;
+    if (F.kind != 0 && r < F.ne) lam[sep[F.sep_off + r] + col * ld_lam] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    st_release(flg + j, epoch);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Many right-hand sides on the tensor cores (mixed form, 4..64 columns): the
+// same substitutions as k_forward_mr / k_backward_mr, every 64 x 64 x 64
+// complex tile product a tcgen05 3xTF32 MMA (M = 128: real and imaginary rows
+// of the left factor, N = 128: real and imaginary parts of the 64 columns,
+// K = 64) accumulated in TMEM.  The CTA's 256 threads stage both operand
+// images (tf32 hi / lo), thread 0 issues the MMAs, and all wait (bounded) on
+// their completion; warps 0-3 drain TMEM into shared memory.
+// ---------------------------------------------------------------------------
+struct TcSolveSmem {
+  unsigned char img[2 * tc::kImage];   // A and B operand images
+  float2 X[T][T + 1];                  // the tile block of right-hand sides
+};
+constexpr int kTcSolveSmem = (int)sizeof(TcSolveSmem) + 1024;
+
+struct TcCtx {
+  unsigned char* imgA;
+  unsigned char* imgB;
+  uint32_t tmem, bar, phase;
+  bool acc;   // the accumulator holds a product
+};
+
+// acc (+)= A B^T with A(r, q) = fa(r, q), B(c, q) = fb(c, q) (r, c, q < 64).
+// A_QFAST / B_QFAST: the loop order that reads global memory contiguously.
+// Returns false when the wait for the MMAs gave up (status recorded).
+template <bool A_QFAST, bool B_QFAST, typename FA, typename FB>
+__device__ bool tc_product(TcCtx& c, FA fa, FB fb, DevStatus* st, int front, int tile) {
+  __shared__ int ok_s;
+  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+    const int r = A_QFAST ? idx / T : idx % T, q = A_QFAST ? idx % T : idx / T;
+    tc::put_a(c.imgA, r, q, fa(r, q));
+  }
+  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+    const int n = B_QFAST ? idx / T : idx % T, q = B_QFAST ? idx % T : idx / T;
+    tc::put_b(c.imgB, n, q, fb(n, q));
+  }
+  asm volatile("fence.proxy.async.shared::cta;");
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (threadIdx.x == 0) {
+    tc::mma_tile(c.tmem, tc::smem_u32(c.imgA), tc::smem_u32(c.imgB), c.acc);
+    tc::mma_commit(c.bar);
+    ok_s = tc::mbar_wait(c.bar, c.phase) ? 1 : 0;
+    if (!ok_s && atomicCAS(&st->code, 0, 8) == 0) {
+      st->front = front;
+      st->row = tile;
+    }
+  }
+  c.phase ^= 1;
+  c.acc = true;
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  return ok_s != 0;
+}
+
+__device__ __forceinline__ void tc_setup(TcCtx& c, unsigned char* raw, uint64_t* bar, uint32_t* slot) {
+  unsigned char* base = raw + ((1024u - (tc::smem_u32(raw) & 1023u)) & 1023u);
+  c.imgA = base;
+  c.imgB = base + tc::kImage;
+  c.bar = tc::smem_u32(bar);
+  c.phase = 0;
+  c.acc = false;
+  if (threadIdx.x == 0) {
+    tc::mbar_init(c.bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(slot)),
+                 "r"(128));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  c.tmem = *slot;
+}
+
+__device__ __forceinline__ void tc_release(const TcCtx& c) {
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (threadIdx.x < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(c.tmem), "r"(128));
+}
+
+// forward: Z_i = L_ii^{-1} P_i (B_i - sum_k L_ik Z_k) for eliminated tiles; update tiles only subtract
+__global__ void __launch_bounds__(256, 1) k_forward_tc(const float2* pool, float2* rpool, const FrontDev* fr,
+                                                       const Task* tasks, int nrhs, int32_t* flags, int epoch,
+                                                       DevStatus* st, const float2* linv, const uint8_t* piv) {
+  extern __shared__ __align__(1024) unsigned char tcs_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t slot;
+  __shared__ int ip[T];
+  TcCtx c;
+  tc_setup(c, tcs_raw, &bar, &slot);
+  float2 (*X)[T + 1] = reinterpret_cast<TcSolveSmem*>(c.imgA)->X;
+  const Task t = tasks[blockIdx.x];
+  const FrontDev F = fr[t.f];
+  const float2* L = pool + F.off;
+  float2* z = rpool + F.roff * nrhs;
+  const int64_t ld = F.ld;
+  const int nte = F.ne_pad / T;
+  const int i = t.i, r0 = i * T;
+  const int kmax = i < nte ? i : nte;
+  int32_t* flg = flags + F.tile_off;
+  bool ok = true;
+  for (int k = 0; k < kmax && ok; ++k) {
+    if (!wait_ready(flg + k, epoch, st, t.f, k)) {
+      ok = false;
+      break;
+    }
+    ok = tc_product<true, false>(
+        c, [&](int r, int q) { return L[(int64_t)(r0 + r) * ld + k * T + q]; },
+        [&](int n, int q) { return n < nrhs ? ldcg(z + (int64_t)(k * T + q) * nrhs + n) : make_float2(0.f, 0.f); }, st,
+        t.f, k);
+  }
+  if (threadIdx.x < T) {
+    const bool pv = piv != nullptr && F.piv != 0 && i < nte;
+    const int cc = threadIdx.x;
+    ip[pv ? piv[((int64_t)F.tile_off + i) * T + cc] : cc] = cc;
+  }
+  __syncthreads();
+  // X = P_i (B_i - acc)
+  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+    const int rr = idx / T, col = idx % T;
+    X[ip[rr]][col] = col < nrhs ? ldcg(z + (int64_t)(r0 + rr) * nrhs + col) : make_float2(0.f, 0.f);
+  }
+  __syncthreads();
+  if (ok && c.acc && threadIdx.x < 128)
+    tc::read_tile(c.tmem, [&](int r, int col, float2 v) { X[ip[r]][col] = csub(X[ip[r]][col], v); });
+  __syncthreads();
+  if (ok && i < nte) {
+    // Z_i = Linv_ii X
+    const float2* Li = linv + ((int64_t)F.tile_off + i) * T * T;
+    c.acc = false;
+    ok = tc_product<true, false>(c, [&](int r, int q) { return Li[r * T + q]; },
+                                 [&](int n, int q) { return X[q][n]; }, st, t.f, i);
+    if (ok && threadIdx.x < 128) tc::read_tile(c.tmem, [&](int r, int col, float2 v) { X[r][col] = v; });
+    __syncthreads();
+  }
+  tc_release(c);
+  if (!ok) return;
+  for (int idx = threadIdx.x; idx < T * nrhs; idx += blockDim.x) {
+    const int rr = idx / nrhs, col = idx % nrhs;
+    z[(int64_t)(r0 + rr) * nrhs + col] = X[rr][col];
+  }
+  if (i < nte) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      st_release(flg + i, epoch);
+    }
+  }
+}
+
+// backward: X_j = P_j^T L_jj^{-T} (D_j^{-1} Z_j - L_uj^T X_u - sum_{i>j} L_ij^T X_i)
+__global__ void __launch_bounds__(256, 1) k_backward_tc(const float2* pool, float2* rpool, const FrontDev* fr,
+                                                        const Task* tasks, int nrhs, const int32_t* upd,
+                                                        const int32_t* sep, float2* lam, int64_t ld_lam,
+                                                        int32_t* flags, int epoch, DevStatus* st, const float2* linv,
+                                                        const uint8_t* piv) {
+  extern __shared__ __align__(1024) unsigned char tcs_raw[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t slot;
+  __shared__ float2 dinv[T];
+  __shared__ float2 g1s[T];   // D_j^{-1} with 2x2 blocks: y_c = dinv_c z_c + g1_c z_q
+  __shared__ int qs[T], perm[T];
+  TcCtx c;
+  tc_setup(c, tcs_raw, &bar, &slot);
+  float2 (*X)[T + 1] = reinterpret_cast<TcSolveSmem*>(c.imgA)->X;
+  const Task t = tasks[blockIdx.x];
+  const FrontDev F = fr[t.f];
+  const float2* L = pool + F.off;
+  float2* z = rpool + F.roff * nrhs;
+  const int64_t ld = F.ld;
+  const int nte = F.ne_pad / T;
+  const int j = t.i, c0 = j * T;
+  int32_t* flg = flags + F.tile_off;
+  const bool pv = piv != nullptr && F.piv != 0;
+  if (threadIdx.x < T) {
+    if (pv) {
+      float2 g0, g1;
+      int q;
+      dinv_col(L + (int64_t)c0 * ld + c0, ld, threadIdx.x, g0, g1, q);
+      dinv[threadIdx.x] = g0;
+      g1s[threadIdx.x] = g1;
+      qs[threadIdx.x] = q;
+      perm[threadIdx.x] = piv[((int64_t)F.tile_off + j) * T + threadIdx.x];
+    } else {
+      dinv[threadIdx.x] = cdiv(make_float2(1.f, 0.f), L[(c0 + threadIdx.x) * (ld + 1)]);
+      g1s[threadIdx.x] = make_float2(0.f, 0.f);
+      qs[threadIdx.x] = threadIdx.x;
+      perm[threadIdx.x] = threadIdx.x;
+    }
+  }
+  __syncthreads();
+  bool ok = true;
+  // update rows: acc += L_uj^T X_u with X_u the known ancestor values, 64 rows at a time
+  for (int u0 = 0; u0 < F.nu && ok; u0 += T) {
+    ok = tc_product<false, true>(
+        c,
+        [&](int r, int q) {
+          return u0 + q < F.nu ? L[(int64_t)(F.ne_pad + u0 + q) * ld + c0 + r] : make_float2(0.f, 0.f);
+        },
+        [&](int n, int q) {
+          return (u0 + q < F.nu && n < nrhs) ? lam[upd[F.upd_off + u0 + q] + n * ld_lam] : make_float2(0.f, 0.f);
+        },
+        st, t.f, j);
+  }
+  for (int i = nte - 1; i > j && ok; --i) {
+    if (!wait_ready(flg + i, epoch, st, t.f, i)) {
+      ok = false;
+      break;
+    }
+    ok = tc_product<false, false>(
+        c, [&](int r, int q) { return L[(int64_t)(i * T + q) * ld + c0 + r]; },
+        [&](int n, int q) { return n < nrhs ? ldcg(z + (int64_t)(i * T + q) * nrhs + n) : make_float2(0.f, 0.f); }, st,
+        t.f, i);
+  }
+  // Y = D^{-1} Z_j - acc
+  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
+    const int cc = idx / T, col = idx % T;
+    float2 y = make_float2(0.f, 0.f);
+    if (col < nrhs) {
+      y = cmul(ldcg(z + (int64_t)(c0 + cc) * nrhs + col), dinv[cc]);
+      if (pv) y = cfma(ldcg(z + (int64_t)(c0 + qs[cc]) * nrhs + col), g1s[cc], y);
+    }
+    X[cc][col] = y;
+  }
+  __syncthreads();
+  if (ok && c.acc && threadIdx.x < 128)
+    tc::read_tile(c.tmem, [&](int r, int col, float2 v) { X[r][col] = csub(X[r][col], v); });
+  __syncthreads();
+  if (ok) {
+    // X_j = Linv^T Y: out[cc][col] = sum_r Linv[r][cc] Y[r][col]
+    const float2* Li = linv + ((int64_t)F.tile_off + j) * T * T;
+    c.acc = false;
+    ok = tc_product<false, false>(c, [&](int r, int q) { return Li[q * T + r]; },
+                                  [&](int n, int q) { return X[q][n]; }, st, t.f, j);
+    if (ok && threadIdx.x < 128) tc::read_tile(c.tmem, [&](int r, int col, float2 v) { X[r][col] = v; });
+    __syncthreads();
+  }
+  tc_release(c);
+  if (!ok) return;
+  for (int idx = threadIdx.x; idx < T * nrhs; idx += blockDim.x) {
+    const int cc = idx / nrhs, col = idx % nrhs;
+    const float2 v = X[cc][col];
+    const int r = c0 + perm[cc];   // X_j = P_j^T (L_jj^{-T} Y)
+    z[(int64_t)r * nrhs + col] = v;
+    if (F.kind != 0 && r < F.ne) lam[sep[F.sep_off + r] + col * ld_lam] = v;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -708,9 +978,19 @@ __global__ void k_wait_probe(const int32_t* flag, DevStatus* st) { wait_ready(fl
 
 template <typename S>
 __global__ void k_leaf_out(const S* rpool, const FrontDev* fr, const LeafDev* lv, const int32_t* perm, double2* u,
-                           int64_t ldu, int nrhs, int accumulate) {
+                           int64_t ldu, int nrhs, int accumulate, const S* lam, int64_t ld_lam, int n_dual) {
   const LeafDev L = lv[blockIdx.x];
   const FrontDev F = fr[L.front];
+  if (F.kind == 2) {
+    // a sparse domain: the backward substitution left u_i in the row-id vector
+    for (int64_t e = threadIdx.x; e < (int64_t)L.n * nrhs; e += blockDim.x) {
+      const int r = (int)(e % L.n), j = (int)(e / L.n);
+      double2* p = u + L.vec_off + r + j * ldu;
+      const double2 v = cconv<double2>(lam[n_dual + L.vec_off + r + j * ld_lam]);
+      *p = accumulate ? cadd(*p, v) : v;
+    }
+    return;
+  }
   const S* z = rpool + F.roff * nrhs;
   const int32_t* pm = perm + L.perm_off;
   for (int64_t e = threadIdx.x; e < (int64_t)L.n * nrhs; e += blockDim.x) {
@@ -813,10 +1093,13 @@ void launch_rhs_leaf(int prec, void* rpool, const FrontDev* fronts, const LeafDe
 }
 
 void launch_rhs_node(int prec, void* rpool, const FrontDev* fronts, const int32_t* ids, int n, const int32_t* sep,
-                     const double2* g, int64_t ldg, int nrhs, cudaStream_t s) {
+                     const double2* g, int64_t ldg, const double2* f, int64_t ldf, int n_dual, int nrhs,
+                     cudaStream_t s) {
   if (n <= 0) return;
-  if (prec == 0) k_rhs_node<double2><<<n, 256, 0, s>>>((double2*)rpool, fronts, ids, sep, g, ldg, nrhs);
-  else k_rhs_node<float2><<<n, 256, 0, s>>>((float2*)rpool, fronts, ids, sep, g, ldg, nrhs);
+  if (prec == 0)
+    k_rhs_node<double2><<<n, 256, 0, s>>>((double2*)rpool, fronts, ids, sep, g, ldg, f, ldf, n_dual, nrhs);
+  else
+    k_rhs_node<float2><<<n, 256, 0, s>>>((float2*)rpool, fronts, ids, sep, g, ldg, f, ldf, n_dual, nrhs);
 }
 
 void launch_rhs_extend_add(int prec, void* rpool, const FrontDev* fronts, const int32_t* ids, int n, int slot,
@@ -839,8 +1122,18 @@ bool fits_one_wave(K kernel, int n) {
 
 void launch_forward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const Task* tasks, int n,
                     int nrhs, int32_t* flags, int epoch, DevStatus* st, cudaStream_t s, const void* linv,
-                    const uint8_t* piv) {
+                    const uint8_t* piv, int tensor) {
   if (n <= 0) return;
+  if (prec == 1 && linv != nullptr && nrhs >= 4 && nrhs <= T && tensor) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSolveSmem);
+      attr = true;
+    }
+    k_forward_tc<<<n, 256, kTcSolveSmem, s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs, flags, epoch,
+                                              st, (const float2*)linv, piv);
+    return;
+  }
   if (prec == 1 && linv != nullptr && nrhs >= 4 && nrhs <= T) {
     static bool attr = false;
     if (!attr) {
@@ -862,8 +1155,18 @@ void launch_forward(int prec, const void* pool, void* rpool, const FrontDev* fro
 int launch_backward(int prec, const void* pool, void* rpool, const FrontDev* fronts, const Task* tasks, int n,
                     int nrhs, const int32_t* upd, const int32_t* sep, void* lam_work, int64_t ld_lam,
                     int32_t* flags, int epoch, DevStatus* st, cudaStream_t s, const void* linv,
-                    const uint8_t* piv, void* upart, int nsplit) {
+                    const uint8_t* piv, void* upart, int nsplit, int tensor) {
   if (n <= 0) return 0;
+  if (prec == 1 && linv != nullptr && nrhs >= 4 && nrhs <= T && tensor) {
+    static bool attr = false;
+    if (!attr) {
+      cudaFuncSetAttribute(k_backward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSolveSmem);
+      attr = true;
+    }
+    k_backward_tc<<<n, 256, kTcSolveSmem, s>>>((const float2*)pool, (float2*)rpool, fronts, tasks, nrhs, upd, sep,
+                                               (float2*)lam_work, ld_lam, flags, epoch, st, (const float2*)linv, piv);
+    return 1;
+  }
   if (prec == 1 && linv != nullptr && nrhs >= 4 && nrhs <= T) {
     static bool attr = false;
     if (!attr) {
@@ -913,12 +1216,15 @@ int launch_backward(int prec, const void* pool, void* rpool, const FrontDev* fro
 }
 
 void launch_leaf_out(int prec, const void* rpool, const FrontDev* fronts, const LeafDev* leaves, int n_leaves,
-                     const int32_t* perm, double2* u, int64_t ldu, int nrhs, int accumulate, cudaStream_t s) {
+                     const int32_t* perm, double2* u, int64_t ldu, int nrhs, int accumulate, cudaStream_t s,
+                     const void* lam, int64_t ld_lam, int n_dual) {
   if (n_leaves <= 0) return;
   if (prec == 0)
-    k_leaf_out<double2><<<n_leaves, 256, 0, s>>>((const double2*)rpool, fronts, leaves, perm, u, ldu, nrhs, accumulate);
+    k_leaf_out<double2><<<n_leaves, 256, 0, s>>>((const double2*)rpool, fronts, leaves, perm, u, ldu, nrhs, accumulate,
+                                                 (const double2*)lam, ld_lam, n_dual);
   else
-    k_leaf_out<float2><<<n_leaves, 256, 0, s>>>((const float2*)rpool, fronts, leaves, perm, u, ldu, nrhs, accumulate);
+    k_leaf_out<float2><<<n_leaves, 256, 0, s>>>((const float2*)rpool, fronts, leaves, perm, u, ldu, nrhs, accumulate,
+                                                (const float2*)lam, ld_lam, n_dual);
 }
 
 void launch_lam_out(int prec, const void* lam_work, int64_t ld_work, int n_dual, int nrhs, double2* lam, int64_t ldl,

@@ -13,10 +13,9 @@
 //     forms Re = Re L Re W - Im L Im W, Im = Re L Im W + Im L Re W with
 //     lane shuffles;
 //   * 3xTF32 split for FP32-class accuracy: X Y^T ~ Xh Yh^T + Xh Yl^T + Xl Yh^T;
-//   * operands are the pre-split, 64B-swizzled K-major images written by the
+//   * operands are the pre-split, 128B-swizzled K-major images written by the
 //     panel kernel, streamed into shared memory by bulk asynchronous copies
-//     (TMA engine) completing on mbarriers, one 48 KB stage per 16-wide K atom,
-//     four stages in flight;
+//     (TMA engine) completing on mbarriers, one 96 KB stage per 32-wide K atom;
 //     the accumulator lives in TMEM (two of 128 lanes x 256 fp32 columns).
 // C is read and written once per task, so pairing two panels per task halves
 // the trailing-matrix traffic.  Every wait is bounded: on timeout the CTA
@@ -33,14 +32,14 @@ constexpr int kWaitPolls = 1 << 24;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// shared-memory matrix descriptor: K-major, 64B swizzle, 8-row groups 512 B apart
-__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
+// shared-memory matrix descriptor: K-major, 128B swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
   d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(512 >> 4) << 32;   // stride byte offset
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
   d |= (uint64_t)1 << 46;            // descriptor version
-  d |= (uint64_t)4 << 61;            // 64B swizzle
+  d |= (uint64_t)2 << 61;            // 128B swizzle
   return d;
 }
 
@@ -76,15 +75,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t ta, uint32_t (&r)[32]) {
 
 // Persistent, warp-specialised: warp 0 lane 0 claims task groups (runs of <= 8
 // tasks of one row tile, in list order, through an atomic counter) and streams
-// the operand pieces of each task through a four-stage ring; warp 1 lane 0
+// the operand pieces of each task through a two-stage ring; warp 1 lane 0
 // issues the MMAs into one of two TMEM accumulators; warps 2-5 drain the other
 // accumulator into C.  Task .pad: bit 0 / 1 store column tile j / j + 1 (with
 // bit 1 clear the MMAs use N = 128 and only tile j's operand is loaded),
 // bit 2 / 3 panel k / k + 1 contributes.
-constexpr int kStageA = 2 * DD_TC_ATOM;          // hi, lo pieces of the row tile: 16 KB
-constexpr int kStageB = 2 * 2 * DD_TC_ATOM;      // hi, lo x two column tiles: 32 KB
-constexpr int kStage = kStageA + kStageB;        // 48 KB per K atom
-constexpr int kStages = 4;
+constexpr int kStageA = 2 * DD_TC_ATOM;          // hi, lo pieces of the row tile: 32 KB
+constexpr int kStageB = 2 * 2 * DD_TC_ATOM;      // hi, lo x two column tiles: 64 KB
+constexpr int kStage = kStageA + kStageB;        // 96 KB per K atom
+constexpr int kStages = 2;
 constexpr int kStg = 16 * 33;                    // per epilogue warp: 16 rows x 32 complex, padded
 constexpr int kSmemP = kStages * kStage + 4 * kStg * 8 + 1024;
 constexpr int kAccCols = 256;                    // fp32 columns per accumulator; two accumulators
@@ -268,18 +267,18 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
           const unsigned char* w = pp ? ws1 : ws0;
           const unsigned char* gA = w + F.ws_off + (int64_t)(t.i - p - 1) * DD_TC_ATILE;
           const unsigned char* gB = w + F.ws_boff + (int64_t)(t.j - p - 1) * DD_TC_BTILE;
-          for (int a = 0; a < DD_TC_NATOM; ++a, ++u) {
+          for (int a = 0; a < 2; ++a, ++u) {
             const int sidx = u % kStages;
             if (!mbar_wait(b_empty0 + 8 * sidx, ((u / kStages) & 1) ^ 1)) { fail = 1; break; }
             const uint32_t fb = b_full0 + 8 * sidx;
             unsigned char* stg = smem + sidx * kStage;
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(bytes) : "memory");
             for (int sp = 0; sp < 2; ++sp)
-              bulk_g2s(smem_u32(stg + sp * DD_TC_ATOM), gA + (sp * DD_TC_NATOM + a) * DD_TC_ATOM, DD_TC_ATOM, fb);
+              bulk_g2s(smem_u32(stg + sp * DD_TC_ATOM), gA + (sp * 2 + a) * DD_TC_ATOM, DD_TC_ATOM, fb);
             for (int sp = 0; sp < 2; ++sp)
               for (int c = 0; c < ncol; ++c)
                 bulk_g2s(smem_u32(stg + kStageA + sp * 2 * DD_TC_ATOM + c * DD_TC_ATOM),
-                         gB + (int64_t)c * DD_TC_BTILE + (sp * DD_TC_NATOM + a) * DD_TC_ATOM, DD_TC_ATOM, fb);
+                         gB + (int64_t)c * DD_TC_BTILE + (sp * 2 + a) * DD_TC_ATOM, DD_TC_ATOM, fb);
           }
         }
       }
@@ -304,18 +303,18 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
         uint32_t acc_on = 0;
         for (int pp = 0; pp < 2 && !fail; ++pp) {
           if (!(t.pad & (4 << pp))) continue;
-          for (int a = 0; a < DD_TC_NATOM; ++a, ++u) {
+          for (int a = 0; a < 2; ++a, ++u) {
             const int sidx = u % kStages;
             if (!mbar_wait(b_full0 + 8 * sidx, (u / kStages) & 1)) { fail = 1; break; }
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t a0 = s0 + sidx * kStage, b0 = a0 + kStageA;
 #pragma unroll
-            for (int s8 = 0; s8 < DD_TC_KATOM / 8; ++s8)   // K = 8 per MMA: 32 B into the 64 B rows
+            for (int s4 = 0; s4 < 4; ++s4)
 #pragma unroll
               for (int sp = 0; sp < 3; ++sp) {   // split pairs (hi, hi), (hi, lo), (lo, hi)
                 const int as = sp == 2 ? 1 : 0, bs = sp == 1 ? 1 : 0;
-                const uint64_t ad = desc_sw64(a0 + as * DD_TC_ATOM + s8 * 32);
-                const uint64_t bd = desc_sw64(b0 + bs * 2 * DD_TC_ATOM + s8 * 32);
+                const uint64_t ad = desc_sw128(a0 + as * DD_TC_ATOM + s4 * 32);
+                const uint64_t bd = desc_sw128(b0 + bs * 2 * DD_TC_ATOM + s4 * 32);
                 asm volatile(
                     "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                     " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dacc),
