@@ -99,43 +99,47 @@ __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
   lo = __uint_as_float(l);
 }
 
-// Operand image of a 64 x 64 complex tile (K = 64): pieces of 128 rows x 32 K
-// (16 KB), piece (split s, atom a) at (s * 2 + a) * 16 KB; 64 KB in all.
+// Operand image of 64 complex rows and NA atoms of 32 K (K = 32 NA): pieces of
+// 128 rows x 32 K (16 KB), piece (split s, atom a) at (s NA + a) 16 KB.
 constexpr int kAtom = 16384;
-constexpr int kImage = 4 * kAtom;
+constexpr int kImage = 4 * kAtom;   // NA = 2: the full K = 64 of a tile
+template <int NA>
 __device__ __forceinline__ void put_split(unsigned char* img, int row, int k, float v) {
   float h, l;
   split_tf32(v, h, l);
   const int a = k >> 5, kk = k & 31;
-  *reinterpret_cast<float*>(img + (0 * 2 + a) * kAtom + swz128(row, kk)) = h;
-  *reinterpret_cast<float*>(img + (1 * 2 + a) * kAtom + swz128(row, kk)) = l;
+  *reinterpret_cast<float*>(img + (0 * NA + a) * kAtom + swz128(row, kk)) = h;
+  *reinterpret_cast<float*>(img + (1 * NA + a) * kAtom + swz128(row, kk)) = l;
 }
 // A operand: complex row r (0..63), K index k
+template <int NA = 2>
 __device__ __forceinline__ void put_a(unsigned char* img, int r, int k, float2 v) {
   const int ra = (r >> 4) * 32 + (r & 15);
-  put_split(img, ra, k, v.x);
-  put_split(img, ra + 16, k, v.y);
+  put_split<NA>(img, ra, k, v.x);
+  put_split<NA>(img, ra + 16, k, v.y);
 }
 // B operand: complex row n (0..63), K index k
+template <int NA = 2>
 __device__ __forceinline__ void put_b(unsigned char* img, int n, int k, float2 v) {
-  put_split(img, n, k, v.x);
-  put_split(img, n + 64, k, v.y);
+  put_split<NA>(img, n, k, v.x);
+  put_split<NA>(img, n + 64, k, v.y);
 }
 
-// Issues acc (+)= A B^T for two 64 KB images (M = 128, N = 128, K = 64 tf32,
-// 3xTF32: 24 MMAs) from one thread.
+// Issues acc (+)= A B^T for two images of NA atoms (M = 128, N = 128,
+// K = 32 NA tf32, 3xTF32: 12 NA MMAs) from one thread.
+template <int NA = 2>
 __device__ __forceinline__ void mma_tile(uint32_t dacc, uint32_t sA, uint32_t sB, bool accumulate) {
   constexpr uint32_t idesc = idesc_tf32(128);
   uint32_t on = accumulate ? 1u : 0u;
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
+  for (int a = 0; a < NA; ++a)
 #pragma unroll
     for (int s4 = 0; s4 < 4; ++s4)
 #pragma unroll
       for (int sp = 0; sp < 3; ++sp) {   // split pairs (hi, hi), (hi, lo), (lo, hi)
         const int as = sp == 2 ? 1 : 0, bs = sp == 1 ? 1 : 0;
-        mma_tf32(dacc, desc_sw128(sA + (as * 2 + a) * kAtom + s4 * 32), desc_sw128(sB + (bs * 2 + a) * kAtom + s4 * 32),
-                 idesc, on);
+        mma_tf32(dacc, desc_sw128(sA + (as * NA + a) * kAtom + s4 * 32),
+                 desc_sw128(sB + (bs * NA + a) * kAtom + s4 * 32), idesc, on);
         on = 1;
       }
 }

@@ -628,19 +628,20 @@ __global__ void __launch_bounds__(256) k_trsm_mx(float2* pool, const FrontDev* f
   if ((threadIdx.x & 31) == 0 && mx > 0.f && isfinite(mx)) atomic_max_pos(&st->max_abs_l, sqrt((double)mx));
 }
 
-// mixed form panel on the tensor cores: X = A_ik P_k^T L_kk^{-T} as one 3xTF32
+// mixed form panel on the tensor cores: X = A_ik P_k^T L_kk^{-T} as a 3xTF32
 // tcgen05 product with the stored inverse (M = 128: real and imaginary rows
-// of A_ik, N = 128: real and imaginary rows of L_kk^{-1}, K = 64), the
-// accumulator in TMEM; then L_ik = X D_k^{-1} and the operand images of the
-// trailing update, as k_trsm_mx.  256 threads; warps 0-3 drain TMEM.
-constexpr int kTrsmTcSmem = 2 * tc::kImage + 1024;   // A and B images (later X), 1024-aligned
+// of A_ik, N = 128: real and imaginary rows of L_kk^{-1}, K = 64 in two
+// halves of 32, so that the 64 KB of operand images let three CTAs share an
+// SM), the accumulator in TMEM; then L_ik = X D_k^{-1} and the operand
+// images of the trailing update, as k_trsm_mx.  256 threads; warps 0-3 drain TMEM.
+constexpr int kTrsmTcSmem = tc::kImage + 1024;   // A and B images of one K half (later X), 1024-aligned
 __global__ void __launch_bounds__(256, 1) k_trsm_tc(float2* pool, const FrontDev* fr, const Task* tasks, int k,
                                                     DevStatus* st, const float2* linv, unsigned char* ws,
                                                     const uint8_t* piv) {
   extern __shared__ __align__(1024) unsigned char tc_raw[];
   unsigned char* smem = tc_raw + ((1024u - (tc::smem_u32(tc_raw) & 1023u)) & 1023u);
   unsigned char* imgA = smem;
-  unsigned char* imgB = smem + tc::kImage;
+  unsigned char* imgB = smem + tc::kImage / 2;
   float2 (*Xs)[T + 1] = reinterpret_cast<float2 (*)[T + 1]>(smem);   // after the product
   __shared__ float2 rinv[T];
   __shared__ float2 g1[T];
@@ -683,24 +684,29 @@ __global__ void __launch_bounds__(256, 1) k_trsm_tc(float2* pool, const FrontDev
     }
   }
   __syncthreads();
-  // operand images: A = A_ik P_k^T (rows r, K index q), B = L_kk^{-1} (rows p, K index q)
-  for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
-    const int r = idx / T, q = idx % T;
-    tc::put_a(imgA, r, q, Aik[(int64_t)r * ld + perm[q]]);
-    tc::put_b(imgB, r, q, Li[idx]);
-  }
-  asm volatile("fence.proxy.async.shared::cta;");
-  asm volatile("tcgen05.fence::before_thread_sync;");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
-  if (threadIdx.x == 0) {
-    tc::mma_tile(tmem, tc::smem_u32(imgA), tc::smem_u32(imgB), false);
-    tc::mma_commit(b);
+  // operand images of K half h: A = A_ik P_k^T (rows r, K index q), B = L_kk^{-1} (rows p, K index q)
+  if (threadIdx.x == 0) ok_s = 1;
+  for (int h = 0; h < 2; ++h) {
+    for (int idx = threadIdx.x; idx < T * (T / 2); idx += blockDim.x) {
+      const int r = idx / (T / 2), q = idx % (T / 2);
+      tc::put_a<1>(imgA, r, q, Aik[(int64_t)r * ld + perm[h * 32 + q]]);
+      tc::put_b<1>(imgB, r, q, Li[r * T + h * 32 + q]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (threadIdx.x == 0) {
+      if (ok_s) {
+        tc::mma_tile<1>(tmem, tc::smem_u32(imgA), tc::smem_u32(imgB), h > 0);
+        tc::mma_commit(b);
+        ok_s = tc::mbar_wait(b, h) ? 1 : 0;
+      }
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
   }
-  if (threadIdx.x == 0) ok_s = tc::mbar_wait(b, 0) ? 1 : 0;
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
   const bool ok = ok_s != 0;
   if (ok && warp < 4) tc::read_tile(tmem, [&](int r, int c, float2 v) { Xs[r][c] = v; });
   asm volatile("tcgen05.fence::before_thread_sync;");
