@@ -1020,28 +1020,6 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
   // kGroupCap long, claimed one at a time by the persistent update kernel (consecutive
   // groups in flight share their column tiles' operand images through L2)
   constexpr int kGroupCap = 8;
-  // Row-pair tensor-core tasks of front f over the row tiles [r0, r1) and the
-  // column segments cb[0..ncb) (tiles of one segment share their zero
-  // panels): row tiles (i, i + 1), column tiles (j, j + 1), panel bits pm;
-  // .pad bit 4 marks the second row tile, bits 6..9 the stored lower-triangle
-  // tiles (i, j), (i, j + 1), (i + 1, j), (i + 1, j + 1).
-  auto tc_pairs = [&](int f, int r0, int r1, const int* cb, int ncb, int pm, std::vector<Task>& out) {
-    for (int i = r0; i < r1; i += 2) {
-      const bool two_r = i + 1 < r1;
-      const int rmax = two_r ? i + 1 : i;
-      for (int sg = 0; sg + 1 < ncb; ++sg)
-        for (int j = cb[sg]; j < cb[sg + 1] && j <= rmax; j += 2) {
-          const bool two_c = j + 1 < cb[sg + 1] && j + 1 <= rmax;
-          int mask = 0;
-          if (j <= i) mask |= 1 << 6;
-          if (two_c && j + 1 <= i) mask |= 1 << 7;
-          if (two_r && j <= i + 1) mask |= 1 << 8;
-          if (two_r && two_c && j + 1 <= i + 1) mask |= 1 << 9;
-          if (!mask) continue;
-          out.push_back(Task{f, i, j, 1 | (two_c ? 2 : 0) | (two_r ? 16 : 0) | pm | mask});
-        }
-    }
-  };
   auto add_groups = [&](const std::vector<Task>& tl, int64_t first, int64_t count) -> int {
     int ng = 0;
     for (int64_t q = first; q < first + count;) {
@@ -1102,25 +1080,21 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
           trsm_flops += 8.0 * r * w * (w - 1) / 2.0;
           upd_flops += 8.0 * w * r * (r + 1) / 2.0;
         }
-        // tensor-core tasks: row tiles (i, i + 1) x column tiles (j, j + 1);
-        // neither pair straddles the first update-row tile, so all tiles of a
-        // task share their structurally zero panels
-        if (h->use_tc && !zero_tile(k + 1)) {
-          const int cn[2] = {k + 1, k + 2};
-          const int rs[3] = {k + 1, std::max(nte, k + 1), nt};
-          for (int sg = 0; sg < 2; ++sg)
-            if (rs[sg] < rs[sg + 1] && !zero_tile(rs[sg])) tc_pairs(f, rs[sg], rs[sg + 1], cn, 2, 4, tc_next);
-        }
+        // tensor-core tasks: row tile i x column tiles (j, j + 1); column pairs
+        // never straddle the first update-row tile, so both columns of a task
+        // share their structurally zero panels
         if (h->use_tc) {
-          const int cb[3] = {k + 2, std::max(nte, k + 2), nt};
-          const int rs[3] = {k + 2, std::max(nte, k + 2), nt};
-          for (int sg = 0; sg < 2; ++sg) {
-            if (rs[sg] >= rs[sg + 1] || zero_tile(rs[sg])) continue;
-            for (int cg = 0; cg < 2; ++cg) {
-              if (cb[cg] >= cb[cg + 1] || zero_tile(cb[cg])) continue;
-              const int cc[2] = {cb[cg], cb[cg + 1]};
-              tc_pairs(f, rs[sg], rs[sg + 1], cc, 2, 4, tc_rest);
-            }
+          for (int i = k + 1; i < nt; ++i)
+            if (!zero_tile(i) && !zero_tile(k + 1)) tc_next.push_back(Task{f, i, k + 1, 1 | 4});
+          const int sb[3] = {k + 2, std::max(nte, k + 2), nt};
+          for (int i = k + 2; i < nt; ++i) {
+            if (zero_tile(i)) continue;
+            for (int sg = 0; sg < 2; ++sg)
+              for (int j = sb[sg]; j < sb[sg + 1] && j <= i; j += 2) {
+                if (zero_tile(j)) continue;
+                const int two = (j + 1 < sb[sg + 1] && j + 1 <= i) ? 2 : 0;
+                tc_rest.push_back(Task{f, i, j, 1 | two | 4});
+              }
           }
         }
       }
@@ -1157,20 +1131,16 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
           const int np = (k + 1 < nte) ? 2 : 1;
           auto zero = [&](int p, int i) { return F.kind == 0 && i >= nte && (p + 1) * T <= F.n_int; };
           const int sb[3] = {k + 2, std::max(nte, k + 2), nt};
-          std::vector<Task> all;
-          for (int sg = 0; sg < 2; ++sg)
-            for (int cg = 0; cg < 2; ++cg) {
-              if (sb[sg] >= sb[sg + 1] || sb[cg] >= sb[cg + 1]) continue;
-              int pm = 0;
-              for (int pp = 0; pp < np; ++pp)
-                if (!zero(k + pp, sb[sg]) && !zero(k + pp, sb[cg])) pm |= 4 << pp;
-              if (!pm) continue;
-              const int cc[2] = {sb[cg], sb[cg + 1]};
-              tc_pairs(f, sb[sg], sb[sg + 1], cc, 2, pm, all);
-            }
-          // group the tasks of one row pair together, columns in order
-          std::stable_sort(all.begin(), all.end(), [](const Task& a, const Task& b) { return a.i < b.i; });
-          for (const Task& t : all) (t.j <= k + 3 ? near : far).push_back(t);
+          for (int i = k + 2; i < nt; ++i)
+            for (int sg = 0; sg < 2; ++sg)
+              for (int j = sb[sg]; j < sb[sg + 1] && j <= i; j += 2) {
+                int pm = 0;
+                for (int pp = 0; pp < np; ++pp)
+                  if (!zero(k + pp, i) && !zero(k + pp, j)) pm |= 4 << pp;
+                if (!pm) continue;
+                const int two = (j + 1 < sb[sg + 1] && j + 1 <= i) ? 2 : 0;
+                (j <= k + 3 ? near : far).push_back(Task{f, i, j, 1 | two | pm});
+              }
         }
         P.n_near = (int)near.size();
         P.n_far = (int)far.size();

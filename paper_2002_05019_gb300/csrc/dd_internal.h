@@ -44,19 +44,16 @@ struct FrontDev {
 };
 
 // Panel operand images for the tensor-core trailing update (mixed form), one
-// per trailing 64-row tile t of a panel step, 64B-swizzled K-major, in pieces
-// of 128 rows x one K atom (16 tf32, 64 B a row) = 8 KB, indexed (split
-// hi/lo, atom 0..3):
+// per trailing 64-row tile t of a panel step, 128B-swizzled K-major, in pieces
+// of 128 rows x one K atom (32 tf32) = 16 KB, indexed (split hi/lo, atom):
 //   A image (rows of L): within a piece, for each group of 16 tile rows, their
 //     real parts then their imaginary parts (piece row 32 (r / 16) + r % 16 and
 //     + 16), so the two parts of a row land in one TMEM sub-partition;
 //   B image (rows of W = L D): within a piece, the 64 real rows then the 64
 //     imaginary rows.
-#define DD_TC_KATOM 16
-#define DD_TC_NATOM (DD_TILE / DD_TC_KATOM)
-#define DD_TC_ATOM 8192
-#define DD_TC_ATILE (2 * DD_TC_NATOM * DD_TC_ATOM)
-#define DD_TC_BTILE (2 * DD_TC_NATOM * DD_TC_ATOM)
+#define DD_TC_ATOM 16384
+#define DD_TC_ATILE (2 * 2 * DD_TC_ATOM)
+#define DD_TC_BTILE (2 * 2 * DD_TC_ATOM)
 
 struct LeafDev {
   int64_t csr_off;   // offset of the domain's nonzeros in the concatenated CSR arrays

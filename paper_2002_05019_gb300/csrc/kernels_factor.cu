@@ -23,14 +23,9 @@ constexpr int T = DD_TILE;
 __device__ __forceinline__ int tri(int i, int c) { return (i * (i + 1)) / 2 + c; }
 
 using tc::split_tf32;
-// byte offset of element (row, k), k in 0..15, in a 64B-swizzled K-major atom
-// (8-row groups of 512 B; the 16-byte chunk index is XORed with address bits
-// 7-8, i.e. with (row / 2) % 4)
-__device__ __forceinline__ int swz64(int row, int k) {
-  return (row >> 3) * 512 + (row & 7) * 64 + ((((k >> 2) ^ ((row >> 1) & 3))) << 4) + (k & 3) * 4;
-}
+using tc::swz128;
 __device__ __forceinline__ void put_img(unsigned char* base, int row, int k, float v) {
-  *reinterpret_cast<float*>(base + swz64(row, k)) = v;
+  *reinterpret_cast<float*>(base + swz128(row, k)) = v;
 }
 
 template <typename S>
@@ -40,23 +35,23 @@ template <>
 __device__ __forceinline__ void write_images<float2>(unsigned char* ws, const FrontDev& F, int ti, int rc, float2 L,
                                                      float2 W) {
   const int r = rc >> 6, p = rc & 63;              // row of the tile, K index
-  const int a = p / DD_TC_KATOM, kk = p % DD_TC_KATOM;
+  const int a = p >> 5, kk = p & 31;
   const int ra = (r >> 4) * 32 + (r & 15);         // A piece row of the real part (imaginary: + 16)
   unsigned char* Ab = ws + F.ws_off + (int64_t)ti * DD_TC_ATILE;
   unsigned char* Bb = ws + F.ws_boff + (int64_t)ti * DD_TC_BTILE;
   float h, l;
   split_tf32(L.x, h, l);
-  put_img(Ab + (0 * DD_TC_NATOM + a) * DD_TC_ATOM, ra, kk, h);
-  put_img(Ab + (1 * DD_TC_NATOM + a) * DD_TC_ATOM, ra, kk, l);
+  put_img(Ab + (0 * 2 + a) * DD_TC_ATOM, ra, kk, h);
+  put_img(Ab + (1 * 2 + a) * DD_TC_ATOM, ra, kk, l);
   split_tf32(L.y, h, l);
-  put_img(Ab + (0 * DD_TC_NATOM + a) * DD_TC_ATOM, ra + 16, kk, h);
-  put_img(Ab + (1 * DD_TC_NATOM + a) * DD_TC_ATOM, ra + 16, kk, l);
+  put_img(Ab + (0 * 2 + a) * DD_TC_ATOM, ra + 16, kk, h);
+  put_img(Ab + (1 * 2 + a) * DD_TC_ATOM, ra + 16, kk, l);
   split_tf32(W.x, h, l);
-  put_img(Bb + (0 * DD_TC_NATOM + a) * DD_TC_ATOM, r, kk, h);
-  put_img(Bb + (1 * DD_TC_NATOM + a) * DD_TC_ATOM, r, kk, l);
+  put_img(Bb + (0 * 2 + a) * DD_TC_ATOM, r, kk, h);
+  put_img(Bb + (1 * 2 + a) * DD_TC_ATOM, r, kk, l);
   split_tf32(W.y, h, l);
-  put_img(Bb + (0 * DD_TC_NATOM + a) * DD_TC_ATOM, r + 64, kk, h);
-  put_img(Bb + (1 * DD_TC_NATOM + a) * DD_TC_ATOM, r + 64, kk, l);
+  put_img(Bb + (0 * 2 + a) * DD_TC_ATOM, r + 64, kk, h);
+  put_img(Bb + (1 * 2 + a) * DD_TC_ATOM, r + 64, kk, l);
 }
 
 __device__ void status_pivot(DevStatus* st, int front, int row) {
