@@ -558,7 +558,7 @@ def main():
     ap.add_argument("--ref-threads", type=int, default=0, help="reference arm: host threads (0: all)")
     ap.add_argument("--pivoting", type=int, default=0, choices=[0, 1, 2],
                     help="restricted Bunch-Kaufman: 0 none, 1 auxiliary fronts, 2 every front")
-    ap.add_argument("--update-panels", type=int, default=2, choices=[1, 2],
+    ap.add_argument("--update-panels", type=int, default=2, choices=[1, 2, 4],
                     help="mixed form: panels fused per tensor-core trailing-update pass")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default factor schedule")
     ap.add_argument("--kernel-timing", default="update", choices=["update", "all", "none"],

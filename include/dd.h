@@ -109,8 +109,10 @@ typedef struct {
   int32_t simt_update;      /* MIXED: 1 runs the trailing updates on the FP32 FMA pipes instead of
                                the tensor cores (comparison baseline; default 0) */
   int32_t update_panels;    /* MIXED, tensor cores: panels fused per trailing-update pass, 1 (C read
-                               and written after every 64-wide panel) or 2 (after every pair of
-                               panels, K = 128; default); other values: DD_ERR_INVALID_ARG */
+                               and written after every 64-wide panel), 2 (after every pair of
+                               panels, K = 128; default) or 4 (after every four panels, K = 256,
+                               on tree levels without look-ahead; the others use pairs); other
+                               values: DD_ERR_INVALID_ARG */
   int32_t sparse_min;       /* Section II factors each domain with a sparse direct solver: domains of
                                at least sparse_min unknowns are split into a tree of fronts by nested
                                dissection of their matrix graph (interface unknowns last, in the
@@ -150,7 +152,7 @@ typedef struct {
 
 /* Schedule of the tensor-core factorization path (MIXED form). */
 typedef struct {
-  int32_t update_panels;  /* panels fused per trailing-update pass: 1 or 2 */
+  int32_t update_panels;  /* panels fused per trailing-update pass: 1, 2 or 4 */
   int32_t ahead_fronts;   /* one-step look-ahead on tree levels with at most this many fronts (0: none) */
   int32_t reserve_sms;    /* SMs the look-ahead update leaves to the panel chain */
   double factor_ms;       /* dd_autotune: device time of one dd_factor with this schedule */
@@ -176,7 +178,7 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
  * device memory (detected).  The handle becomes unfactored. */
 int dd_set_values(dd_handle* h, const dd_c128* vals);
 
-/* Set the schedule of the tensor-core path (update_panels 1 or 2, ahead_fronts
+/* Set the schedule of the tensor-core path (update_panels 1, 2 or 4, ahead_fronts
  * in [0, 1024], reserve_sms in [0, 64]); factor_ms and configs_tried are ignored.
  * The factors already computed stay valid; the next dd_factor uses the new
  * schedule.  No effect in the FP64 form or with simt_update.
@@ -184,7 +186,7 @@ int dd_set_values(dd_handle* h, const dd_c128* vals);
 int dd_set_schedule(dd_handle* h, const dd_schedule* sched);
 
 /* Autotuner: times dd_factor (the minimum over `repeats` runs each) under every
- * schedule of the grid update_panels {1, 2} x ahead_fronts {0, 8, 32, 128, 1024} x
+ * schedule of the grid update_panels {1, 2, 4} x ahead_fronts {0, 8, 32, 128, 1024} x
  * reserve_sms {8, 16, 32} (look-ahead off: reserve not varied), keeps the
  * fastest for this handle and returns it in *out; the handle is left factored
  * with it.  FP64 form / simt_update: one dd_factor, configs_tried = 1.

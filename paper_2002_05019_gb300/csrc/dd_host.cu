@@ -66,11 +66,22 @@ struct PairRange {
   int n_grp_near, n_grp_far;
 };
 
+// four-panel updates of steps k .. k + 3 (k = 0, 4, 8, ...): near = columns
+// k + 2, k + 3 with panels k, k + 1; far = columns >= k + 4 with all four
+struct QuadRange {
+  int k;
+  int64_t tc_off;
+  int n_near, n_far;
+  int64_t grp_off;
+  int n_grp_near, n_grp_far;
+};
+
 struct Level {
   std::vector<int32_t> ids;       // fronts in this level
   int64_t ids_off = 0;            // offset into d_level_ids
   std::vector<StepRange> steps;   // factor schedule
   std::vector<PairRange> pairs;   // two-panel updates of steps (0, 1), (2, 3), ... (tensor-core path)
+  std::vector<QuadRange> quads;   // four-panel updates of steps (0..3), (4..7), ... (tensor-core path)
   bool ahead = false;             // one-step look-ahead on a second stream
   int max_child_nu = 0;
   int64_t fwd_off = 0, bwd_off = 0;   // solve tasks (forward by row tile, backward by column tile)
@@ -188,6 +199,7 @@ struct dd_handle {
   size_t ws_bytes = 0;
   int use_tc = 0;
   bool pair_panels = false;        // two-panel trailing updates (K = 128)
+  bool quad_panels = false;        // four-panel trailing updates (K = 256) on levels without look-ahead
   // schedule knobs of the tensor-core path (dd_autotune picks them)
   int ahead_fronts = 32;           // look-ahead on levels with at most this many fronts (0: off)
   int reserve_sms = 16;            // SMs the look-ahead leaves to the panel chain
@@ -571,7 +583,7 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
   if (opt.precision != DD_PREC_FP64 && opt.precision != DD_PREC_MIXED) return DD_ERR_INVALID_ARG;
   if (opt.pivoting < 0 || opt.pivoting > 2 || opt.max_refine < 0 || !(opt.refine_tol >= 0))
     return DD_ERR_INVALID_ARG;
-  if (opt.update_panels != 1 && opt.update_panels != 2) return DD_ERR_INVALID_ARG;
+  if (opt.update_panels != 1 && opt.update_panels != 2 && opt.update_panels != 4) return DD_ERR_INVALID_ARG;
   if (opt.sparse_min < 0 || opt.sparse_leaf < 0) return DD_ERR_INVALID_ARG;
   if (opt.device < 0) return DD_ERR_INVALID_ARG;
 
@@ -594,7 +606,8 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
   h->elem = opt.precision == DD_PREC_FP64 ? 16 : 8;
   h->time_kernels = opt.time_kernels == 2 ? 2 : (opt.time_kernels ? 1 : 0);
   h->use_tc = (opt.precision == DD_PREC_MIXED && !opt.simt_update) ? 1 : 0;
-  h->pair_panels = h->use_tc && opt.update_panels == 2;
+  h->pair_panels = h->use_tc && opt.update_panels >= 2;
+  h->quad_panels = h->use_tc && opt.update_panels == 4;
   h->pivoting = opt.pivoting;
   h->max_abs_a = std::max(amax, 1.0);
   cudaStream_t s = h->stream;
@@ -1008,10 +1021,13 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
       need = std::max(need, (size_t)w);
       if (L.ahead) need_ahead = std::max(need_ahead, (size_t)w);
     }
-    h->ws_bytes = 2 * need + 2 * need_ahead;
+    // four-panel passes hold the images of panels k .. k + 3 at once: slots
+    // 2 and 3 are sized for every level then
+    (void)need_ahead;
+    h->ws_bytes = 4 * need;
     h->ws_slot_off[1] = need;
     h->ws_slot_off[2] = 2 * need;
-    h->ws_slot_off[3] = 2 * need + need_ahead;
+    h->ws_slot_off[3] = 3 * need;
   }
   std::vector<int32_t> h_level_ids, h_diag;
   std::vector<Task> h_trsm, h_updt, h_tc, h_tc2;
@@ -1150,6 +1166,60 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
         P.n_grp_near = add_groups(h_tc2, P.tc2_off, P.n_near);
         P.n_grp_far = add_groups(h_tc2, P.tc2_off + P.n_near, P.n_far);
         L.pairs.push_back(P);
+      }
+    // four-panel updates: every column gets each of its panels exactly once
+    // (column k + 1: panel k with step k's first update; columns k + 2, k + 3:
+    // panels k, k + 1 here (near); column k + 3: panel k + 2 with step k + 2's
+    // first update; columns >= k + 4: panels k .. k + 3 here (far))
+    if (h->use_tc)
+      for (int k = 0; k + 3 < max_steps; k += 4) {
+        QuadRange Q{};
+        Q.k = k;
+        Q.tc_off = (int64_t)h_tc2.size();
+        std::vector<Task> near, far;
+        for (int f : L.ids) {
+          const FrontDev& F = h->fronts[f];
+          const int nte = F.ne_pad / T, nt = F.ld / T;
+          if (k >= nte) continue;
+          const int np = std::min(4, nte - k);
+          auto zero = [&](int p, int i) { return F.kind == 0 && i >= nte && (p + 1) * T <= F.n_int; };
+          auto mask = [&](int i, int j, int npp) {
+            int pm = 0;
+            for (int pp = 0; pp < npp; ++pp)
+              if (!zero(k + pp, i) && !zero(k + pp, j)) pm |= 4 << pp;
+            return pm;
+          };
+          for (int i = k + 2; i < nt; ++i) {
+            // near: columns k + 2 and k + 3, one task when both are on the same side of nte
+            const int j0 = k + 2, j1 = k + 3;
+            if (j0 <= i && j0 < nt) {
+              const bool pair = j1 <= i && j1 < nt && ((j0 < nte) == (j1 < nte));
+              const int pm = mask(i, j0, std::min(2, np));
+              if (pm) near.push_back(Task{f, i, j0, 1 | (pair ? 2 : 0) | pm});
+              if (!pair && j1 <= i && j1 < nt) {
+                const int pm1 = mask(i, j1, std::min(2, np));
+                if (pm1) near.push_back(Task{f, i, j1, 1 | pm1});
+              }
+            }
+            // far: columns >= k + 4 in pairs that do not straddle nte
+            const int sb[3] = {k + 4, std::max(nte, k + 4), nt};
+            for (int sg = 0; sg < 2; ++sg)
+              for (int j = sb[sg]; j < sb[sg + 1] && j <= i; j += 2) {
+                const int pm = mask(i, j, np);
+                if (!pm) continue;
+                const int two = (j + 1 < sb[sg + 1] && j + 1 <= i) ? 2 : 0;
+                far.push_back(Task{f, i, j, 1 | two | pm});
+              }
+          }
+        }
+        Q.n_near = (int)near.size();
+        Q.n_far = (int)far.size();
+        h_tc2.insert(h_tc2.end(), near.begin(), near.end());
+        h_tc2.insert(h_tc2.end(), far.begin(), far.end());
+        Q.grp_off = (int64_t)h_grp.size();
+        Q.n_grp_near = add_groups(h_tc2, Q.tc_off, Q.n_near);
+        Q.n_grp_far = add_groups(h_tc2, Q.tc_off + Q.n_near, Q.n_far);
+        L.quads.push_back(Q);
       }
   }
   // solve tasks: forward (front, row tile) by increasing tile, backward (front,
@@ -1444,7 +1514,10 @@ static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& n
     const bool ahead = h->use_tc && L.ahead && (int)L.ids.size() <= h->ahead_fronts && L.steps.size() > 1;
     const int reserve = ahead ? h->reserve_sms : 0;   // SMs left free for the panel chain
     // image slot of panel k: even / odd panels alternate, the look-ahead levels over four slots
-    auto wsp = [&](int k) -> unsigned char* { return h->d_ws + h->ws_slot_off[ahead ? (k & 3) : (k & 1)]; };
+    const bool quad = h->quad_panels && !ahead && !L.quads.empty();
+    auto wsp = [&](int k) -> unsigned char* {
+      return h->d_ws + h->ws_slot_off[(ahead || quad) ? (k & 3) : (k & 1)];
+    };
     auto panel = [&](const StepRange& R) -> cudaError_t {
       unsigned char* ws = h->use_tc ? wsp(R.k) : nullptr;
       cudaError_t e = mark(DD_K_DIAG, true);
@@ -1479,8 +1552,8 @@ static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& n
       if (e != cudaSuccess) return e;
       if (h->use_tc)
         ddk::launch_update_tc(h->pool, h->d_fronts, h->d_tc, h->d_grp + R.grp_off + (next_part ? 0 : R.n_grp_next),
-                              next_part ? R.n_grp_next : R.n_grp_rest, R.k, ws, nullptr, h->d_status, on, cap,
-                              h->d_counters + (next_counter++ % h->n_counters));
+                              next_part ? R.n_grp_next : R.n_grp_rest, R.k, ddk::PanelImages{{ws, nullptr, nullptr, nullptr}},
+                              h->d_status, on, cap, h->d_counters + (next_counter++ % h->n_counters));
       else
         ddk::launch_update(p, h->pool, h->d_fronts, h->d_updt + first, n, R.k, on);
       count(DD_K_UPDATE, n);
@@ -1491,10 +1564,22 @@ static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& n
       cudaError_t e = mark_on(DD_K_UPDATE, true, on);
       if (e != cudaSuccess) return e;
       ddk::launch_update_tc(h->pool, h->d_fronts, h->d_tc2, h->d_grp + P.grp_off + (near_part ? 0 : P.n_grp_near),
-                             near_part ? P.n_grp_near : P.n_grp_far, P.k, wsp(P.k), wsp(P.k + 1), h->d_status, on,
-                             cap, h->d_counters + (next_counter++ % h->n_counters));
+                             near_part ? P.n_grp_near : P.n_grp_far, P.k,
+                             ddk::PanelImages{{wsp(P.k), wsp(P.k + 1), nullptr, nullptr}}, h->d_status, on, cap,
+                             h->d_counters + (next_counter++ % h->n_counters));
       count(DD_K_UPDATE, near_part ? P.n_near : P.n_far);
       return mark_on(DD_K_UPDATE, false, on);
+    };
+    // four-panel update of steps Q.k .. Q.k + 3: near (columns k + 2, k + 3) or far (the rest)
+    auto quad_update = [&](const QuadRange& Q, bool near_part) -> cudaError_t {
+      cudaError_t e = mark_on(DD_K_UPDATE, true, s);
+      if (e != cudaSuccess) return e;
+      ddk::launch_update_tc(h->pool, h->d_fronts, h->d_tc2, h->d_grp + Q.grp_off + (near_part ? 0 : Q.n_grp_near),
+                             near_part ? Q.n_grp_near : Q.n_grp_far, Q.k,
+                             ddk::PanelImages{{wsp(Q.k), wsp(Q.k + 1), wsp(Q.k + 2), wsp(Q.k + 3)}}, h->d_status, s, 0,
+                             h->d_counters + (next_counter++ % h->n_counters));
+      count(DD_K_UPDATE, near_part ? Q.n_near : Q.n_far);
+      return mark_on(DD_K_UPDATE, false, s);
     };
     const size_t ns = L.steps.size();
     if (!h->use_tc || (!h->pair_panels && !ahead)) {
@@ -1519,6 +1604,39 @@ static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& n
           DD_CUDA(cudaEventRecord(h->ev_panel, s));
         }
         DD_CUDA(cudaStreamWaitEvent(s, h->ev_rest, 0));
+      }
+    } else if (quad) {
+      // steps in fours: panel k, column k + 1; panel k + 1, columns k + 2, k + 3
+      // with panels k, k + 1; panel k + 2, column k + 3 with it; panel k + 3,
+      // then the columns >= k + 4 with all four panels (C read and written
+      // once per four steps); the last steps in pairs
+      for (size_t q = 0; q < ns;) {
+        const StepRange& R = L.steps[q];
+        if (q + 3 < ns) {
+          const QuadRange& Q = L.quads[q / 4];
+          DD_CUDA(panel(R));
+          DD_CUDA(update(R, true, s, 0));
+          DD_CUDA(panel(L.steps[q + 1]));
+          DD_CUDA(quad_update(Q, true));
+          DD_CUDA(panel(L.steps[q + 2]));
+          DD_CUDA(update(L.steps[q + 2], true, s, 0));
+          DD_CUDA(panel(L.steps[q + 3]));
+          DD_CUDA(quad_update(Q, false));
+          q += 4;
+        } else {
+          DD_CUDA(panel(R));
+          DD_CUDA(update(R, true, s, 0));
+          if (q + 1 < ns) {
+            const PairRange& P = L.pairs[q / 2];
+            DD_CUDA(panel(L.steps[q + 1]));
+            DD_CUDA(pair_update(P, true, s, 0));
+            DD_CUDA(pair_update(P, false, s, 0));
+            q += 2;
+          } else {
+            DD_CUDA(update(R, false, s, 0));
+            q += 1;
+          }
+        }
       }
     } else if (!ahead) {
       // steps in pairs: panel k, column k + 1, panel k + 1, then both panels at once
@@ -1640,11 +1758,12 @@ int dd_factor(dd_handle* h) {
 
 int dd_set_schedule(dd_handle* h, const dd_schedule* sc) {
   if (!h || !sc) return DD_ERR_INVALID_ARG;
-  if ((sc->update_panels != 1 && sc->update_panels != 2) || sc->ahead_fronts < 0 ||
+  if ((sc->update_panels != 1 && sc->update_panels != 2 && sc->update_panels != 4) || sc->ahead_fronts < 0 ||
       sc->ahead_fronts > kAheadMaxFronts || sc->reserve_sms < 0 || sc->reserve_sms > 64)
     return DD_ERR_INVALID_ARG;
   if (!h->use_tc) return DD_OK;
-  h->pair_panels = sc->update_panels == 2;
+  h->pair_panels = sc->update_panels >= 2;
+  h->quad_panels = sc->update_panels == 4;
   h->ahead_fronts = sc->ahead_fronts;
   h->reserve_sms = sc->reserve_sms;
   if (h->factor_exec) cudaGraphExecDestroy(h->factor_exec);   // recaptured by the next dd_factor
@@ -1665,7 +1784,7 @@ int dd_autotune(dd_handle* h, int32_t repeats, dd_schedule* out) {
     }
     return DD_OK;
   };
-  dd_schedule cur{h->pair_panels ? 2 : 1, h->ahead_fronts, h->reserve_sms, 0.0, 0};
+  dd_schedule cur{h->quad_panels ? 4 : (h->pair_panels ? 2 : 1), h->ahead_fronts, h->reserve_sms, 0.0, 0};
   if (!h->use_tc) {
     const int st = time_it(&cur.factor_ms);
     cur.configs_tried = 1;
@@ -1673,7 +1792,7 @@ int dd_autotune(dd_handle* h, int32_t repeats, dd_schedule* out) {
     return st;
   }
   std::vector<dd_schedule> grid;
-  for (int panels : {1, 2})
+  for (int panels : {1, 2, 4})
     for (int ahead : {0, 8, 32, 128, 1024})
       for (int reserve : {8, 16, 32}) {
         if (ahead == 0 && reserve != 16) continue;   // no look-ahead: the reserve is unused

@@ -113,13 +113,13 @@ void launch_trsm_mx(void* pool, const FrontDev* fronts, const Task* tasks, int n
                     const void* linv, unsigned char* ws, cudaStream_t s, const uint8_t* piv = nullptr,
                     int tensor = 0);
 // tensor-core trailing update (mixed form): task (front, row tile i, column
-// tile j); .pad bits 0 / 1 store column tiles j / j + 1, bits 2 / 3 add the
-// products of panel k (images in ws0) / panel k + 1 (images in ws1).
+// tile j); .pad bits 0 / 1 store column tiles j / j + 1, bits 2..5 add the
+// products of panels k .. k + 3 (images in ws.p[0 .. 3]).
 // groups: (first task, count) of runs of tasks of one row tile; n = number of groups;
 // counter: a zeroed int in device memory used to claim groups dynamically (one per launch)
+struct PanelImages { const unsigned char* p[4]; };
 void launch_update_tc(void* pool, const FrontDev* fronts, const Task* tasks, const int2* groups, int n, int k,
-                      const unsigned char* ws0, const unsigned char* ws1, DevStatus* st, cudaStream_t s,
-                      int reserve_sms, int* counter);
+                      const PanelImages& ws, DevStatus* st, cudaStream_t s, int reserve_sms, int* counter);
 void launch_update(int prec, void* pool, const FrontDev* fronts, const Task* tasks, int n, int k,
                    cudaStream_t s);
 void launch_extend_add(int prec, void* pool, const FrontDev* fronts, const int32_t* node_ids, int n,

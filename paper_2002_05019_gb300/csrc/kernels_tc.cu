@@ -79,7 +79,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t ta, uint32_t (&r)[32]) {
 // issues the MMAs into one of two TMEM accumulators; warps 2-5 drain the other
 // accumulator into C.  Task .pad: bit 0 / 1 store column tile j / j + 1 (with
 // bit 1 clear the MMAs use N = 128 and only tile j's operand is loaded),
-// bit 2 / 3 panel k / k + 1 contributes.
+// bits 2..5 panel k .. k + 3 contributes (its images in ws.p[0 .. 3]).
 constexpr int kStageA = 2 * DD_TC_ATOM;          // hi, lo pieces of the row tile: 32 KB
 constexpr int kStageB = 2 * 2 * DD_TC_ATOM;      // hi, lo x two column tiles: 64 KB
 constexpr int kStage = kStageA + kStageB;        // 96 KB per K atom
@@ -206,7 +206,7 @@ __device__ __forceinline__ void epilogue_role(float2* pool, const FrontDev* fr, 
 
 __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontDev* fr, const Task* tasks,
                                                       const int2* groups, int n_groups, int k,
-                                                      const unsigned char* ws0, const unsigned char* ws1,
+                                                      const PanelImages ws,
                                                       DevStatus* st, int* counter) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -261,10 +261,10 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
         const FrontDev F = fr[t.f];
         const int ncol = (t.pad & 2) ? 2 : 1;
         const int bytes = kStageA + ncol * 2 * DD_TC_ATOM;
-        for (int pp = 0; pp < 2 && !fail; ++pp) {
+        for (int pp = 0; pp < 4 && !fail; ++pp) {
           if (!(t.pad & (4 << pp))) continue;
           const int p = k + pp;
-          const unsigned char* w = pp ? ws1 : ws0;
+          const unsigned char* w = ws.p[pp];
           const unsigned char* gA = w + F.ws_off + (int64_t)(t.i - p - 1) * DD_TC_ATILE;
           const unsigned char* gB = w + F.ws_boff + (int64_t)(t.j - p - 1) * DD_TC_BTILE;
           for (int a = 0; a < 2; ++a, ++u) {
@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
         const uint32_t dacc = tmem + ab * kAccCols;
         const uint32_t idesc = (t.pad & 2) ? kIdesc256 : kIdesc128;
         uint32_t acc_on = 0;
-        for (int pp = 0; pp < 2 && !fail; ++pp) {
+        for (int pp = 0; pp < 4 && !fail; ++pp) {
           if (!(t.pad & (4 << pp))) continue;
           for (int a = 0; a < 2; ++a, ++u) {
             const int sidx = u % kStages;
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
 }  // namespace
 
 void launch_update_tc(void* pool, const FrontDev* fronts, const Task* tasks, const int2* groups, int n, int k,
-                      const unsigned char* ws0, const unsigned char* ws1, DevStatus* st, cudaStream_t s,
+                      const PanelImages& ws, DevStatus* st, cudaStream_t s,
                       int reserve_sms, int* counter) {
   if (n <= 0) return;
   static int sms = 0;
@@ -359,7 +359,7 @@ void launch_update_tc(void* pool, const FrontDev* fronts, const Task* tasks, con
   }
   const int avail = sms - reserve_sms > 1 ? sms - reserve_sms : 1;
   const int grid = n < avail ? n : avail;
-  k_update_tc<<<grid, 192, kSmemP, s>>>((float2*)pool, fronts, tasks, groups, n, k, ws0, ws1, st, counter);
+  k_update_tc<<<grid, 192, kSmemP, s>>>((float2*)pool, fronts, tasks, groups, n, k, ws, st, counter);
 }
 
 }  // namespace ddk

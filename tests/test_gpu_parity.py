@@ -198,7 +198,7 @@ def test_batched_512_domains_full_size(c2_linear, precision):
 
 @pytest.mark.parametrize("p_name", ["c1", "medium"])
 def test_tensor_core_update_matches_simt_update(c1, p_name):
-    """The tcgen05 3xTF32 trailing update, one or two panels per pass, and the
+    """The tcgen05 3xTF32 trailing update, one, two or four panels per pass, and the
     FP32 FMA-pipe update give the same F_i to the accuracy of 3xTF32 products
     (two independent errors of cond(A_i) 2^-21 each) and all refine to the
     mixed tolerance."""
@@ -206,9 +206,9 @@ def test_tensor_core_update_matches_simt_update(c1, p_name):
     o = oracle.DDOracle(p) if p_name == "c1" else None
     xo = o.gather(o.solve([s.f for s in p.subs])[0])[0] if o else None
     res = {}
-    for mode in ("tc2", "tc1", "simt"):
+    for mode in ("tc2", "tc1", "tc4", "simt"):
         s = dd.Solver.from_problem(p, precision="mixed", simt_update=(mode == "simt"),
-                                   update_panels=(1 if mode == "tc1" else 2))
+                                   update_panels={"tc1": 1, "tc4": 4}.get(mode, 2))
         s.factor()
         u, lam = s.solve(dd.stacked_loads(p))
         if xo is not None:
@@ -216,7 +216,7 @@ def test_tensor_core_update_matches_simt_update(c1, p_name):
         res[mode] = ([s.schur(i)[0] for i in range(0, p.n_sub, max(1, p.n_sub // 8))], u)
         s.free()
     tols = [2 * tol_f("mixed", p.subs[i]) for i in range(0, p.n_sub, max(1, p.n_sub // 8))]
-    for mode in ("tc1", "simt"):
+    for mode in ("tc1", "tc4", "simt"):
         for a, b, t in zip(res["tc2"][0], res[mode][0], tols):
             assert rel(a, b) <= t
         assert rel(res["tc2"][1], res[mode][1]) <= TOL["mixed"] * 10
