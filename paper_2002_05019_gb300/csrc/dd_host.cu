@@ -31,7 +31,7 @@ namespace {
 
 constexpr int T = DD_TILE;
 constexpr int kSolveBlock = 64;   // right-hand sides per direct-solve pass
-constexpr int kAheadMaxFronts = 1024;  // look-ahead is possible on levels with at most this many fronts
+constexpr int kAheadMaxFronts = 4096;  // look-ahead is possible on levels with at most this many fronts
 constexpr int kNormBlocks = 16;   // reduction blocks per column for the refinement norms
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
@@ -71,9 +71,10 @@ struct PairRange {
 struct QuadRange {
   int k;
   int64_t tc_off;
-  int n_near, n_far;
+  int n_near, n_far;          // far = columns >= k + 4: first n_far4 of them columns k + 4 .. k + 7
+  int n_far4;
   int64_t grp_off;
-  int n_grp_near, n_grp_far;
+  int n_grp_near, n_grp_far, n_grp_far4;
 };
 
 struct Level {
@@ -189,7 +190,7 @@ struct dd_handle {
   int* d_counters = nullptr;       // one group counter per tensor-core update launch of a factor
   int n_counters = 0;
   unsigned char* d_ws = nullptr;   // panel operand images (mixed form), four slots
-  size_t ws_slot_off[4] = {0, 0, 0, 0};
+  size_t ws_slot_off[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   float2* d_linv = nullptr;        // mixed form: L_kk^{-1} of every diagonal tile (index tile_off + k)
   uint8_t* d_piv = nullptr;        // restricted Bunch-Kaufman: permutation of every diagonal tile (64 bytes each)
   int pivoting = 0;
@@ -1022,12 +1023,11 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
       if (L.ahead) need_ahead = std::max(need_ahead, (size_t)w);
     }
     // four-panel passes hold the images of panels k .. k + 3 at once: slots
-    // 2 and 3 are sized for every level then
-    (void)need_ahead;
-    h->ws_bytes = 4 * need;
-    h->ws_slot_off[1] = need;
-    h->ws_slot_off[2] = 2 * need;
-    h->ws_slot_off[3] = 3 * need;
+    // 0-3 are sized for every level; with look-ahead the far part of a
+    // four-panel update still reads them while the next four panels are
+    // formed into slots 4-7, sized for the levels that may look ahead
+    h->ws_bytes = 4 * need + 4 * need_ahead;
+    for (int q = 1; q < 8; ++q) h->ws_slot_off[q] = q <= 4 ? q * need : 4 * need + (q - 4) * need_ahead;
   }
   std::vector<int32_t> h_level_ids, h_diag;
   std::vector<Task> h_trsm, h_updt, h_tc, h_tc2;
@@ -1212,13 +1212,18 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
               }
           }
         }
+        // far tasks of columns k + 4 .. k + 7 first (the next four panels' columns:
+        // the look-ahead schedule applies them on the main stream), the rest after
+        std::stable_partition(far.begin(), far.end(), [&](const Task& t) { return t.j <= k + 7; });
         Q.n_near = (int)near.size();
         Q.n_far = (int)far.size();
+        Q.n_far4 = (int)std::count_if(far.begin(), far.end(), [&](const Task& t) { return t.j <= k + 7; });
         h_tc2.insert(h_tc2.end(), near.begin(), near.end());
         h_tc2.insert(h_tc2.end(), far.begin(), far.end());
         Q.grp_off = (int64_t)h_grp.size();
         Q.n_grp_near = add_groups(h_tc2, Q.tc_off, Q.n_near);
-        Q.n_grp_far = add_groups(h_tc2, Q.tc_off + Q.n_near, Q.n_far);
+        Q.n_grp_far4 = add_groups(h_tc2, Q.tc_off + Q.n_near, Q.n_far4);
+        Q.n_grp_far = Q.n_grp_far4 + add_groups(h_tc2, Q.tc_off + Q.n_near + Q.n_far4, Q.n_far - Q.n_far4);
         L.quads.push_back(Q);
       }
   }
@@ -1514,9 +1519,10 @@ static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& n
     const bool ahead = h->use_tc && L.ahead && (int)L.ids.size() <= h->ahead_fronts && L.steps.size() > 1;
     const int reserve = ahead ? h->reserve_sms : 0;   // SMs left free for the panel chain
     // image slot of panel k: even / odd panels alternate, the look-ahead levels over four slots
-    const bool quad = h->quad_panels && !ahead && !L.quads.empty();
+    // four-panel passes (slots k & 3, or k & 7 with look-ahead)
+    const bool quad = h->quad_panels && !L.quads.empty();
     auto wsp = [&](int k) -> unsigned char* {
-      return h->d_ws + h->ws_slot_off[(ahead || quad) ? (k & 3) : (k & 1)];
+      return h->d_ws + h->ws_slot_off[quad ? (ahead ? (k & 7) : (k & 3)) : (ahead ? (k & 3) : (k & 1))];
     };
     auto panel = [&](const StepRange& R) -> cudaError_t {
       unsigned char* ws = h->use_tc ? wsp(R.k) : nullptr;
@@ -1570,16 +1576,33 @@ static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& n
       count(DD_K_UPDATE, near_part ? P.n_near : P.n_far);
       return mark_on(DD_K_UPDATE, false, on);
     };
-    // four-panel update of steps Q.k .. Q.k + 3: near (columns k + 2, k + 3) or far (the rest)
-    auto quad_update = [&](const QuadRange& Q, bool near_part) -> cudaError_t {
-      cudaError_t e = mark_on(DD_K_UPDATE, true, s);
+    // four-panel update of steps Q.k .. Q.k + 3, part 0: columns k + 2, k + 3
+    // (panels k, k + 1); 1: columns >= k + 4; 2: columns k + 4 .. k + 7; 3: columns >= k + 8
+    auto quad_update = [&](const QuadRange& Q, int part, cudaStream_t on, int cap) -> cudaError_t {
+      cudaError_t e = mark_on(DD_K_UPDATE, true, on);
       if (e != cudaSuccess) return e;
-      ddk::launch_update_tc(h->pool, h->d_fronts, h->d_tc2, h->d_grp + Q.grp_off + (near_part ? 0 : Q.n_grp_near),
-                             near_part ? Q.n_grp_near : Q.n_grp_far, Q.k,
-                             ddk::PanelImages{{wsp(Q.k), wsp(Q.k + 1), wsp(Q.k + 2), wsp(Q.k + 3)}}, h->d_status, s, 0,
-                             h->d_counters + (next_counter++ % h->n_counters));
-      count(DD_K_UPDATE, near_part ? Q.n_near : Q.n_far);
-      return mark_on(DD_K_UPDATE, false, s);
+      int64_t g0 = Q.grp_off;
+      int ng = Q.n_grp_near, nt_ = Q.n_near;
+      if (part == 1) { g0 += Q.n_grp_near; ng = Q.n_grp_far; nt_ = Q.n_far; }
+      if (part == 2) { g0 += Q.n_grp_near; ng = Q.n_grp_far4; nt_ = Q.n_far4; }
+      if (part == 3) { g0 += Q.n_grp_near + Q.n_grp_far4; ng = Q.n_grp_far - Q.n_grp_far4; nt_ = Q.n_far - Q.n_far4; }
+      ddk::launch_update_tc(h->pool, h->d_fronts, h->d_tc2, h->d_grp + g0, ng, Q.k,
+                             ddk::PanelImages{{wsp(Q.k), wsp(Q.k + 1), wsp(Q.k + 2), wsp(Q.k + 3)}}, h->d_status, on,
+                             cap, h->d_counters + (next_counter++ % h->n_counters));
+      count(DD_K_UPDATE, nt_);
+      return mark_on(DD_K_UPDATE, false, on);
+    };
+    // the panels of steps q0 .. q0 + 3 with the updates between them that they need
+    auto quad_panels = [&](size_t q0) -> cudaError_t {
+      const QuadRange& Q = L.quads[q0 / 4];
+      cudaError_t e;
+      if ((e = panel(L.steps[q0])) != cudaSuccess) return e;
+      if ((e = update(L.steps[q0], true, s, 0)) != cudaSuccess) return e;      // column k + 1
+      if ((e = panel(L.steps[q0 + 1])) != cudaSuccess) return e;
+      if ((e = quad_update(Q, 0, s, 0)) != cudaSuccess) return e;               // columns k + 2, k + 3
+      if ((e = panel(L.steps[q0 + 2])) != cudaSuccess) return e;
+      if ((e = update(L.steps[q0 + 2], true, s, 0)) != cudaSuccess) return e;  // column k + 3, panel k + 2
+      return panel(L.steps[q0 + 3]);
     };
     const size_t ns = L.steps.size();
     if (!h->use_tc || (!h->pair_panels && !ahead)) {
@@ -1609,19 +1632,33 @@ static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& n
       // steps in fours: panel k, column k + 1; panel k + 1, columns k + 2, k + 3
       // with panels k, k + 1; panel k + 2, column k + 3 with it; panel k + 3,
       // then the columns >= k + 4 with all four panels (C read and written
-      // once per four steps); the last steps in pairs
-      for (size_t q = 0; q < ns;) {
+      // once per four steps); the last steps in pairs.  With look-ahead the
+      // columns >= k + 8 run on the second stream while the main stream
+      // applies the four panels to columns k + 4 .. k + 7 and forms the next four.
+      size_t q = 0;
+      if (ahead) {
+        DD_CUDA(cudaEventRecord(h->ev_panel, s));
+        DD_CUDA(cudaStreamWaitEvent(h->s2, h->ev_panel, 0));
+        DD_CUDA(cudaEventRecord(h->ev_rest, h->s2));
+        DD_CUDA(quad_panels(0));
+        for (; q + 3 < ns; q += 4) {
+          const QuadRange& Q = L.quads[q / 4];
+          DD_CUDA(cudaStreamWaitEvent(s, h->ev_rest, 0));     // the previous far part is done
+          DD_CUDA(cudaEventRecord(h->ev_panel, s));
+          DD_CUDA(cudaStreamWaitEvent(h->s2, h->ev_panel, 0));
+          DD_CUDA(quad_update(Q, 3, h->s2, reserve));          // columns >= k + 8
+          DD_CUDA(cudaEventRecord(h->ev_rest, h->s2));
+          DD_CUDA(quad_update(Q, 2, s, 0));                    // columns k + 4 .. k + 7
+          if (q + 7 < ns) DD_CUDA(quad_panels(q + 4));
+        }
+        DD_CUDA(cudaStreamWaitEvent(s, h->ev_rest, 0));
+      }
+      for (; q < ns;) {
         const StepRange& R = L.steps[q];
         if (q + 3 < ns) {
           const QuadRange& Q = L.quads[q / 4];
-          DD_CUDA(panel(R));
-          DD_CUDA(update(R, true, s, 0));
-          DD_CUDA(panel(L.steps[q + 1]));
-          DD_CUDA(quad_update(Q, true));
-          DD_CUDA(panel(L.steps[q + 2]));
-          DD_CUDA(update(L.steps[q + 2], true, s, 0));
-          DD_CUDA(panel(L.steps[q + 3]));
-          DD_CUDA(quad_update(Q, false));
+          DD_CUDA(quad_panels(q));
+          DD_CUDA(quad_update(Q, 1, s, 0));                    // columns >= k + 4
           q += 4;
         } else {
           DD_CUDA(panel(R));
@@ -1793,7 +1830,7 @@ int dd_autotune(dd_handle* h, int32_t repeats, dd_schedule* out) {
   }
   std::vector<dd_schedule> grid;
   for (int panels : {1, 2, 4})
-    for (int ahead : {0, 8, 32, 128, 1024})
+    for (int ahead : {0, 8, 32, 128, 1024, 4096})
       for (int reserve : {8, 16, 32}) {
         if (ahead == 0 && reserve != 16) continue;   // no look-ahead: the reserve is unused
         grid.push_back(dd_schedule{panels, ahead, reserve, 0.0, 0});
