@@ -179,14 +179,14 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
 int dd_set_values(dd_handle* h, const dd_c128* vals);
 
 /* Set the schedule of the tensor-core path (update_panels 1, 2 or 4, ahead_fronts
- * in [0, 4096], reserve_sms in [0, 64]); factor_ms and configs_tried are ignored.
+ * in [0, 1024], reserve_sms in [0, 64]); factor_ms and configs_tried are ignored.
  * The factors already computed stay valid; the next dd_factor uses the new
  * schedule.  No effect in the FP64 form or with simt_update.
  * DD_ERR_INVALID_ARG for values out of range. */
 int dd_set_schedule(dd_handle* h, const dd_schedule* sched);
 
 /* Autotuner: times dd_factor (the minimum over `repeats` runs each) under every
- * schedule of the grid update_panels {1, 2, 4} x ahead_fronts {0, 8, 32, 128, 1024, 4096} x
+ * schedule of the grid update_panels {1, 2, 4} x ahead_fronts {0, 8, 32, 128, 1024} x
  * reserve_sms {8, 16, 32} (look-ahead off: reserve not varied), keeps the
  * fastest for this handle and returns it in *out; the handle is left factored
  * with it.  FP64 form / simt_update: one dd_factor, configs_tried = 1.

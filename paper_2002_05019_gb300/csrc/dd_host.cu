@@ -31,7 +31,7 @@ namespace {
 
 constexpr int T = DD_TILE;
 constexpr int kSolveBlock = 64;   // right-hand sides per direct-solve pass
-constexpr int kAheadMaxFronts = 4096;  // look-ahead is possible on levels with at most this many fronts
+constexpr int kAheadMaxFronts = 1024;  // look-ahead is possible on levels with at most this many fronts
 constexpr int kNormBlocks = 16;   // reduction blocks per column for the refinement norms
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
@@ -1830,7 +1830,7 @@ int dd_autotune(dd_handle* h, int32_t repeats, dd_schedule* out) {
   }
   std::vector<dd_schedule> grid;
   for (int panels : {1, 2, 4})
-    for (int ahead : {0, 8, 32, 128, 1024, 4096})
+    for (int ahead : {0, 8, 32, 128, 1024})
       for (int reserve : {8, 16, 32}) {
         if (ahead == 0 && reserve != 16) continue;   // no look-ahead: the reserve is unused
         grid.push_back(dd_schedule{panels, ahead, reserve, 0.0, 0});

@@ -55,8 +55,8 @@ def test_autotune_picks_and_keeps_a_schedule(c1):
     p, xo = c1
     s = dd.Solver.from_problem(p, precision="mixed")
     r = s.autotune(repeats=1)
-    assert r["configs_tried"] == 48 and r["factor_ms"] > 0
-    assert r["update_panels"] in (1, 2, 4) and r["ahead_fronts"] in (0, 8, 32, 128, 1024, 4096)
+    assert r["configs_tried"] == 39 and r["factor_ms"] > 0
+    assert r["update_panels"] in (1, 2, 4) and r["ahead_fronts"] in (0, 8, 32, 128, 1024)
     u, _ = s.solve(dd.stacked_loads(p))          # factored by the tuner with its choice
     assert rel(_x(p, u), xo) <= TOL
     with pytest.raises(dd.DDError) as e:
