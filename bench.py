@@ -49,6 +49,7 @@ WORKLOADS = {
     "many": ("multi_rhs_c5", "box n=8 Kuhn tets, 8 equal domains, eps_r=2-0.1j, 64 RHS: 56 edge currents "
              "+ 8 plane waves, factor once"),
     "plain": ("plain_c1", "box n=8 Kuhn tets, 8 equal domains, eps_r=2-0.1j, 1 edge-current RHS"),
+    "big": ("big_domains", "box n=24 Kuhn tets, 8 equal domains of 13,428 unknowns, eps_r=2-0.1j, 1 edge-current RHS"),
 }
 
 
@@ -318,9 +319,14 @@ def time_form(p, precision, args, torch, stream, steps, warmup, e2e=True, autotu
     s = dd.Solver.from_problem(p, precision=precision, stream=stream.cuda_stream, device=torch.cuda.current_device(),
                                time_kernels={"all": 1, "update": 2, "none": 0}[args.kernel_timing],
                                refine_tol=args.refine_tol,
-                               pivoting=args.pivoting, update_panels=args.update_panels)
+                               pivoting=args.pivoting, update_panels=args.update_panels,
+                               sparse_min=args.sparse_min)
     sched = None
-    if precision == "mixed" and autotune and not args.no_autotune:
+    if precision == "mixed" and args.schedule:
+        panels, ahead, reserve = (int(x) for x in args.schedule.split(","))
+        s.set_schedule(panels, ahead, reserve)
+        sched = {"update_panels": panels, "ahead_fronts": ahead, "reserve_sms": reserve, "set": True}
+    elif precision == "mixed" and autotune and not args.no_autotune:
         sched = s.autotune(repeats=2)      # untimed: picks the factor schedule for this workload
     f_host = dd.stacked_loads(p)
     f_dev = torch.from_numpy(f_host).cuda()
@@ -488,6 +494,7 @@ def ours_arm(args):
         "config": {"workload": WORKLOADS[args.workload][1], "form": args.precision, "n_dofs": p.n,
                    "n_domains": p.n_sub, "n_duals": p.n_dual, "nrhs": p.nrhs, "pivoting": args.pivoting,
                    "update_panels": args.update_panels, "schedule": main.get("schedule"),
+                   "sparse_min": args.sparse_min,
                    "refine_tol": args.refine_tol,
                    "l2": "inputs larger than L2: the front pool is far larger than the 129 MB L2",
                    "parallelism": f"replicas x{ws}"},
@@ -561,6 +568,11 @@ def main():
     ap.add_argument("--update-panels", type=int, default=2, choices=[1, 2, 4],
                     help="mixed form: panels fused per tensor-core trailing-update pass")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default factor schedule")
+    ap.add_argument("--schedule", default="", help="PANELS,AHEAD_FRONTS,RESERVE_SMS: set this factor schedule "
+                                                   "instead of autotuning")
+    ap.add_argument("--sparse-min", type=int, default=0,
+                    help="domains of at least this many unknowns are factored as nested-dissection front trees "
+                         "(0: every domain one dense front)")
     ap.add_argument("--kernel-timing", default="update", choices=["update", "all", "none"],
                     help="CUDA events in the timed factorizations: around the trailing-update launches "
                          "(the roofline kernel; default), around every launch (per-class breakdown, slower), "
