@@ -719,6 +719,11 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
   // row id of stacked primal row r (rows of sparse-domain fronts)
   auto vid = [&](int i, int r) -> int32_t { return (int32_t)(n_dual + spd[i].vec_off + r); };
   if (h->n_sparse && (int64_t)n_dual + spd[n_sub - 1].vec_off + subs[n_sub - 1].n > INT32_MAX) return DD_ERR_INVALID_ARG;
+  if (h->n_sparse) {   // the scatter initialisation indexes the stacked CSR values with 32-bit ints
+    int64_t nnz_all = 0;
+    for (int i = 0; i < n_sub; ++i) nnz_all += subs[i].rowptr[subs[i].n];
+    if (nnz_all > INT32_MAX) return DD_ERR_INVALID_ARG;
+  }
 
   // ---- leaf structures --------------------------------------------------------
   h->fronts.assign(n_front_all, FrontDev{});
