@@ -98,6 +98,24 @@ int dd_domain_assembly(int32_t n, const int32_t* rowptr, const int32_t* colind, 
                        int64_t rows_cap, int64_t* rows_ptr, int32_t* rows, int32_t* ea_map, int32_t* a_front,
                        int32_t* a_row, int32_t* a_col);
 
+/* Shard plan of the front tree over n_ranks ranks (host only, touching no
+ * device; multi-GPU sharding of Section II's independent domain factorizations
+ * and of the tree of the auxiliary matrix's dense blocks).  The front tree is
+ * dd_symbolic's (same inputs and options); it is cut into n_ranks subtrees of
+ * about equal algorithmic work by repeatedly splitting the subtree of largest
+ * work into its children.  Rank r owns the subtree rooted at rank_root[r]
+ * (its domains and fronts); rank 0 also owns the fronts above the cuts.  The
+ * exchange this implies: each cut subtree's root passes its Schur complement
+ * (on its update duals, dd_symbolic's upd_idx) to the owner of its parent
+ * front, and in a solve the right-hand side of those duals up and their
+ * solved values down.
+ * Outputs, caller-allocated: n_front; front_rank[max_fronts] (the owner of
+ * every front); rank_root[n_ranks] (ascending front ids).
+ * Returns DD_OK, DD_ERR_INVALID_ARG (n_ranks < 1, more ranks than the tree can
+ * be cut into, a NULL output, max_fronts too small) or dd_symbolic's codes. */
+int dd_shard_plan(int32_t n_sub, const dd_subdomain* subs, int32_t n_dual, const dd_options* opt, int32_t n_ranks,
+                  int32_t max_fronts, int32_t* n_front, int32_t* front_rank, int32_t* rank_root);
+
 #ifdef __cplusplus
 }
 #endif

@@ -27,6 +27,10 @@ Routes to the same solution x = A^{-1} b of the assembled FEM system:
                               auxiliary matrix's symbolic factorization
                               (Section II), by clique-graph elimination and
                               from the domain tree;
+  * shard.plan / ShardedTreeDD - the tree route sharded over ranks along a
+                              cut of the front tree (one subtree per rank, the
+                              fronts above the cut on rank 0), run on a
+                              torch.distributed group (gloo on the CPU);
   * domain_symbolic          - validity of a nested dissection of one domain
                               and its front structure, by row-by-row graph
                               elimination and by reach.
@@ -40,9 +44,9 @@ from .dd import DDOracle, SparseDDOracle, gather_copies, subdomain_schur, arrow_
 from .refine import residual_dd, refine, backward_error
 from .tree import TreeDDOracle, subtree_nodes
 from .symbolic import fronts_by_elimination, fronts_by_tree, lca_fronts, dual_domains
-from . import domain_symbolic
+from . import domain_symbolic, shard
 
 __all__ = ["lu_solve", "ldlt", "ldlt_solve", "ldlt_bk_restricted", "ldlt_bk_solve", "BandLDLT", "rcm", "envelope_entries",
            "DDOracle", "SparseDDOracle", "TreeDDOracle", "subtree_nodes", "gather_copies", "subdomain_schur", "arrow_residual", "local_B", "arrow_dense", "arrow_solve",
-           "fronts_by_elimination", "fronts_by_tree", "lca_fronts", "dual_domains", "domain_symbolic",
+           "fronts_by_elimination", "fronts_by_tree", "lca_fronts", "dual_domains", "domain_symbolic", "shard",
            "residual_dd", "refine", "backward_error"]

@@ -57,6 +57,55 @@ def subtree_nodes(parent, node: int) -> np.ndarray:
     return np.nonzero(inside)[0]
 
 
+def eliminate_fronts(n_dual, fronts, sep, upd, children, passed):
+    """Step 3 over `fronts` (children first): each front sums the blocks its
+    children pass up (popped from `passed`: child -> (duals, block)) and
+    passes up its Schur complement (stored in `passed` under its id).
+    Returns the LU of every F_ss, every F_us, and every front's order."""
+    pos = np.full(n_dual, -1, dtype=np.int64)
+    Fss, Fus_all, front_rows = {}, {}, {}
+    for v in fronts:
+        S, U = sep[v], upd[v]
+        rows = np.concatenate([S, U])
+        pos[rows] = np.arange(rows.size)
+        W = np.zeros((rows.size, rows.size), dtype=np.complex128)
+        for c in children[v]:
+            duals, M = passed.pop(c)
+            ix = pos[duals]
+            if (ix < 0).any():
+                raise ValueError(f"front {v}: a child passes a dual outside the front")
+            W[np.ix_(ix, ix)] += M
+        pos[rows] = -1
+        ns = S.size
+        Fus = W[ns:, :ns].copy()
+        if ns:
+            lu = sla.lu_factor(W[:ns, :ns], check_finite=False)
+            schur = W[ns:, ns:] - Fus @ sla.lu_solve(lu, Fus.T, check_finite=False)
+        else:
+            lu = None
+            schur = W[ns:, ns:]
+        Fss[v], Fus_all[v] = lu, Fus
+        front_rows[v] = rows.size
+        passed[v] = (U, schur)
+    return Fss, Fus_all, front_rows
+
+
+def forward_fronts(fronts, sep, upd, Fss, Fus, d):
+    """Step 4, the elimination of d over `fronts` in order (in place)."""
+    for v in fronts:
+        S, U = sep[v], upd[v]
+        if S.size:
+            d[U] -= Fus[v] @ sla.lu_solve(Fss[v], d[S], check_finite=False)
+
+
+def backward_fronts(fronts, sep, upd, Fss, Fus, d, lam):
+    """Step 4, the back substitution over `fronts` in reverse order (in place)."""
+    for v in reversed(fronts):
+        S, U = sep[v], upd[v]
+        if S.size:
+            lam[S] = sla.lu_solve(Fss[v], d[S] - Fus[v].T @ lam[U], check_finite=False)
+
+
 class TreeDDOracle:
     """Factor once (steps 1-3), solve for any loads (steps 4-5)."""
 
@@ -89,40 +138,15 @@ class TreeDDOracle:
             passed[i] = (duals.astype(np.int64), Fi)
 
         # step 3: block elimination of F over the front tree, children first
-        pos = np.full(p.n_dual, -1, dtype=np.int64)
-        self.Fss, self.Fus = {}, {}
-        self.front_rows = {}
-        for v in self.fronts:
-            S, U = self.sep[v], self.upd[v]
-            rows = np.concatenate([S, U])
-            pos[rows] = np.arange(rows.size)
-            W = np.zeros((rows.size, rows.size), dtype=np.complex128)
-            for c in children[v]:
-                duals, M = passed.pop(c)
-                ix = pos[duals]
-                if (ix < 0).any():
-                    raise ValueError(f"front {v}: a child passes a dual outside the front")
-                W[np.ix_(ix, ix)] += M
-            pos[rows] = -1
-            ns = S.size
-            Fus = W[ns:, :ns].copy()
-            if ns:
-                lu = sla.lu_factor(W[:ns, :ns], check_finite=False)
-                schur = W[ns:, ns:] - Fus @ sla.lu_solve(lu, Fus.T, check_finite=False)
-            else:
-                lu = None
-                schur = W[ns:, ns:]
-            self.Fss[v], self.Fus[v] = lu, Fus
-            self.front_rows[v] = rows.size
-            passed[v] = (U, schur)
+        self.Fss, self.Fus, self.front_rows = eliminate_fronts(p.n_dual, self.fronts, self.sep, self.upd, children,
+                                                               passed)
         # what is left: the Schur complement handed to the ancestors of the top
         # node (empty for the whole tree, whose root has no update duals)
         self.passed_up = passed
 
-    def solve(self, f_list, g=None):
-        """Loads f_i (n_i, k), indexed by domain id (all domains of the problem),
-        and the dual right-hand side g (n_dual, k) or None.  Returns (u_list in
-        the order of self.domains, lambda (n_dual, k))."""
+    def forward(self, f_list, g=None):
+        """d = sum_i B_i A_i^{-1} f_i - g over this tree's domains (n_dual, k),
+        then step 4's elimination over this tree's fronts."""
         p = self.p
         k = f_list[self.domains[0]].shape[1]
         d = np.zeros((p.n_dual, k), dtype=np.complex128)
@@ -131,20 +155,30 @@ class TreeDDOracle:
             d[duals] += Bt.T @ sla.lu_solve(self.lu[i], f_list[i], check_finite=False)
         if g is not None:
             d -= g
-        for v in self.fronts:                                    # step 4, elimination of d
-            S, U = self.sep[v], self.upd[v]
-            if S.size:
-                d[U] -= self.Fus[v] @ sla.lu_solve(self.Fss[v], d[S], check_finite=False)
-        lam = np.zeros_like(d)
-        for v in reversed(self.fronts):                          # back substitution
-            S, U = self.sep[v], self.upd[v]
-            if S.size:
-                lam[S] = sla.lu_solve(self.Fss[v], d[S] - self.Fus[v].T @ lam[U], check_finite=False)
+        forward_fronts(self.fronts, self.sep, self.upd, self.Fss, self.Fus, d)
+        return d
+
+    def backward(self, d, lam):
+        """Back substitution over this tree's fronts (reverse order); lam holds
+        the values of the update duals of the top front on entry."""
+        backward_fronts(self.fronts, self.sep, self.upd, self.Fss, self.Fus, d, lam)
+        return lam
+
+    def recover(self, f_list, lam):
+        """Step 5 for this tree's domains: u_i = A_i^{-1} (f_i - B_i^T lambda)."""
         u = []
-        for i in self.domains:                                   # step 5
+        for i in self.domains:
             Bt, duals = self.Bt[i]
             u.append(sla.lu_solve(self.lu[i], f_list[i] - Bt @ lam[duals], check_finite=False))
-        return u, lam
+        return u
+
+    def solve(self, f_list, g=None):
+        """Loads f_i (n_i, k), indexed by domain id (all domains of the problem),
+        and the dual right-hand side g (n_dual, k) or None.  Returns (u_list in
+        the order of self.domains, lambda (n_dual, k))."""
+        d = self.forward(f_list, g)
+        lam = self.backward(d, np.zeros_like(d))
+        return self.recover(f_list, lam), lam
 
     def gather(self, u_list):
         """Global vector from the local copies (whole tree only) and the copy mismatch."""

@@ -74,7 +74,7 @@ class Schedule(C.Structure):
 EXPORTS = ["dd_default_options", "dd_setup", "dd_set_values", "dd_factor", "dd_solve", "dd_solve_subset", "dd_get_schur",
            "dd_set_schedule", "dd_autotune",
            "dd_get_stats", "dd_strerror", "dd_free", "dd_dense_solve_noalloc", "dd_selftest_wait_timeout",
-           "dd_symbolic", "dd_domain_symbolic", "dd_domain_assembly"]
+           "dd_symbolic", "dd_domain_symbolic", "dd_domain_assembly", "dd_shard_plan"]
 
 
 def library_path() -> str:
@@ -117,6 +117,8 @@ def load(build_if_missing: bool = True):
                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.dd_symbolic.argtypes = [C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
+    lib.dd_shard_plan.argtypes = [C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
+                                  C.c_void_p, C.c_void_p]
     lib.dd_dense_solve_noalloc.argtypes = [C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64,
                                            C.c_void_p, C.c_int64, C.c_void_p]
     _lib = lib
@@ -252,9 +254,29 @@ def domain_assembly(indptr, indices, is_last=None, leaf_max: int = 256) -> dict:
             "a_col": ac[:nnz].copy()}
 
 
+def shard_plan(subdomains, n_dual: int, n_ranks: int, tree_parent=None, centroids=None) -> dict:
+    """Cut of the front tree into n_ranks subtrees (dd_shard_plan; host only):
+    the owner rank of every front and the root front of every rank's subtree."""
+    lib = load()
+    subs, opt, keep = _marshal(subdomains, tree_parent, centroids)
+    cap = 2 * len(subdomains) + 1
+    nf = C.c_int32(0)
+    front_rank = np.zeros(cap, np.int32)
+    rank_root = np.zeros(max(int(n_ranks), 1), np.int32)
+    _check(lib.dd_shard_plan(len(subdomains), subs, int(n_dual), C.byref(opt), int(n_ranks), cap, C.byref(nf),
+                             front_rank.ctypes.data, rank_root.ctypes.data), "dd_shard_plan")
+    del keep
+    return {"n_front": nf.value, "front_rank": front_rank[:nf.value].copy(), "rank_root": rank_root.copy()}
+
+
 def symbolic_problem(p) -> dict:
     """symbolic() for a femgen.Problem, with its domain tree."""
     return symbolic(_problem_subs(p), p.n_dual, tree_parent=p.rcb.parent)
+
+
+def shard_plan_problem(p, n_ranks: int) -> dict:
+    """shard_plan() for a femgen.Problem, with its domain tree."""
+    return shard_plan(_problem_subs(p), p.n_dual, n_ranks, tree_parent=p.rcb.parent)
 
 
 class Solver:
@@ -417,5 +439,5 @@ def unstack(problem, u: np.ndarray):
 
 
 __all__ = ["Solver", "DDError", "load", "library_path", "stacked_loads", "unstack", "symbolic", "symbolic_problem",
-           "domain_symbolic", "domain_assembly",
+           "domain_symbolic", "domain_assembly", "shard_plan", "shard_plan_problem",
            "EXPORTS", "PRECISION"]
