@@ -493,7 +493,8 @@ def ours_arm(args):
         "vs_baseline": None, "dtype": "c64+f64" if args.precision == "mixed" else "c128", "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload][1], "form": args.precision, "n_dofs": p.n,
                    "n_domains": p.n_sub, "n_duals": p.n_dual, "nrhs": p.nrhs, "pivoting": args.pivoting,
-                   "update_panels": args.update_panels, "schedule": main.get("schedule"),
+                   "update_panels": (main.get("schedule") or {}).get("update_panels", args.update_panels),
+                   "schedule": main.get("schedule"),
                    "sparse_min": args.sparse_min,
                    "refine_tol": args.refine_tol,
                    "l2": "inputs larger than L2: the front pool is far larger than the 129 MB L2",

@@ -79,7 +79,8 @@ typedef struct {
 typedef struct {
   int32_t precision;        /* DD_PREC_FP64: every step in FP64 complex.
                                DD_PREC_MIXED: complex64 factors and solves,
-                               FP64 pivot blocks of the auxiliary matrix and
+                               wide pivot blocks of the auxiliary matrix (double-float,
+                               an FP32 pair of about 48 bits; FP64 with pivoting) and
                                FP64 iterative refinement on the arrowhead system. */
   double refine_tol;        /* MIXED: stop when |du|/|u| <= refine_tol, or when the error left
                                after the update, estimated from the contraction of successive

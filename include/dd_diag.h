@@ -23,6 +23,23 @@ extern "C" {
  * `cuda_stream` (NULL = legacy default stream) and synchronises it. */
 int dd_selftest_wait_timeout(void* cuda_stream);
 
+/* Factor one 64 x 64 diagonal tile with the mixed form's diagonal kernel, as
+ * a separator front of the auxiliary matrix would be (Section II: the block
+ * LDL^T of the auxiliary matrix; unpivoted): the two 32 x 32 pivot blocks in
+ * FP32 (precision 0), double-float (1: an FP32 pair, about 48 bits, the
+ * library's choice for unpivoted separator fronts) or FP64 (2), the rest in
+ * FP32.  tile: host, 64 x 64 complex64 interleaved (re, im), row-major, lower
+ * triangle read.  out_tile (host, same layout): the factor, D on the
+ * diagonal and L strictly below it (unit diagonal implied); the upper
+ * triangle is left as it came in.  out_linv (host, same layout): L^-1, lower
+ * triangular, zeros above.  Diagnostics for testing the pivot-block
+ * precision; allocates and frees a few KB of device memory, runs on
+ * `cuda_stream` (NULL = legacy default stream) and synchronises it.
+ * Returns DD_OK, DD_ERR_SINGULAR_PIVOT (a zero or non-finite pivot),
+ * DD_ERR_INVALID_ARG, DD_ERR_OOM or DD_ERR_CUDA. */
+int dd_selftest_pivot_tile(const float* tile, int32_t precision, float* out_tile, float* out_linv,
+                           void* cuda_stream);
+
 /* The symbolic analysis of dd_setup alone (Section II: the auxiliary matrix
  * is factored after a symbolic factorization on the clique graph of the
  * domain interfaces), on the host, touching no device.  Same inputs and

@@ -74,7 +74,7 @@ class Schedule(C.Structure):
 EXPORTS = ["dd_default_options", "dd_setup", "dd_set_values", "dd_factor", "dd_solve", "dd_solve_subset", "dd_get_schur",
            "dd_set_schedule", "dd_autotune",
            "dd_get_stats", "dd_strerror", "dd_free", "dd_dense_solve_noalloc", "dd_selftest_wait_timeout",
-           "dd_symbolic", "dd_domain_symbolic", "dd_domain_assembly", "dd_shard_plan"]
+           "dd_symbolic", "dd_domain_symbolic", "dd_domain_assembly", "dd_shard_plan", "dd_selftest_pivot_tile"]
 
 
 def library_path() -> str:
@@ -109,6 +109,7 @@ def load(build_if_missing: bool = True):
     lib.dd_free.argtypes = [C.c_void_p]
     lib.dd_free.restype = None
     lib.dd_selftest_wait_timeout.argtypes = [C.c_void_p]
+    lib.dd_selftest_pivot_tile.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.dd_domain_symbolic.argtypes = [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                        C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
@@ -252,6 +253,23 @@ def domain_assembly(indptr, indices, is_last=None, leaf_max: int = 256) -> dict:
     return {"n_front": k, "parent": parent[:k].copy(), "ne": ne[:k].copy(), "rows_ptr": rows_ptr[:k + 1].copy(),
             "rows": rows[:m].copy(), "ea_map": ea[:m].copy(), "a_front": af[:nnz].copy(), "a_row": ar[:nnz].copy(),
             "a_col": ac[:nnz].copy()}
+
+
+def pivot_tile(tile, precision: str = "dfloat"):
+    """One 64 x 64 complex diagonal tile through the mixed form's diagonal
+    kernel (dd_selftest_pivot_tile; needs a GPU): pivot blocks in "fp32",
+    "dfloat" (double-float) or "fp64".  Returns (factor, L^-1) as complex64
+    arrays: D on the factor's diagonal, L strictly below."""
+    lib = load()
+    a = np.ascontiguousarray(tile, dtype=np.complex64)
+    if a.shape != (64, 64):
+        raise ValueError("a 64 x 64 tile")
+    out = a.copy()
+    linv = np.zeros_like(a)
+    code = {"fp32": 0, "dfloat": 1, "fp64": 2}[precision]
+    _check(lib.dd_selftest_pivot_tile(a.ctypes.data, code, out.ctypes.data, linv.ctypes.data, None),
+           "dd_selftest_pivot_tile")
+    return out, linv
 
 
 def shard_plan(subdomains, n_dual: int, n_ranks: int, tree_parent=None, centroids=None) -> dict:
@@ -439,5 +457,5 @@ def unstack(problem, u: np.ndarray):
 
 
 __all__ = ["Solver", "DDError", "load", "library_path", "stacked_loads", "unstack", "symbolic", "symbolic_problem",
-           "domain_symbolic", "domain_assembly", "shard_plan", "shard_plan_problem",
+           "domain_symbolic", "domain_assembly", "shard_plan", "shard_plan_problem", "pivot_tile",
            "EXPORTS", "PRECISION"]

@@ -85,6 +85,7 @@ struct Level {
   std::vector<QuadRange> quads;   // four-panel updates of steps (0..3), (4..7), ... (tensor-core path)
   bool ahead = false;             // one-step look-ahead on a second stream
   int max_child_nu = 0;
+  int max_ld = 0;                 // largest separator front (pull assembly grid)
   int64_t fwd_off = 0, bwd_off = 0;   // solve tasks (forward by row tile, backward by column tile)
   int n_fwd = 0, n_bwd = 0;
   int upd_split = 0;   // separator levels: CTAs per backward task of the split update-row product
@@ -181,6 +182,9 @@ struct dd_handle {
   int64_t* d_btrow = nullptr;
   int8_t* d_btsign = nullptr;
   int32_t *d_upd = nullptr, *d_sep = nullptr, *d_maps = nullptr;
+  int32_t* d_imaps = nullptr;      // separator fronts: row -> child update row (-1: none), per child
+  int2* d_ztiles = nullptr;        // (front, tile row) of the fronts zeroed before each factorization
+  int64_t n_ztiles = 0;
   int32_t *d_level_ids = nullptr, *d_diag_ids = nullptr;
   Task *d_trsm = nullptr, *d_updt = nullptr;
   Task *d_fwd = nullptr, *d_bwd = nullptr;
@@ -731,7 +735,7 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
   std::vector<int8_t> h_bsign, h_blsign;
   std::vector<double2> h_val;
   std::vector<LeafDev> h_leaves(n_sub);
-  std::vector<int32_t> h_upd, h_sep, h_maps;
+  std::vector<int32_t> h_upd, h_sep, h_maps, h_imaps;
   std::vector<std::vector<int32_t>> sp_sep(n_front_all), sp_upd(n_front_all);   // sparse-domain fronts
   h->leaf_duals.resize(n_sub);
   h->leaf_vec_off.resize(n_sub);
@@ -971,6 +975,21 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
       for (int d : sep[v]) rowpos[d] = -1;
       for (int d : upd[v]) rowpos[d] = -1;
     }
+    // inverse maps of the separator fronts (pull assembly): row here -> child
+    // update row, -1 where the child has none
+    h_imaps.clear();
+    for (int v = 0; v < n_front_all; ++v) {
+      FrontDev& F = h->fronts[v];
+      F.imap_off[0] = F.imap_off[1] = -1;
+      if (F.kind != 1) continue;
+      for (int slot = 0; slot < 2; ++slot) {
+        const int c = F.child[slot];
+        if (c < 0) continue;
+        F.imap_off[slot] = (int32_t)h_imaps.size();
+        h_imaps.insert(h_imaps.end(), (size_t)F.ld, -1);
+        for (int a = 0; a < h->fronts[c].nu; ++a) h_imaps[(size_t)F.imap_off[slot] + h_maps[(size_t)F.map_off[slot] + a]] = a;
+      }
+    }
     // the B rows of each domain front in their new order
     h->leaf_upd.assign(n_sub, {});
     size_t q0 = 0;
@@ -998,6 +1017,15 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
   }
   h->pool_bytes = (size_t)off * h->elem;
   h->rows_total = roff;
+  // lower-triangular tiles zeroed before each factorization: every front but
+  // the separator fronts, which the pull assembly writes in full; long tile
+  // rows first
+  std::vector<int2> h_ztiles;
+  for (int x = 0; x < n_front_all; ++x)
+    if (h->fronts[x].kind != 1)
+      for (int t = 0; t < h->fronts[x].ld / T; ++t) h_ztiles.push_back(make_int2(x, t));
+  std::stable_sort(h_ztiles.begin(), h_ztiles.end(), [](const int2& a, const int2& b) { return a.y > b.y; });
+  h->n_ztiles = (int64_t)h_ztiles.size();
   h->n_tiles = toff;
   int max_h = 0;
   for (int x = 0; x < n_front_all; ++x) max_h = std::max(max_h, height[x]);
@@ -1057,6 +1085,7 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
     h_level_ids.insert(h_level_ids.end(), L.ids.begin(), L.ids.end());
     int max_steps = 0;
     for (int f : L.ids) {
+      if (h->fronts[f].kind == 1) L.max_ld = std::max(L.max_ld, h->fronts[f].ld);
       max_steps = std::max(max_steps, h->fronts[f].ne_pad / T);
       for (int slot = 0; slot < 2; ++slot) {
         const int c = h->fronts[f].child[slot];
@@ -1364,6 +1393,8 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
   DD_CUDA(A.upload(&h->d_upd, h_upd, s));
   DD_CUDA(A.upload(&h->d_sep, h_sep, s));
   DD_CUDA(A.upload(&h->d_maps, h_maps, s));
+  DD_CUDA(A.upload(&h->d_imaps, h_imaps, s));
+  DD_CUDA(A.upload(&h->d_ztiles, h_ztiles, s));
   DD_CUDA(A.upload(&h->d_level_ids, h_level_ids, s));
   DD_CUDA(A.upload(&h->d_diag_ids, h_diag, s));
   DD_CUDA(A.upload(&h->d_trsm, h_trsm, s));
@@ -1491,7 +1522,7 @@ static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& n
       h->stats.kernel_launches[cls]++;
     }
   };
-  ddk::launch_zero(h->pool, h->pool_bytes, s);
+  ddk::launch_zero_lower(h->pool, h->elem, h->d_fronts, h->d_ztiles, h->n_ztiles, s);
   if (h->d_counters) ddk::launch_zero(h->d_counters, sizeof(int) * h->n_counters, s);
   int next_counter = 0;
   DD_CUDA(mark(DD_K_INIT, true));
@@ -1507,16 +1538,19 @@ static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& n
     const int n = (int)L.ids.size();
     if (l > 0) {
       DD_CUDA(mark(DD_K_ASSEMBLE, true));
+      ddk::launch_assemble(p, h->pool, h->d_fronts, ids, n, h->d_imaps, L.max_ld, s);
       ddk::launch_node_init(p, h->pool, h->d_fronts, ids, n, s);
       ddk::launch_extend_add(p, h->pool, h->d_fronts, ids, n, 0, h->d_maps, L.max_child_nu, s);
       ddk::launch_extend_add(p, h->pool, h->d_fronts, ids, n, 1, h->d_maps, L.max_child_nu, s);
       DD_CUDA(mark(DD_K_ASSEMBLE, false));
+      count(DD_K_ASSEMBLE, L.max_ld > 0 ? n : 0);
       count(DD_K_ASSEMBLE, n);
       count(DD_K_ASSEMBLE, n);
       count(DD_K_ASSEMBLE, n);
     }
-    // mixed form: FP64 pivot blocks for the auxiliary matrix's separator fronts,
-    // FP32 for the fronts that eliminate domain unknowns
+    // mixed form: wide pivot blocks (double-float, or FP64 with pivoting) for the
+    // auxiliary matrix's separator fronts, FP32 for the fronts that eliminate
+    // domain unknowns
     const int diag64 = L.n_aux == 0 ? 0 : (L.n_aux == (int)L.ids.size() ? 1 : 2);
     // one-step look-ahead on levels with few fronts: the main stream updates
     // only the next panel columns and factors those panels, while the second
@@ -2199,6 +2233,51 @@ int dd_selftest_wait_timeout(void* cuda_stream) {
       code = host.code == 8 ? DD_ERR_TIMEOUT : (host.code == 0 ? DD_OK : DD_ERR_CUDA);
   }
   cudaFree(flag);
+  cudaFree(st);
+  return code;
+}
+
+int dd_selftest_pivot_tile(const float* tile, int32_t precision, float* out_tile, float* out_linv,
+                           void* cuda_stream) {
+  if (!tile || !out_tile || !out_linv || precision < 0 || precision > 2) return DD_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  constexpr size_t kTile = (size_t)T * T * sizeof(float2);
+  float2* pool = nullptr;
+  float2* linv = nullptr;
+  FrontDev* fr = nullptr;
+  int32_t* fid = nullptr;
+  DevStatus* st = nullptr;
+  int code = DD_ERR_OOM;
+  if (cudaMalloc(&pool, kTile) == cudaSuccess && cudaMalloc(&linv, kTile) == cudaSuccess &&
+      cudaMalloc(&fr, sizeof(FrontDev)) == cudaSuccess && cudaMalloc(&fid, sizeof(int32_t)) == cudaSuccess &&
+      cudaMalloc(&st, sizeof(DevStatus)) == cudaSuccess) {
+    FrontDev F{};
+    F.ld = T;
+    F.ne = T;
+    F.ne_pad = T;
+    F.kind = 1;
+    F.sub = -1;
+    F.child[0] = F.child[1] = -1;
+    const int32_t zero = 0;
+    DevStatus host{};
+    code = DD_ERR_CUDA;
+    if (cudaMemcpyAsync(pool, tile, kTile, cudaMemcpyHostToDevice, s) == cudaSuccess &&
+        cudaMemcpyAsync(fr, &F, sizeof(F), cudaMemcpyHostToDevice, s) == cudaSuccess &&
+        cudaMemcpyAsync(fid, &zero, sizeof(zero), cudaMemcpyHostToDevice, s) == cudaSuccess &&
+        cudaMemsetAsync(st, 0, sizeof(DevStatus), s) == cudaSuccess) {
+      ddk::launch_diag_tile(precision, pool, fr, fid, st, linv, s);
+      if (cudaGetLastError() == cudaSuccess &&
+          cudaMemcpyAsync(out_tile, pool, kTile, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+          cudaMemcpyAsync(out_linv, linv, kTile, cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+          cudaMemcpyAsync(&host, st, sizeof(host), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+          cudaStreamSynchronize(s) == cudaSuccess)
+        code = host.code == 3 ? DD_ERR_SINGULAR_PIVOT : (host.code == 0 ? DD_OK : DD_ERR_CUDA);
+    }
+  }
+  cudaFree(pool);
+  cudaFree(linv);
+  cudaFree(fr);
+  cudaFree(fid);
   cudaFree(st);
   return code;
 }

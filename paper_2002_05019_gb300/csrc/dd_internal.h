@@ -37,6 +37,7 @@ struct FrontDev {
   int32_t sep_off;   // node / sparse-domain front: offset of the ne row ids of its own rows
   int32_t child[2];  // node: child fronts (-1 if absent)
   int32_t map_off[2];// node: offsets of the extend-add maps (child update row -> row here)
+  int32_t imap_off[2];// separator front: offsets of the inverse maps (row here -> child update row or -1)
   int32_t tile_off;  // offset of this front's per-tile ready flags (ld / DD_TILE of them)
   int32_t piv;       // 1: its diagonal tiles use restricted Bunch-Kaufman pivoting
   int64_t ws_off;    // mixed form: byte offset of this front's A operand images in the panel workspace
@@ -108,6 +109,10 @@ void launch_trsm(int prec, void* pool, const FrontDev* fronts, const Task* tasks
 // L_kk^{-1} (FP32, 64 x 64 per front id) for the panel product
 void launch_diag_mx(int diag_fp64, void* pool, const FrontDev* fronts, const int32_t* fids, int n, int k,
                     DevStatus* st, void* linv, cudaStream_t s, uint8_t* piv = nullptr);
+// one 64 x 64 mixed-form diagonal tile (front 0 of `front`, step 0), unpivoted:
+// prec 0 FP32 pivot blocks, 1 double-float, 2 FP64 (diagnostics)
+void launch_diag_tile(int prec, void* pool, const FrontDev* front, const int32_t* fid, DevStatus* st, void* linv,
+                      cudaStream_t s);
 // tensor != 0: the product with L_kk^{-1} on the tensor cores (tcgen05 3xTF32), else on the FP32 FMA pipes
 void launch_trsm_mx(void* pool, const FrontDev* fronts, const Task* tasks, int n, int k, DevStatus* st,
                     const void* linv, unsigned char* ws, cudaStream_t s, const uint8_t* piv = nullptr,
@@ -124,6 +129,14 @@ void launch_update(int prec, void* pool, const FrontDev* fronts, const Task* tas
                    cudaStream_t s);
 void launch_extend_add(int prec, void* pool, const FrontDev* fronts, const int32_t* node_ids, int n,
                        int slot, const int32_t* maps, int max_nu, cudaStream_t s);
+// lower-triangular tiles (tile row t: columns [0, 64 (t + 1))) of the listed
+// (front, tile row) pairs set to zero; elem = bytes per complex entry
+void launch_zero_lower(void* pool, int elem, const FrontDev* fronts, const int2* tiles, int64_t n, cudaStream_t s);
+// assembly of the separator fronts (kind 1) of a level by pulling their
+// children's trailing blocks: every entry of the lower-triangular tiles written
+// once (no zeroing, no read-modify-write); other fronts are skipped
+void launch_assemble(int prec, void* pool, const FrontDev* fronts, const int32_t* node_ids, int n,
+                     const int32_t* imaps, int max_ld, cudaStream_t s);
 
 // ---- solve --------------------------------------------------------------------
 void launch_rhs_leaf(int prec, void* rpool, const FrontDev* fronts, const LeafDev* leaves, int n_leaves,

@@ -9,7 +9,11 @@
 // Complex symmetric: plain transposes, no conjugation.  Fronts are stored
 // row-major (lower triangle), interleaved complex, double2 (FP64 form) or
 // float2 (mixed form).
+#include <algorithm>
+#include <type_traits>
+
 #include "dd_complex.cuh"
+#include "dd_dfloat.cuh"
 #include "dd_internal.h"
 #include "dd_pivot.cuh"
 #include "dd_tc.cuh"
@@ -341,6 +345,13 @@ __device__ void factor_pivot32_bk(float2* a, int jb, C* ap, C* w, C* w1, int* pe
   __syncthreads();
 }
 
+// the pivoting factorization where the precision supports it (FP32, FP64); the
+// double-float form serves unpivoted fronts only and never calls it
+template <typename C, typename CB>
+__device__ void factor_pivot32_any_bk(float2* a, int jb, C* ap, C* w, CB* w1, int* perm, CB* dsup, int* cnt) {
+  if constexpr (std::is_same<C, CB>::value) factor_pivot32_bk<C>(a, jb, ap, w, w1, perm, dsup, cnt);
+}
+
 // N = L^{-1} of the unit-lower 32 x 32 block jb of the tile, into the same
 // positions of the packed 64 x 64 li: 8 lanes per column, rows in order
 __device__ void inv_unit_lower32(const float2* a, int jb, float2* li) {
@@ -377,18 +388,22 @@ __global__ void __launch_bounds__(256, 1) k_diag_mx(float2* pool, const FrontDev
   __shared__ C rinv;
   __shared__ float2 lcol[PB];    // the scaled column of the current pivot, FP32, for N
   __shared__ float2 d1inv[PB];   // D1^{-1}: (D1^{-1} x)_c = d1inv[c] x_c + g1[c] x_{q1[c]}
-  // restricted Bunch-Kaufman (fronts that pivot): 2x2 column, permutation, 2x2 off-diagonals
-  __shared__ C w1[PB];
+  // restricted Bunch-Kaufman (fronts that pivot): 2x2 column, permutation, 2x2
+  // off-diagonals; in precision C, or FP64 (unused) for the double-float form,
+  // which serves unpivoted fronts only
+  constexpr bool kBK = !std::is_same<C, dfc>::value;
+  using CB = typename std::conditional<kBK, C, double2>::type;
+  __shared__ CB w1[PB];
   __shared__ float2 g1[PB];
   __shared__ int q1[PB];
   __shared__ int perm[T];
-  __shared__ C dsup[T];
+  __shared__ CB dsup[T];
   __shared__ int cnt[2];
   const int f = fids[blockIdx.x];
   const FrontDev F = fr[f];
   // sel 1: separator fronts of the auxiliary matrix only, 2: domain fronts only
   if ((sel == 1 && F.kind != 1) || (sel == 2 && F.kind == 1)) return;
-  const bool pv = piv != nullptr && F.piv != 0;
+  const bool pv = kBK && piv != nullptr && F.piv != 0;
   float2* base = pool + F.off + (int64_t)(k * T) * F.ld + k * T;
   for (int idx = threadIdx.x; idx < T * T; idx += blockDim.x) {
     const int i = idx / T, c = idx % T;
@@ -396,7 +411,7 @@ __global__ void __launch_bounds__(256, 1) k_diag_mx(float2* pool, const FrontDev
   }
   if (threadIdx.x < 2) cnt[threadIdx.x] = 0;
   __syncthreads();
-  if (pv) factor_pivot32_bk<C>(a, 0, ap, w, w1, perm, dsup, cnt);
+  if (pv) factor_pivot32_any_bk<C, CB>(a, 0, ap, w, w1, perm, dsup, cnt);
   else factor_pivot32<C>(a, 0, ap, w, lcol, &rinv, li);
   // D1^{-1} (from the precision-C factor while ap still holds it) and N11
   if (threadIdx.x < PB) {
@@ -467,7 +482,7 @@ __global__ void __launch_bounds__(256, 1) k_diag_mx(float2* pool, const FrontDev
   }
   __syncthreads();
   if (pv) {
-    factor_pivot32_bk<C>(a, PB, ap, w, w1, perm + PB, dsup + PB, cnt);
+    factor_pivot32_any_bk<C, CB>(a, PB, ap, w, w1, perm + PB, dsup + PB, cnt);
     // rows of L21 follow the interchanges of the second pivot block
     for (int idx = threadIdx.x; idx < PB * PB; idx += blockDim.x) {
       const int rr = idx / PB, c = idx % PB;
@@ -521,7 +536,7 @@ __global__ void __launch_bounds__(256, 1) k_diag_mx(float2* pool, const FrontDev
   }
   if (pv) {
     __syncthreads();
-    store_pivots<float2, C>(base, F.ld, perm, dsup, piv + ((int64_t)F.tile_off + k) * T);
+    store_pivots<float2, CB>(base, F.ld, perm, dsup, piv + ((int64_t)F.tile_off + k) * T);
     if (threadIdx.x == 0 && (cnt[0] | cnt[1])) {
       atomicAdd(&st->n_swap, (unsigned long long)cnt[0]);
       atomicAdd(&st->n_2x2, (unsigned long long)cnt[1]);
@@ -880,7 +895,7 @@ __global__ void __launch_bounds__(256) k_extend_add(S* pool, const FrontDev* fr,
                                                     const int32_t* maps) {
   const FrontDev P = fr[nodes[blockIdx.x]];
   const int c = P.child[slot];
-  if (c < 0) return;
+  if (c < 0 || P.kind == 1) return;   // separator fronts are assembled by k_assemble
   const FrontDev Cf = fr[c];
   const int a = blockIdx.y * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (a >= Cf.nu) return;
@@ -894,6 +909,67 @@ __global__ void __launch_bounds__(256) k_extend_add(S* pool, const FrontDev* fr,
     const int hi = ra > rb ? ra : rb, lo = ra > rb ? rb : ra;
     S* p = dst + (int64_t)hi * P.ld + lo;
     *p = cadd(*p, v);
+  }
+}
+
+// Assembly of a separator front by pulling (Section II: the auxiliary
+// matrix's blocks are sums of the children's Schur complements): entry (i, j)
+// of the lower-triangular tiles is the sum over the children of their
+// trailing-block entry at the inverse-mapped rows (child 0 first, then child 1,
+// the order of the extend-add), 1 on the padding diagonal, 0 elsewhere.  The
+// maps are increasing, so j <= i reads the children's lower triangles.  A warp
+// per row, rows of 8 per CTA, grid-strided over the front.
+template <typename S>
+__global__ void __launch_bounds__(256) k_assemble(S* pool, const FrontDev* fr, const int32_t* nodes,
+                                                  const int32_t* imaps) {
+  const FrontDev P = fr[nodes[blockIdx.x]];
+  if (P.kind != 1) return;
+  const int lane = threadIdx.x & 31;
+  for (int i = blockIdx.y * 8 + (threadIdx.x >> 5); i < P.ld; i += gridDim.y * 8) {
+    const S* src[2] = {nullptr, nullptr};
+    const int32_t* inv[2] = {nullptr, nullptr};
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const int c = P.child[s];
+      if (c < 0) continue;
+      const int32_t* m = imaps + P.imap_off[s];
+      const int mi = m[i];
+      if (mi < 0) continue;
+      const FrontDev C = fr[c];
+      inv[s] = m;
+      src[s] = pool + C.off + (int64_t)(C.ne_pad + mi) * C.ld + C.ne_pad;
+    }
+    S* dst = pool + P.off + (int64_t)i * P.ld;
+    const int jend = min(P.ld, (i / T + 1) * T);
+    const bool pad = i >= P.ne && i < P.ne_pad;
+    for (int j = lane; j < jend; j += 32) {
+      S v = czero<S>();
+      if (j <= i) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+          if (src[s]) {
+            const int mj = inv[s][j];
+            if (mj >= 0) v = cadd(v, src[s][mj]);
+          }
+        if (pad && j == i) v = cmake<S>(1, 0);
+      }
+      dst[j] = v;
+    }
+  }
+}
+
+// tile row t of front f: rows [64 t, 64 t + 64), columns [0, 64 (t + 1)), in
+// 16-byte stores (front offsets and row strides are multiples of 64 entries)
+__global__ void __launch_bounds__(256) k_zero_lower(unsigned char* pool, int elem, const FrontDev* fr,
+                                                    const int2* tiles) {
+  const int2 ft = tiles[blockIdx.x];
+  const FrontDev F = fr[ft.x];
+  const int64_t row_bytes = (int64_t)F.ld * elem;
+  const int vec = (ft.y + 1) * T * elem / 16;
+  unsigned char* base = pool + ((int64_t)F.off + (int64_t)ft.y * T * F.ld) * elem;
+  for (int64_t idx = threadIdx.x; idx < (int64_t)T * vec; idx += blockDim.x) {
+    const int r = (int)(idx / vec), v = (int)(idx % vec);
+    reinterpret_cast<uint4*>(base + r * row_bytes)[v] = make_uint4(0u, 0u, 0u, 0u);
   }
 }
 
@@ -912,6 +988,18 @@ void set_trsm_attr() {
 
 void launch_zero(void* p, size_t bytes, cudaStream_t s) {
   if (bytes) cudaMemsetAsync(p, 0, bytes, s);
+}
+
+void launch_zero_lower(void* pool, int elem, const FrontDev* fronts, const int2* tiles, int64_t n, cudaStream_t s) {
+  if (n > 0) k_zero_lower<<<(unsigned)n, 256, 0, s>>>((unsigned char*)pool, elem, fronts, tiles);
+}
+
+void launch_assemble(int prec, void* pool, const FrontDev* fronts, const int32_t* node_ids, int n,
+                     const int32_t* imaps, int max_ld, cudaStream_t s) {
+  if (n <= 0 || max_ld <= 0) return;
+  dim3 grid(n, std::min((max_ld + 7) / 8, 32768));
+  if (prec == 0) k_assemble<double2><<<grid, 256, 0, s>>>((double2*)pool, fronts, node_ids, imaps);
+  else k_assemble<float2><<<grid, 256, 0, s>>>((float2*)pool, fronts, node_ids, imaps);
 }
 
 void launch_leaf_init(int prec, void* pool, const FrontDev* fronts, const LeafDev* leaves, int n_leaves,
@@ -951,11 +1039,22 @@ void launch_diag_mx(int diag_fp64, void* pool, const FrontDev* fronts, const int
                     DevStatus* st, void* linv, cudaStream_t s, uint8_t* piv) {
   if (n <= 0) return;
   // diag_fp64: 0 FP32 pivot blocks, 1 FP64, 2 by front: FP64 for the auxiliary
-  // matrix's separator fronts, FP32 for domain fronts (two launches)
-  if (diag_fp64 == 1 || diag_fp64 == 2)
+  // matrix's separator fronts, FP32 for domain fronts (two launches).  The
+  // unpivoted FP64 blocks run in double-float arithmetic (about 48 bits, on
+  // the FP32 pipes); restricted Bunch-Kaufman pivoting keeps true FP64.
+  if ((diag_fp64 == 1 || diag_fp64 == 2) && piv)
     k_diag_mx<double2><<<n, 256, 0, s>>>((float2*)pool, fronts, fids, k, st, (float2*)linv, piv, diag_fp64 == 2 ? 1 : 0);
+  if ((diag_fp64 == 1 || diag_fp64 == 2) && !piv)
+    k_diag_mx<dfc><<<n, 256, 0, s>>>((float2*)pool, fronts, fids, k, st, (float2*)linv, piv, diag_fp64 == 2 ? 1 : 0);
   if (diag_fp64 == 0 || diag_fp64 == 2)
     k_diag_mx<float2><<<n, 256, 0, s>>>((float2*)pool, fronts, fids, k, st, (float2*)linv, piv, diag_fp64 == 2 ? 2 : 0);
+}
+
+void launch_diag_tile(int prec, void* pool, const FrontDev* front, const int32_t* fid, DevStatus* st, void* linv,
+                      cudaStream_t s) {
+  if (prec == 0) k_diag_mx<float2><<<1, 256, 0, s>>>((float2*)pool, front, fid, 0, st, (float2*)linv, nullptr, 0);
+  if (prec == 1) k_diag_mx<dfc><<<1, 256, 0, s>>>((float2*)pool, front, fid, 0, st, (float2*)linv, nullptr, 0);
+  if (prec == 2) k_diag_mx<double2><<<1, 256, 0, s>>>((float2*)pool, front, fid, 0, st, (float2*)linv, nullptr, 0);
 }
 
 void launch_trsm_mx(void* pool, const FrontDev* fronts, const Task* tasks, int n, int k, DevStatus* st,
