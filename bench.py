@@ -410,12 +410,23 @@ def form_summary(p, f, ws):
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_update_tc_traffic.md")
 
 
+def kernel_sources_sha() -> str:
+    """Hash of the sources that decide the update kernel's memory traffic: the
+    kernel (kernels_tc.cu) and the panel kernels writing its operand images
+    (kernels_factor.cu)."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("kernels_tc.cu", "kernels_factor.cu"):
+        with open(os.path.join(ROOT, "paper_2002_05019_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def update_traffic(flops_per_launch: float):
     """DRAM bytes per launch of the tensor-core update, scaled from the ncu
     counters in profiles/ (bytes per algorithmic flop, over every launch of one
     factorization) by the launch's algorithmic flops; None when no summary
-    exists or the kernel source changed since the counters were taken."""
-    import hashlib
+    exists or the kernel sources changed since the counters were taken."""
     try:
         with open(TRAFFIC_FILE) as fh:
             txt = fh.read()
@@ -424,12 +435,9 @@ def update_traffic(flops_per_launch: float):
     vals = {}
     for ln in txt.splitlines():
         parts = ln.strip().strip("`").split()
-        if len(parts) == 2 and parts[0] in ("bytes_per_flop", "kernels_tc_sha256"):
+        if len(parts) == 2 and parts[0] in ("bytes_per_flop", "kernels_sha256"):
             vals[parts[0]] = parts[1]
-    src = os.path.join(ROOT, "paper_2002_05019_gb300", "csrc", "kernels_tc.cu")
-    with open(src, "rb") as fh:
-        sha = hashlib.sha256(fh.read()).hexdigest()[:16]
-    if "bytes_per_flop" not in vals or vals.get("kernels_tc_sha256") != sha:
+    if "bytes_per_flop" not in vals or vals.get("kernels_sha256") != kernel_sources_sha():
         return None, None
     return float(vals["bytes_per_flop"]) * flops_per_launch, float(vals["bytes_per_flop"])
 

@@ -50,8 +50,9 @@ struct FrontDev {
 //   A image (rows of L): within a piece, for each group of 16 tile rows, their
 //     real parts then their imaginary parts (piece row 32 (r / 16) + r % 16 and
 //     + 16), so the two parts of a row land in one TMEM sub-partition;
-//   B image (rows of W = L D): within a piece, the 64 real rows then the 64
-//     imaginary rows.
+//   B image (rows of W = L D, fronts that pivot only): the same layout.
+// Unpivoted fronts write only the A image, of M = L D^(1/2), which the update
+// reads as both operands (L_i D L_j^T = M_i M_j^T).
 #define DD_TC_ATOM 16384
 #define DD_TC_ATILE (2 * 2 * DD_TC_ATOM)
 #define DD_TC_BTILE (2 * 2 * DD_TC_ATOM)

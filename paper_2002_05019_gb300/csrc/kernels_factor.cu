@@ -33,29 +33,42 @@ __device__ __forceinline__ void put_img(unsigned char* base, int row, int k, flo
 }
 
 template <typename S>
-__device__ __forceinline__ void write_images(unsigned char*, const FrontDev&, int, int, S, S) {}
-// mixed form: A image of L_ik and B image of W_ik = L_ik D_k for the tensor-core update
+__device__ __forceinline__ void write_images(unsigned char*, const FrontDev&, int, int, S, S, bool) {}
+// mixed form: the operand images of the tensor-core update.  Unpivoted
+// fronts: one image of M_ik = L_ik D_k^(1/2) serves as both operands
+// (L_i D L_j^T = M_i M_j^T); fronts that pivot (2 x 2 blocks in D): the A image
+// of L_ik and the B image of W_ik = L_ik D_k.  Both images use the A layout.
 template <>
-__device__ __forceinline__ void write_images<float2>(unsigned char* ws, const FrontDev& F, int ti, int rc, float2 L,
-                                                     float2 W) {
+__device__ __forceinline__ void write_images<float2>(unsigned char* ws, const FrontDev& F, int ti, int rc, float2 va,
+                                                     float2 vb, bool dual) {
   const int r = rc >> 6, p = rc & 63;              // row of the tile, K index
   const int a = p >> 5, kk = p & 31;
-  const int ra = (r >> 4) * 32 + (r & 15);         // A piece row of the real part (imaginary: + 16)
+  const int ra = (r >> 4) * 32 + (r & 15);         // piece row of the real part (imaginary: + 16)
   unsigned char* Ab = ws + F.ws_off + (int64_t)ti * DD_TC_ATILE;
-  unsigned char* Bb = ws + F.ws_boff + (int64_t)ti * DD_TC_BTILE;
   float h, l;
-  split_tf32(L.x, h, l);
+  split_tf32(va.x, h, l);
   put_img(Ab + (0 * 2 + a) * DD_TC_ATOM, ra, kk, h);
   put_img(Ab + (1 * 2 + a) * DD_TC_ATOM, ra, kk, l);
-  split_tf32(L.y, h, l);
+  split_tf32(va.y, h, l);
   put_img(Ab + (0 * 2 + a) * DD_TC_ATOM, ra + 16, kk, h);
   put_img(Ab + (1 * 2 + a) * DD_TC_ATOM, ra + 16, kk, l);
-  split_tf32(W.x, h, l);
-  put_img(Bb + (0 * 2 + a) * DD_TC_ATOM, r, kk, h);
-  put_img(Bb + (1 * 2 + a) * DD_TC_ATOM, r, kk, l);
-  split_tf32(W.y, h, l);
-  put_img(Bb + (0 * 2 + a) * DD_TC_ATOM, r + 64, kk, h);
-  put_img(Bb + (1 * 2 + a) * DD_TC_ATOM, r + 64, kk, l);
+  if (!dual) return;
+  unsigned char* Bb = ws + F.ws_boff + (int64_t)ti * DD_TC_BTILE;
+  split_tf32(vb.x, h, l);
+  put_img(Bb + (0 * 2 + a) * DD_TC_ATOM, ra, kk, h);
+  put_img(Bb + (1 * 2 + a) * DD_TC_ATOM, ra, kk, l);
+  split_tf32(vb.y, h, l);
+  put_img(Bb + (0 * 2 + a) * DD_TC_ATOM, ra + 16, kk, h);
+  put_img(Bb + (1 * 2 + a) * DD_TC_ATOM, ra + 16, kk, l);
+}
+
+// a square root w of z, w^2 = z (principal branch: for Re z >= 0,
+// w = (t, Im z / 2t), else (|Im z| / 2t, sign(Im z) t), t = sqrt((|z| + |Re z|) / 2))
+__device__ __forceinline__ float2 csqrt_f(float2 z) {
+  const float t = sqrtf(0.5f * (hypotf(z.x, z.y) + fabsf(z.x)));
+  if (t == 0.f) return make_float2(0.f, 0.f);
+  if (z.x >= 0.f) return make_float2(t, 0.5f * z.y / t);
+  return make_float2(0.5f * fabsf(z.y) / t, copysignf(t, z.y));
 }
 
 __device__ void status_pivot(DevStatus* st, int front, int row) {
@@ -566,6 +579,7 @@ __global__ void __launch_bounds__(256) k_trsm_mx(float2* pool, const FrontDev* f
   float2 (*Bs)[T + 1] = As + KC;
   float2 (*Xs)[T + 1] = As;
   __shared__ float2 rinv[T];
+  __shared__ float2 rsq[T];      // unpivoted: a square root of 1 / d_p (image scaling D^(-1/2))
   __shared__ float2 g1[T];
   __shared__ int qc[T];
   __shared__ int perm[T];
@@ -589,6 +603,7 @@ __global__ void __launch_bounds__(256) k_trsm_mx(float2* pool, const FrontDev* f
       perm[p] = piv[((int64_t)F.tile_off + k) * T + p];
     } else {
       rinv[p] = cdiv(make_float2(1.f, 0.f), Dk[(int64_t)p * (ld + 1)]);
+      rsq[p] = csqrt_f(rinv[p]);
       perm[p] = p;
     }
   }
@@ -637,7 +652,8 @@ __global__ void __launch_bounds__(256) k_trsm_mx(float2* pool, const FrontDev* f
       mx = fmaxf(mx, x.x * x.x + x.y * x.y);
       const float2 lv = pv ? cfma(Xs[rr][qc[p]], g1[p], cmul(x, rinv[p])) : cmul(x, rinv[p]);
       Aik[(int64_t)rr * ld + p] = lv;
-      if (ws) write_images<float2>(ws, F, t.i - k - 1, rr * T + p, lv, x);
+      // unpivoted: M = X D^(-1/2) = L D^(1/2) serves as both operand images
+      if (ws) write_images<float2>(ws, F, t.i - k - 1, rr * T + p, pv ? lv : cmul(x, rsq[p]), x, pv);
     }
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0 && mx > 0.f && isfinite(mx)) atomic_max_pos(&st->max_abs_l, sqrt((double)mx));
@@ -659,6 +675,7 @@ __global__ void __launch_bounds__(256, 1) k_trsm_tc(float2* pool, const FrontDev
   unsigned char* imgB = smem + tc::kImage / 2;
   float2 (*Xs)[T + 1] = reinterpret_cast<float2 (*)[T + 1]>(smem);   // after the product
   __shared__ float2 rinv[T];
+  __shared__ float2 rsq[T];      // unpivoted: a square root of 1 / d_p (image scaling D^(-1/2))
   __shared__ float2 g1[T];
   __shared__ int qc[T];
   __shared__ int perm[T];
@@ -695,6 +712,7 @@ __global__ void __launch_bounds__(256, 1) k_trsm_tc(float2* pool, const FrontDev
       perm[p] = piv[((int64_t)F.tile_off + k) * T + p];
     } else {
       rinv[p] = cdiv(make_float2(1.f, 0.f), Dk[(int64_t)p * (ld + 1)]);
+      rsq[p] = csqrt_f(rinv[p]);
       perm[p] = p;
     }
   }
@@ -743,7 +761,8 @@ __global__ void __launch_bounds__(256, 1) k_trsm_tc(float2* pool, const FrontDev
     mx = fmaxf(mx, x.x * x.x + x.y * x.y);
     const float2 lv = pv ? cfma(Xs[rr][qc[p]], g1[p], cmul(x, rinv[p])) : cmul(x, rinv[p]);
     Aik[(int64_t)rr * ld + p] = lv;
-    if (ws) write_images<float2>(ws, F, t.i - k - 1, idx, lv, x);
+    // unpivoted: M = X D^(-1/2) = L D^(1/2) serves as both operand images
+    if (ws) write_images<float2>(ws, F, t.i - k - 1, idx, pv ? lv : cmul(x, rsq[p]), x, pv);
   }
   for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   if ((threadIdx.x & 31) == 0 && mx > 0.f && isfinite(mx)) atomic_max_pos(&st->max_abs_l, sqrt((double)mx));
@@ -803,7 +822,7 @@ __global__ void __launch_bounds__(256) k_trsm(S* pool, const FrontDev* fr, const
     mx = fmax(mx, cabs2d(x));
     const S lv = pv ? cfma(X[qc[p] * (T + 1) + rr], g1[p], cmul(x, rinv[p])) : cmul(x, rinv[p]);
     Aik[(int64_t)rr * F.ld + p] = lv;
-    if (ws) write_images<S>(ws, F, t.i - k - 1, idx, lv, x);
+    if (ws) write_images<S>(ws, F, t.i - k - 1, idx, lv, x, true);
   }
   // block max of |L D| for the growth statistic
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));

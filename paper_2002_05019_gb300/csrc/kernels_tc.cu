@@ -8,10 +8,12 @@
 //   * the complex product as one real GEMM: the A operand stacks the real and
 //     imaginary rows of L (for each group of 16 rows, Re rows then Im rows, so
 //     both parts of a row of C sit in the same TMEM sub-partition), the B
-//     operand the real and imaginary rows of W = L D of both column tiles;
-//     the accumulator holds [Re L; Im L] [Re W | Im W]^T and the epilogue
-//     forms Re = Re L Re W - Im L Im W, Im = Re L Im W + Im L Re W with
-//     lane shuffles;
+//     operand the real and imaginary rows of W = L D of both column tiles in
+//     the same layout; the accumulator holds [Re L; Im L] [Re W | Im W]^T and
+//     the epilogue forms Re = Re L Re W - Im L Im W, Im = Re L Im W + Im L Re W
+//     with lane shuffles.  For unpivoted fronts both operands are one image of
+//     M = L D^(1/2) (L_i D L_j^T = M_i M_j^T), so the panel writes half the
+//     image bytes;
 //   * 3xTF32 split for FP32-class accuracy: X Y^T ~ Xh Yh^T + Xh Yl^T + Xl Yh^T;
 //   * operands are the pre-split, 128B-swizzled K-major images written by the
 //     panel kernel, streamed into shared memory by bulk asynchronous copies
@@ -162,11 +164,22 @@ __device__ __forceinline__ void epilogue_role(float2* pool, const FrontDev* fr, 
         if (!(t.pad & (1 << ct))) continue;
 #pragma unroll 1
         for (int hf = 0; hf < 2; ++hf) {
-          uint32_t xr[32], xi[32];   // this lane's row times [Re W] and [Im W], 32 columns
-          const uint32_t ta = tmem + ab * kAccCols + ((uint32_t)(sub * 32) << 16) + ct * 128 + hf * 32;
-          tmem_ld32(ta, xr);
-          tmem_ld32(ta + 64, xi);
+          // B rows in the A layout: per 16 rows of W, 16 real columns then 16
+          // imaginary ones, so columns 64 hf .. 64 hf + 63 of the tile hold
+          // W rows 32 hf .. 32 hf + 31 as (Re 0-15, Im 0-15, Re 16-31, Im 16-31)
+          uint32_t u[32], v[32];
+          const uint32_t ta = tmem + ab * kAccCols + ((uint32_t)(sub * 32) << 16) + ct * 128 + hf * 64;
+          tmem_ld32(ta, u);
+          tmem_ld32(ta + 32, v);
           asm volatile("tcgen05.wait::ld.sync.aligned;");
+          uint32_t xr[32], xi[32];   // this lane's row times [Re W] and [Im W], 32 columns
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            xr[c] = u[c];
+            xi[c] = u[16 + c];
+            xr[16 + c] = v[c];
+            xi[16 + c] = v[16 + c];
+          }
           // lanes < 16 (Re L) keep columns 0-15 and send 16-31; lanes >= 16 (Im L) the reverse
 #pragma unroll
           for (int c = 0; c < 16; ++c) {
@@ -266,7 +279,8 @@ __global__ void __launch_bounds__(192, 1) k_update_tc(float2* pool, const FrontD
           const int p = k + pp;
           const unsigned char* w = ws.p[pp];
           const unsigned char* gA = w + F.ws_off + (int64_t)(t.i - p - 1) * DD_TC_ATILE;
-          const unsigned char* gB = w + F.ws_boff + (int64_t)(t.j - p - 1) * DD_TC_BTILE;
+          // unpivoted fronts: the one image of M = L D^(1/2) is both operands
+          const unsigned char* gB = w + (F.piv ? F.ws_boff : F.ws_off) + (int64_t)(t.j - p - 1) * DD_TC_BTILE;
           for (int a = 0; a < 2; ++a, ++u) {
             const int sidx = u % kStages;
             if (!mbar_wait(b_empty0 + 8 * sidx, ((u / kStages) & 1) ^ 1)) { fail = 1; break; }
