@@ -1048,8 +1048,10 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
         const int64_t ntr = F.ld / T - 1;  // trailing tiles at the first step
         F.ws_off = w;
         w += ntr * (int64_t)DD_TC_ATILE;
-        F.ws_boff = w;
-        w += ntr * (int64_t)DD_TC_BTILE;
+        // a B image (W = L D) only for fronts that pivot; the others' one
+        // image of M = L D^(1/2) serves as both operands
+        F.ws_boff = F.piv ? w : F.ws_off;
+        if (F.piv) w += ntr * (int64_t)DD_TC_BTILE;
       }
       L.ahead = L.ids.size() <= (size_t)kAheadMaxFronts;   // may look ahead (image slots 2, 3)
       need = std::max(need, (size_t)w);

@@ -273,30 +273,53 @@ __device__ __forceinline__ uint16_t pb_elem(int e) {
   return (uint16_t)((r << 8) | c);
 }
 
+// one complex value of lane `src` to the whole warp
+__device__ __forceinline__ float2 shfl_c(float2 v, int src) {
+  return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+__device__ __forceinline__ double2 shfl_c(double2 v, int src) {
+  return make_double2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+__device__ __forceinline__ dfc shfl_c(dfc v, int src) {
+  dfc r;
+  r.x.hi = __shfl_sync(0xffffffffu, v.x.hi, src);
+  r.x.lo = __shfl_sync(0xffffffffu, v.x.lo, src);
+  r.y.hi = __shfl_sync(0xffffffffu, v.y.hi, src);
+  r.y.lo = __shfl_sync(0xffffffffu, v.y.lo, src);
+  return r;
+}
+
 // Unpivoted LDL^T of pivot block jb of the tile in precision C, and the FP32
 // inverse N = L^{-1} of its unit-lower factor built alongside (N <- E_j N for
-// the elimination E_j of column j: rows r > j of N lose l_rj times row j).  Per
-// column j: the rows below scale their entry (one barrier), then every thread
-// updates its elements of the trailing triangle (precision C) and of N (FP32),
-// the owner of (j+1, j+1) also forming the next reciprocal pivot (one barrier).
-// Each thread owns at most two trailing elements (a column-descending
-// enumeration, so the elements with c > j are e < (31 - j)(32 - j) / 2) and
-// the row r = tid / 8 of N at columns tid % 8 + 8 m.
+// the elimination E_j of column j: rows r > j of N lose l_rj times row j).
+// Right-looking with a look-ahead of one column, one barrier per column:
+// while warps 1-7 apply column j to the columns c >= j + 2 (and to N), warp 0
+// applies it to column j + 1 alone, lane r holding row r, and factors that
+// column at once (the pivot reaches every lane by shuffles, each lane forms
+// the reciprocal itself and scales its entry), so the chain from one pivot to
+// the next is one update, one reciprocal and one scaling inside a warp.  The
+// unscaled column (w) and its FP32 scaled copy (lcol) are double-buffered:
+// warps 1-7 read column j's while warp 0 writes column j + 1's.  Each thread
+// of warps 1-7 owns at most three trailing elements (a column-descending
+// enumeration: the elements with c > j + 1 are e < (30 - j)(31 - j) / 2) and
+// the row r = t / 7 of N at columns t % 7 + 7 m (t = tid - 32).
 template <typename C>
-__device__ void factor_pivot32(float2* a, int jb, C* ap, C* w, float2* lcol, C* rinv, float2* li) {
-  const int tid = threadIdx.x;
-  int er[2], ec[2], erc[2], er0[2];
+__device__ void factor_pivot32(float2* a, int jb, C* ap, C* w, float2* lcol, float2* li) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  constexpr int kW = 224;   // threads of warps 1-7
+  int er[3], ec[3], erc[3], er0[3];
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int e = tid + h * 256;
-    const uint16_t rc = e < PB * (PB - 1) / 2 ? pb_elem(e) : (uint16_t)0;
+  for (int h = 0; h < 3; ++h) {
+    const int e = (tid - 32) + h * kW;
+    const bool has = warp > 0 && e < PB * (PB - 1) / 2;
+    const uint16_t rc = has ? pb_elem(e) : (uint16_t)0;
     er[h] = rc >> 8;
-    ec[h] = e < PB * (PB - 1) / 2 ? (rc & 255) : -1;   // -1: no element
+    ec[h] = has ? (rc & 255) : -1;   // -1: no element
     erc[h] = tri(er[h], ec[h] < 0 ? 0 : ec[h]);
     er0[h] = tri(er[h], 0);
   }
-  const int nr = tid >> 3, nq = tid & 7;          // this thread's row of N and first column
-  const int nbase = tri(jb + nr, jb);             // N[nr][q] at li[nbase + q]
+  const int nt = tid - 32, nr = nt / 7, nq = nt - 7 * (nt / 7);   // N row and first column (warps 1-7)
+  const int nbase = tri(jb + nr, jb);                                 // N[nr][q] at li[nbase + q]
   for (int idx = tid; idx < PB * PB; idx += blockDim.x) {
     const int i = idx / PB, c = idx % PB;
     if (c <= i) {
@@ -305,35 +328,49 @@ __device__ void factor_pivot32(float2* a, int jb, C* ap, C* w, float2* lcol, C* 
     }
   }
   __syncthreads();
-  if (tid == 0) *rinv = crcp(ap[0]);
+  if (warp == 0) {   // column 0
+    const C rv = crcp(ap[0]);
+    if (lane > 0) {
+      const C v = ap[tri(lane, 0)];
+      const C l = cmul(v, rv);
+      w[lane] = v;
+      ap[tri(lane, 0)] = l;
+      lcol[lane] = cconv<float2>(l);
+    }
+  }
   __syncthreads();
   for (int j = 0; j < PB - 1; ++j) {
-    if (tid > j && tid < PB) {
-      const C v = ap[tri(tid, j)];
-      const C l = cmul(v, *rinv);
-      w[tid] = v;
-      ap[tri(tid, j)] = l;
-      lcol[tid] = cconv<float2>(l);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-      if (ec[h] > j) {
-        const C v = cfms(ap[er0[h] + j], w[ec[h]], ap[erc[h]]);
-        ap[erc[h]] = v;
-        if (ec[h] == j + 1 && er[h] == j + 1) *rinv = crcp(v);
+    const int cur = (j & 1) * PB, nxt = PB - cur;   // buffers of columns j and j + 1
+    if (warp == 0) {
+      // column j + 1: update by column j, then the pivot and the scaled column
+      C v = ap[tri(lane, 0)];   // placeholder for lanes above the column
+      if (lane > j) v = cfms(ap[tri(lane, j)], w[cur + j + 1], ap[tri(lane, j + 1)]);
+      const C d = shfl_c(v, j + 1);
+      if (lane == j + 1) ap[tri(lane, lane)] = v;
+      if (lane > j + 1) {
+        const C l = cmul(v, crcp(d));
+        w[nxt + lane] = v;
+        ap[tri(lane, j + 1)] = l;
+        lcol[nxt + lane] = cconv<float2>(l);
       }
-    if (nr > j) {
-      const float2 l = lcol[nr];
-      const int jrow = tri(jb + j, jb);
+    } else {
 #pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const int q = nq + 8 * m;
-        if (q <= j) li[nbase + q] = cfms(l, li[jrow + q], li[nbase + q]);
+      for (int h = 0; h < 3; ++h)
+        if (ec[h] > j + 1) ap[erc[h]] = cfms(ap[er0[h] + j], w[cur + ec[h]], ap[erc[h]]);
+      if (nr > j && nr < PB) {
+        const float2 l = lcol[cur + nr];
+        const int jrow = tri(jb + j, jb);
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+          const int q = nq + 7 * m;
+          if (q <= j) li[nbase + q] = cfms(l, li[jrow + q], li[nbase + q]);
+        }
       }
     }
     __syncthreads();
   }
+  // the last column of N: rows r > 30 lose l_{r,30} times row 30 -- done in
+  // the loop; write the factor back
   for (int idx = tid; idx < PB * PB; idx += blockDim.x) {
     const int i = idx / PB, c = idx % PB;
     if (c <= i) a[tri(jb + i, jb + c)] = cconv<float2>(ap[tri(i, c)]);
@@ -387,7 +424,7 @@ __device__ void inv_unit_lower32(const float2* a, int jb, float2* li) {
 }
 
 template <typename C>
-__global__ void __launch_bounds__(256, 1) k_diag_mx(float2* pool, const FrontDev* fr, const int32_t* fids, int k,
+__global__ void __launch_bounds__(256, 3) k_diag_mx(float2* pool, const FrontDev* fr, const int32_t* fids, int k,
                                                  DevStatus* st, float2* linv, uint8_t* piv, int sel) {
   __shared__ float2 a[T * (T + 1) / 2];
   __shared__ float2 li[T * (T + 1) / 2];   // L_kk^{-1}, packed lower
@@ -397,9 +434,8 @@ __global__ void __launch_bounds__(256, 1) k_diag_mx(float2* pool, const FrontDev
   __shared__ __align__(16) unsigned char ap_raw[kApBytes > kX21Bytes ? kApBytes : kX21Bytes];
   C* ap = reinterpret_cast<C*>(ap_raw);
   float2 (*x21)[PB + 1] = reinterpret_cast<float2 (*)[PB + 1]>(ap_raw);
-  __shared__ C w[PB];
-  __shared__ C rinv;
-  __shared__ float2 lcol[PB];    // the scaled column of the current pivot, FP32, for N
+  __shared__ C w[2 * PB];         // unscaled pivot columns (two buffers)
+  __shared__ float2 lcol[2 * PB];  // the scaled columns, FP32, for N (two buffers)
   __shared__ float2 d1inv[PB];   // D1^{-1}: (D1^{-1} x)_c = d1inv[c] x_c + g1[c] x_{q1[c]}
   // restricted Bunch-Kaufman (fronts that pivot): 2x2 column, permutation, 2x2
   // off-diagonals; in precision C, or FP64 (unused) for the double-float form,
@@ -425,7 +461,7 @@ __global__ void __launch_bounds__(256, 1) k_diag_mx(float2* pool, const FrontDev
   if (threadIdx.x < 2) cnt[threadIdx.x] = 0;
   __syncthreads();
   if (pv) factor_pivot32_any_bk<C, CB>(a, 0, ap, w, w1, perm, dsup, cnt);
-  else factor_pivot32<C>(a, 0, ap, w, lcol, &rinv, li);
+  else factor_pivot32<C>(a, 0, ap, w, lcol, li);
   // D1^{-1} (from the precision-C factor while ap still holds it) and N11
   if (threadIdx.x < PB) {
     const int c = threadIdx.x;
@@ -509,7 +545,7 @@ __global__ void __launch_bounds__(256, 1) k_diag_mx(float2* pool, const FrontDev
     __syncthreads();
     if (threadIdx.x < PB) perm[PB + threadIdx.x] += PB;
   } else {
-    factor_pivot32<C>(a, PB, ap, w, lcol, &rinv, li);
+    factor_pivot32<C>(a, PB, ap, w, lcol, li);
   }
   // N22 (formed with the factor when unpivoted), then N21 = -N22 (L21 N11) through x21 = L21 N11
   if (pv) inv_unit_lower32(a, PB, li);
