@@ -702,7 +702,7 @@ __global__ void __launch_bounds__(256) k_trsm_mx(float2* pool, const FrontDev* f
 // SM), the accumulator in TMEM; then L_ik = X D_k^{-1} and the operand
 // images of the trailing update, as k_trsm_mx.  256 threads; warps 0-3 drain TMEM.
 constexpr int kTrsmTcSmem = tc::kImage + 1024;   // A and B images of one K half (later X), 1024-aligned
-__global__ void __launch_bounds__(256, 1) k_trsm_tc(float2* pool, const FrontDev* fr, const Task* tasks, int k,
+__global__ void __launch_bounds__(256, 3) k_trsm_tc(float2* pool, const FrontDev* fr, const Task* tasks, int k,
                                                     DevStatus* st, const float2* linv, unsigned char* ws,
                                                     const uint8_t* piv) {
   extern __shared__ __align__(1024) unsigned char tc_raw[];
