@@ -323,9 +323,12 @@ def time_form(p, precision, args, torch, stream, steps, warmup, e2e=True, autotu
                                sparse_min=args.sparse_min)
     sched = None
     if precision == "mixed" and args.schedule:
-        panels, ahead, reserve = (int(x) for x in args.schedule.split(","))
-        s.set_schedule(panels, ahead, reserve)
-        sched = {"update_panels": panels, "ahead_fronts": ahead, "reserve_sms": reserve, "set": True}
+        vals = [int(x) for x in args.schedule.split(",")]
+        panels, ahead, reserve = vals[:3]
+        split = vals[3] if len(vals) > 3 else 0
+        s.set_schedule(panels, ahead, reserve, split)
+        sched = {"update_panels": panels, "ahead_fronts": ahead, "reserve_sms": reserve, "split_sms": split,
+                 "set": True}
     elif precision == "mixed" and autotune and not args.no_autotune:
         sched = s.autotune(repeats=2)      # untimed: picks the factor schedule for this workload
     f_host = dd.stacked_loads(p)
@@ -577,8 +580,8 @@ def main():
     ap.add_argument("--update-panels", type=int, default=2, choices=[1, 2, 4],
                     help="mixed form: panels fused per tensor-core trailing-update pass")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default factor schedule")
-    ap.add_argument("--schedule", default="", help="PANELS,AHEAD_FRONTS,RESERVE_SMS: set this factor schedule "
-                                                   "instead of autotuning")
+    ap.add_argument("--schedule", default="", help="PANELS,AHEAD_FRONTS,RESERVE_SMS[,SPLIT_SMS]: set this factor "
+                                                   "schedule instead of autotuning")
     ap.add_argument("--sparse-min", type=int, default=0,
                     help="domains of at least this many unknowns are factored as nested-dissection front trees "
                          "(0: every domain one dense front)")

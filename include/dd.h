@@ -158,6 +158,11 @@ typedef struct {
   int32_t reserve_sms;    /* SMs the look-ahead update leaves to the panel chain */
   double factor_ms;       /* dd_autotune: device time of one dd_factor with this schedule */
   int32_t configs_tried;  /* dd_autotune: schedules timed */
+  int32_t split_sms;      /* 0: the leaf level (the domain fronts) as one launch sequence; 1..120: as
+                             two halves of about equal work on two streams, every trailing update of
+                             a half leaving this many SMs to the other half's panel chain, so that
+                             one half's bandwidth-bound panels overlap the other's tensor-core
+                             updates */
 } dd_schedule;
 
 /* Fill `opt` with defaults (FP64, no tree, default stream, device 0). */
@@ -180,7 +185,8 @@ int dd_setup(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t n
 int dd_set_values(dd_handle* h, const dd_c128* vals);
 
 /* Set the schedule of the tensor-core path (update_panels 1, 2 or 4, ahead_fronts
- * in [0, 1024], reserve_sms in [0, 64]); factor_ms and configs_tried are ignored.
+ * in [0, 1024], reserve_sms in [0, 64], split_sms in [0, 120]); factor_ms and
+ * configs_tried are ignored.
  * The factors already computed stay valid; the next dd_factor uses the new
  * schedule.  No effect in the FP64 form or with simt_update.
  * DD_ERR_INVALID_ARG for values out of range. */
@@ -188,9 +194,11 @@ int dd_set_schedule(dd_handle* h, const dd_schedule* sched);
 
 /* Autotuner: times dd_factor (the minimum over `repeats` runs each) under every
  * schedule of the grid update_panels {1, 2, 4} x ahead_fronts {0, 8, 32, 128, 1024} x
- * reserve_sms {8, 16, 32} (look-ahead off: reserve not varied), keeps the
- * fastest for this handle and returns it in *out; the handle is left factored
- * with it.  FP64 form / simt_update: one dd_factor, configs_tried = 1.
+ * reserve_sms {8, 16, 32} (look-ahead off: reserve not varied) with split_sms 0,
+ * then the best of those with split_sms {24, 40, 64} (when the leaf level has
+ * two fronts or more), keeps the fastest for this handle and returns it in
+ * *out; the handle is left factored with it.  FP64 form / simt_update: one
+ * dd_factor, configs_tried = 1.
  * Errors: as dd_factor; DD_ERR_INVALID_ARG for repeats < 1 or out == NULL. */
 int dd_autotune(dd_handle* h, int32_t repeats, dd_schedule* out);
 

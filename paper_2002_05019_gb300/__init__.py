@@ -68,7 +68,7 @@ class Stats(C.Structure):
 
 class Schedule(C.Structure):
     _fields_ = [("update_panels", C.c_int32), ("ahead_fronts", C.c_int32), ("reserve_sms", C.c_int32),
-                ("factor_ms", C.c_double), ("configs_tried", C.c_int32)]
+                ("factor_ms", C.c_double), ("configs_tried", C.c_int32), ("split_sms", C.c_int32)]
 
 
 EXPORTS = ["dd_default_options", "dd_setup", "dd_set_values", "dd_factor", "dd_solve", "dd_solve_subset", "dd_get_schur",
@@ -391,8 +391,8 @@ class Solver:
         _check(_lib.dd_autotune(self._h, int(repeats), C.byref(sc)), "dd_autotune")
         return {k: getattr(sc, k) for k, _ in Schedule._fields_}
 
-    def set_schedule(self, update_panels: int, ahead_fronts: int, reserve_sms: int):
-        sc = Schedule(int(update_panels), int(ahead_fronts), int(reserve_sms), 0.0, 0)
+    def set_schedule(self, update_panels: int, ahead_fronts: int, reserve_sms: int, split_sms: int = 0):
+        sc = Schedule(int(update_panels), int(ahead_fronts), int(reserve_sms), 0.0, 0, int(split_sms))
         _check(_lib.dd_set_schedule(self._h, C.byref(sc)), "dd_set_schedule")
 
     def solve_subset(self, f, domains, allow_not_converged: bool = False):

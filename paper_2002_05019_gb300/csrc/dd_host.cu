@@ -208,6 +208,9 @@ struct dd_handle {
   // schedule knobs of the tensor-core path (dd_autotune picks them)
   int ahead_fronts = 32;           // look-ahead on levels with at most this many fronts (0: off)
   int reserve_sms = 16;            // SMs the look-ahead leaves to the panel chain
+  int split_sms = 0;               // > 0: the leaf level as two halves on two streams, each update
+                                   // leaving this many SMs to the other half's panel chain
+  std::vector<Level> halves;       // the leaf level's fronts in two halves of about equal work
   int32_t *d_flag_f = nullptr, *d_flag_b = nullptr;
   int64_t n_tiles = 0;
   int epoch = 0;
@@ -1035,6 +1038,25 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
       h->levels[height[x]].ids.push_back(x);
       if (h->fronts[x].kind == 1) h->levels[height[x]].n_aux++;
     }
+  // the leaf level in two halves of about equal work (front work ~ ld^3, each
+  // front to the lighter half, largest first) for the split schedule, whose
+  // halves run on two streams; their task lists are built with the levels'
+  // below and they use the leaf level's image offsets
+  h->halves.clear();
+  if (h->use_tc && !h->levels.empty() && h->levels[0].ids.size() >= 2) {
+    std::vector<int32_t> ord = h->levels[0].ids;
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) { return h->fronts[a].ld > h->fronts[b].ld; });
+    h->halves.assign(2, Level{});
+    double wk[2] = {0.0, 0.0};
+    for (int32_t f : ord) {
+      const int q = wk[0] <= wk[1] ? 0 : 1;
+      const double ld = h->fronts[f].ld;
+      h->halves[q].ids.push_back(f);
+      if (h->fronts[f].kind == 1) h->halves[q].n_aux++;
+      wk[q] += ld * ld * ld;
+    }
+    for (Level& Hf : h->halves) std::sort(Hf.ids.begin(), Hf.ids.end());
+  }
   // mixed form: panel image workspace, reused level after level
   if (h->use_tc) {
     // slots 0 and 1 hold the images of even / odd panels of every level; the
@@ -1082,7 +1104,11 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
     }
     return ng;
   };
-  for (auto& L : h->levels) {
+  std::vector<Level*> gen;   // the levels, then the leaf level's halves
+  for (auto& L : h->levels) gen.push_back(&L);
+  for (auto& L : h->halves) gen.push_back(&L);
+  for (Level* Lp : gen) {
+    Level& L = *Lp;
     L.ids_off = (int64_t)h_level_ids.size();
     h_level_ids.insert(h_level_ids.end(), L.ids.begin(), L.ids.end());
     int max_steps = 0;
@@ -1413,6 +1439,7 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
   {
     int nl = 0;
     for (auto& L : h->levels) nl += 2 * (int)L.steps.size();
+    for (auto& L : h->halves) nl += 2 * (int)L.steps.size();
     h->n_counters = std::max(nl, 1);
     DD_CUDA(A.alloc(&h->d_counters, (size_t)h->n_counters));
   }
@@ -1534,17 +1561,19 @@ static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& n
   DD_CUDA(mark(DD_K_INIT, false));
   count(DD_K_INIT, 1);
   count(DD_K_INIT, h->n_scatter > 0 ? 1 : 0);
-  for (size_t l = 0; l < h->levels.size(); ++l) {
-    const Level& L = h->levels[l];
+  // one level on stream s, or one half of the leaf level (split: no
+  // look-ahead, and every update leaves split_sms SMs to the other half's
+  // panel chain on the other stream)
+  auto run_level = [&](const Level& L, const cudaStream_t s, bool assemble, bool split) -> int {
     const int32_t* ids = h->d_level_ids + L.ids_off;
     const int n = (int)L.ids.size();
-    if (l > 0) {
-      DD_CUDA(mark(DD_K_ASSEMBLE, true));
+    if (assemble) {
+      DD_CUDA(mark_on(DD_K_ASSEMBLE, true, s));
       ddk::launch_assemble(p, h->pool, h->d_fronts, ids, n, h->d_imaps, L.max_ld, s);
       ddk::launch_node_init(p, h->pool, h->d_fronts, ids, n, s);
       ddk::launch_extend_add(p, h->pool, h->d_fronts, ids, n, 0, h->d_maps, L.max_child_nu, s);
       ddk::launch_extend_add(p, h->pool, h->d_fronts, ids, n, 1, h->d_maps, L.max_child_nu, s);
-      DD_CUDA(mark(DD_K_ASSEMBLE, false));
+      DD_CUDA(mark_on(DD_K_ASSEMBLE, false, s));
       count(DD_K_ASSEMBLE, L.max_ld > 0 ? n : 0);
       count(DD_K_ASSEMBLE, n);
       count(DD_K_ASSEMBLE, n);
@@ -1557,8 +1586,9 @@ static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& n
     // one-step look-ahead on levels with few fronts: the main stream updates
     // only the next panel columns and factors those panels, while the second
     // stream applies the rest of the trailing update
-    const bool ahead = h->use_tc && L.ahead && (int)L.ids.size() <= h->ahead_fronts && L.steps.size() > 1;
+    const bool ahead = h->use_tc && L.ahead && (int)L.ids.size() <= h->ahead_fronts && L.steps.size() > 1 && !split;
     const int reserve = ahead ? h->reserve_sms : 0;   // SMs left free for the panel chain
+    const int capn = split ? h->split_sms : 0;        // main-stream updates: SMs left to the other half
     // image slot of panel k: even / odd panels alternate, the look-ahead levels over four slots
     // four-panel passes (slots k & 3, or k & 7 with look-ahead)
     const bool quad = h->quad_panels && !L.quads.empty();
@@ -1567,7 +1597,7 @@ static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& n
     };
     auto panel = [&](const StepRange& R) -> cudaError_t {
       unsigned char* ws = h->use_tc ? wsp(R.k) : nullptr;
-      cudaError_t e = mark(DD_K_DIAG, true);
+      cudaError_t e = mark_on(DD_K_DIAG, true, s);
       if (e != cudaSuccess) return e;
       if (p == 0)
         ddk::launch_diag(p, 0, h->pool, h->d_fronts, h->d_diag_ids + R.diag_off, R.n_diag, R.k, h->d_status, s,
@@ -1575,8 +1605,8 @@ static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& n
       else
         ddk::launch_diag_mx(diag64, h->pool, h->d_fronts, h->d_diag_ids + R.diag_off, R.n_diag, R.k, h->d_status,
                             h->d_linv, s, h->d_piv);
-      if ((e = mark(DD_K_DIAG, false)) != cudaSuccess) return e;
-      if ((e = mark(DD_K_TRSM, true)) != cudaSuccess) return e;
+      if ((e = mark_on(DD_K_DIAG, false, s)) != cudaSuccess) return e;
+      if ((e = mark_on(DD_K_TRSM, true, s)) != cudaSuccess) return e;
       if (p == 0)
         ddk::launch_trsm(p, h->pool, h->d_fronts, h->d_trsm + R.trsm_off, R.n_trsm, R.k, h->d_status, s, nullptr,
                          h->d_piv);
@@ -1586,7 +1616,7 @@ static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& n
       count(DD_K_DIAG, R.n_diag);
       if (p == 1 && diag64 == 2) count(DD_K_DIAG, R.n_diag);
       count(DD_K_TRSM, R.n_trsm);
-      return mark(DD_K_TRSM, false);
+      return mark_on(DD_K_TRSM, false, s);
     };
     // trailing update of step R.k, tasks [first, first + n) of its lists, on stream `on`
     auto update = [&](const StepRange& R, bool next_part, cudaStream_t on, int cap) -> cudaError_t {
@@ -1638,19 +1668,19 @@ static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& n
       const QuadRange& Q = L.quads[q0 / 4];
       cudaError_t e;
       if ((e = panel(L.steps[q0])) != cudaSuccess) return e;
-      if ((e = update(L.steps[q0], true, s, 0)) != cudaSuccess) return e;      // column k + 1
+      if ((e = update(L.steps[q0], true, s, capn)) != cudaSuccess) return e;      // column k + 1
       if ((e = panel(L.steps[q0 + 1])) != cudaSuccess) return e;
-      if ((e = quad_update(Q, 0, s, 0)) != cudaSuccess) return e;               // columns k + 2, k + 3
+      if ((e = quad_update(Q, 0, s, capn)) != cudaSuccess) return e;               // columns k + 2, k + 3
       if ((e = panel(L.steps[q0 + 2])) != cudaSuccess) return e;
-      if ((e = update(L.steps[q0 + 2], true, s, 0)) != cudaSuccess) return e;  // column k + 3, panel k + 2
+      if ((e = update(L.steps[q0 + 2], true, s, capn)) != cudaSuccess) return e;  // column k + 3, panel k + 2
       return panel(L.steps[q0 + 3]);
     };
     const size_t ns = L.steps.size();
     if (!h->use_tc || (!h->pair_panels && !ahead)) {
       for (const StepRange& R : L.steps) {
         DD_CUDA(panel(R));
-        DD_CUDA(update(R, true, s, 0));
-        DD_CUDA(update(R, false, s, 0));
+        DD_CUDA(update(R, true, s, capn));
+        DD_CUDA(update(R, false, s, capn));
       }
     } else if (!h->pair_panels) {
       // one panel per update pass: the rest of step k on the second stream
@@ -1662,7 +1692,7 @@ static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& n
         DD_CUDA(cudaStreamWaitEvent(h->s2, h->ev_panel, 0));
         DD_CUDA(update(R, false, h->s2, reserve));            // columns >= k + 2
         DD_CUDA(cudaEventRecord(h->ev_rest, h->s2));
-        DD_CUDA(update(R, true, s, 0));                       // column k + 1
+        DD_CUDA(update(R, true, s, capn));                       // column k + 1
         if (q + 1 < ns) {
           DD_CUDA(panel(L.steps[q + 1]));
           DD_CUDA(cudaEventRecord(h->ev_panel, s));
@@ -1689,7 +1719,7 @@ static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& n
           DD_CUDA(cudaStreamWaitEvent(h->s2, h->ev_panel, 0));
           DD_CUDA(quad_update(Q, 3, h->s2, reserve));          // columns >= k + 8
           DD_CUDA(cudaEventRecord(h->ev_rest, h->s2));
-          DD_CUDA(quad_update(Q, 2, s, 0));                    // columns k + 4 .. k + 7
+          DD_CUDA(quad_update(Q, 2, s, capn));                    // columns k + 4 .. k + 7
           if (q + 7 < ns) DD_CUDA(quad_panels(q + 4));
         }
         DD_CUDA(cudaStreamWaitEvent(s, h->ev_rest, 0));
@@ -1699,19 +1729,19 @@ static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& n
         if (q + 3 < ns) {
           const QuadRange& Q = L.quads[q / 4];
           DD_CUDA(quad_panels(q));
-          DD_CUDA(quad_update(Q, 1, s, 0));                    // columns >= k + 4
+          DD_CUDA(quad_update(Q, 1, s, capn));                    // columns >= k + 4
           q += 4;
         } else {
           DD_CUDA(panel(R));
-          DD_CUDA(update(R, true, s, 0));
+          DD_CUDA(update(R, true, s, capn));
           if (q + 1 < ns) {
             const PairRange& P = L.pairs[q / 2];
             DD_CUDA(panel(L.steps[q + 1]));
-            DD_CUDA(pair_update(P, true, s, 0));
-            DD_CUDA(pair_update(P, false, s, 0));
+            DD_CUDA(pair_update(P, true, s, capn));
+            DD_CUDA(pair_update(P, false, s, capn));
             q += 2;
           } else {
-            DD_CUDA(update(R, false, s, 0));
+            DD_CUDA(update(R, false, s, capn));
             q += 1;
           }
         }
@@ -1721,15 +1751,15 @@ static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& n
       for (size_t q = 0; q < ns;) {
         const StepRange& R = L.steps[q];
         DD_CUDA(panel(R));
-        DD_CUDA(update(R, true, s, 0));
+        DD_CUDA(update(R, true, s, capn));
         if (q + 1 < ns) {
           const PairRange& P = L.pairs[q / 2];
           DD_CUDA(panel(L.steps[q + 1]));
-          DD_CUDA(pair_update(P, true, s, 0));
-          DD_CUDA(pair_update(P, false, s, 0));
+          DD_CUDA(pair_update(P, true, s, capn));
+          DD_CUDA(pair_update(P, false, s, capn));
           q += 2;
         } else {
-          DD_CUDA(update(R, false, s, 0));
+          DD_CUDA(update(R, false, s, capn));
           q += 1;
         }
       }
@@ -1744,7 +1774,7 @@ static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& n
       DD_CUDA(panel(L.steps[0]));
       for (size_t q = 0; q < ns;) {
         const StepRange& R = L.steps[q];
-        DD_CUDA(update(R, true, s, 0));                       // column k + 1 with panel k
+        DD_CUDA(update(R, true, s, capn));                       // column k + 1 with panel k
         if (q + 1 < ns) {
           const PairRange& P = L.pairs[q / 2];
           DD_CUDA(panel(L.steps[q + 1]));
@@ -1753,7 +1783,7 @@ static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& n
           DD_CUDA(cudaStreamWaitEvent(h->s2, h->ev_panel, 0));
           DD_CUDA(pair_update(P, false, h->s2, reserve));     // columns >= k + 4
           DD_CUDA(cudaEventRecord(h->ev_rest, h->s2));
-          DD_CUDA(pair_update(P, true, s, 0));                // columns k + 2, k + 3
+          DD_CUDA(pair_update(P, true, s, capn));                // columns k + 2, k + 3
           if (q + 2 < ns) DD_CUDA(panel(L.steps[q + 2]));
           q += 2;
         } else {
@@ -1767,6 +1797,22 @@ static int enqueue_factor(dd_handle* h, cudaStream_t s, int& launches, size_t& n
       }
       DD_CUDA(cudaStreamWaitEvent(s, h->ev_rest, 0));
     }
+    return DD_OK;
+  };
+  for (size_t l = 0; l < h->levels.size(); ++l) {
+    if (l == 0 && h->split_sms > 0 && h->halves.size() == 2) {
+      // the leaf level's two halves on the two streams, joined before level 1
+      DD_CUDA(cudaEventRecord(h->ev_panel, s));
+      DD_CUDA(cudaStreamWaitEvent(h->s2, h->ev_panel, 0));
+      int st = run_level(h->halves[0], s, false, true);
+      if (st == DD_OK) st = run_level(h->halves[1], h->s2, false, true);
+      if (st != DD_OK) return st;
+      DD_CUDA(cudaEventRecord(h->ev_rest, h->s2));
+      DD_CUDA(cudaStreamWaitEvent(s, h->ev_rest, 0));
+      continue;
+    }
+    const int st = run_level(h->levels[l], s, l > 0, false);
+    if (st != DD_OK) return st;
   }
   DD_CUDA(cudaGetLastError());
   return DD_OK;
@@ -1837,13 +1883,15 @@ int dd_factor(dd_handle* h) {
 int dd_set_schedule(dd_handle* h, const dd_schedule* sc) {
   if (!h || !sc) return DD_ERR_INVALID_ARG;
   if ((sc->update_panels != 1 && sc->update_panels != 2 && sc->update_panels != 4) || sc->ahead_fronts < 0 ||
-      sc->ahead_fronts > kAheadMaxFronts || sc->reserve_sms < 0 || sc->reserve_sms > 64)
+      sc->ahead_fronts > kAheadMaxFronts || sc->reserve_sms < 0 || sc->reserve_sms > 64 || sc->split_sms < 0 ||
+      sc->split_sms > 120)
     return DD_ERR_INVALID_ARG;
   if (!h->use_tc) return DD_OK;
   h->pair_panels = sc->update_panels >= 2;
   h->quad_panels = sc->update_panels == 4;
   h->ahead_fronts = sc->ahead_fronts;
   h->reserve_sms = sc->reserve_sms;
+  h->split_sms = sc->split_sms;
   if (h->factor_exec) cudaGraphExecDestroy(h->factor_exec);   // recaptured by the next dd_factor
   h->factor_exec = nullptr;
   h->fact_nev = 0;
@@ -1862,7 +1910,8 @@ int dd_autotune(dd_handle* h, int32_t repeats, dd_schedule* out) {
     }
     return DD_OK;
   };
-  dd_schedule cur{h->quad_panels ? 4 : (h->pair_panels ? 2 : 1), h->ahead_fronts, h->reserve_sms, 0.0, 0};
+  dd_schedule cur{h->quad_panels ? 4 : (h->pair_panels ? 2 : 1), h->ahead_fronts, h->reserve_sms, 0.0, 0,
+                  h->split_sms};
   if (!h->use_tc) {
     const int st = time_it(&cur.factor_ms);
     cur.configs_tried = 1;
@@ -1874,7 +1923,7 @@ int dd_autotune(dd_handle* h, int32_t repeats, dd_schedule* out) {
     for (int ahead : {0, 8, 32, 128, 1024})
       for (int reserve : {8, 16, 32}) {
         if (ahead == 0 && reserve != 16) continue;   // no look-ahead: the reserve is unused
-        grid.push_back(dd_schedule{panels, ahead, reserve, 0.0, 0});
+        grid.push_back(dd_schedule{panels, ahead, reserve, 0.0, 0, 0});
       }
   dd_schedule best = cur;
   best.factor_ms = 1e300;
@@ -1884,7 +1933,21 @@ int dd_autotune(dd_handle* h, int32_t repeats, dd_schedule* out) {
     if (st != DD_OK) return st;
     if (c.factor_ms < best.factor_ms) best = c;
   }
-  best.configs_tried = (int32_t)grid.size();
+  // then the split leaf level on top of the best schedule
+  int tried = (int32_t)grid.size();
+  if (h->halves.size() == 2) {
+    const dd_schedule base = best;
+    for (int split : {24, 40, 64}) {
+      dd_schedule c = base;
+      c.split_sms = split;
+      int st = dd_set_schedule(h, &c);
+      if (st == DD_OK) st = time_it(&c.factor_ms);
+      if (st != DD_OK) return st;
+      ++tried;
+      if (c.factor_ms < best.factor_ms) best = c;
+    }
+  }
+  best.configs_tried = tried;
   int st = dd_set_schedule(h, &best);
   if (st == DD_OK) st = dd_factor(h);
   *out = best;

@@ -40,7 +40,8 @@ def _x(p, u):
 
 
 @pytest.mark.parametrize("sched", [(1, 0, 16), (2, 0, 16), (4, 0, 16), (1, 128, 8), (2, 128, 32), (2, 8, 16),
-                                   (2, 1024, 16), (4, 8, 16)])
+                                   (2, 1024, 16), (4, 8, 16), (4, 128, 16, 40), (2, 0, 16, 24), (1, 8, 8, 64),
+                                   (4, 1024, 32, 120)])
 def test_every_schedule_solves(c1, sched):
     p, xo = c1
     s = dd.Solver.from_problem(p, precision="mixed")
@@ -55,12 +56,16 @@ def test_autotune_picks_and_keeps_a_schedule(c1):
     p, xo = c1
     s = dd.Solver.from_problem(p, precision="mixed")
     r = s.autotune(repeats=1)
-    assert r["configs_tried"] == 39 and r["factor_ms"] > 0
+    assert r["configs_tried"] == 39 + 3 and r["factor_ms"] > 0      # the grid, then three leaf splits
+    assert r["split_sms"] in (0, 24, 40, 64)
     assert r["update_panels"] in (1, 2, 4) and r["ahead_fronts"] in (0, 8, 32, 128, 1024)
     u, _ = s.solve(dd.stacked_loads(p))          # factored by the tuner with its choice
     assert rel(_x(p, u), xo) <= TOL
     with pytest.raises(dd.DDError) as e:
         s.set_schedule(3, 0, 16)
+    assert e.value.code == 1
+    with pytest.raises(dd.DDError) as e:
+        s.set_schedule(4, 0, 16, 121)
     assert e.value.code == 1
     s.free()
     f = dd.Solver.from_problem(p, precision="fp64")
