@@ -1107,8 +1107,9 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
   std::vector<Level*> gen;   // the levels, then the leaf level's halves
   for (auto& L : h->levels) gen.push_back(&L);
   for (auto& L : h->halves) gen.push_back(&L);
-  for (Level* Lp : gen) {
-    Level& L = *Lp;
+  for (size_t gi = 0; gi < gen.size(); ++gi) {
+    Level& L = *gen[gi];
+    const bool is_half = gi >= h->levels.size();   // the halves repeat the leaf level's work
     L.ids_off = (int64_t)h_level_ids.size();
     h_level_ids.insert(h_level_ids.end(), L.ids.begin(), L.ids.end());
     int max_steps = 0;
@@ -1183,9 +1184,11 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
       h_tc.insert(h_tc.end(), tc_next.begin(), tc_next.end());
       h_tc.insert(h_tc.end(), tc_rest.begin(), tc_rest.end());
       R.n_diag = (int)((int64_t)h_diag.size() - R.diag_off);
-      h->stats.kernel_flops[DD_K_UPDATE] += upd_flops;
-      h->stats.kernel_flops[DD_K_TRSM] += trsm_flops;
-      h->stats.kernel_flops[DD_K_DIAG] += diag_flops;
+      if (!is_half) {
+        h->stats.kernel_flops[DD_K_UPDATE] += upd_flops;
+        h->stats.kernel_flops[DD_K_TRSM] += trsm_flops;
+        h->stats.kernel_flops[DD_K_DIAG] += diag_flops;
+      }
       R.n_trsm = (int)((int64_t)h_trsm.size() - R.trsm_off);
       R.n_upd = (int)((int64_t)h_updt.size() - R.upd_off);
       R.n_tc = (int)((int64_t)h_tc.size() - R.tc_off);
