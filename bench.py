@@ -565,6 +565,8 @@ def main():
                     help="workload timed in both forms beside the headline (none: skip)")
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of the FP64 form in the comparison")
     ap.add_argument("--fp64-warmup", type=int, default=1)
+    ap.add_argument("--single-form", action="store_true", help="the same as --compare none (kept for the commands "
+                                                                "recorded with earlier profiles)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-domains", type=int, default=64,
@@ -592,6 +594,8 @@ def main():
     ap.add_argument("--refine-tol", type=float, default=1e-11,
                     help="mixed form: stop refinement at this relative correction (1e-11 keeps the error <= 1e-10)")
     args = ap.parse_args()
+    if args.single_form:
+        args.compare = "none"
     if args.impl == "reference":
         return reference_arm(args)
     return ours_arm(args)
