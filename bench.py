@@ -17,8 +17,9 @@ solved with the same factors, and the pivot growth of the factorization.
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload large|batched|plain|medium|many] [--precision mixed|fp64]
 
-With N > 1 (torchrun) every rank solves its own replica (the method has no
-exchange step on one problem that this build shards), scaling "weak".
+With N > 1 (torchrun) every rank solves its own replica (the library runs one
+problem on one GPU; its subtree shard plan, dd_shard_plan, has no GPU
+multi-rank engine), scaling "weak".
 """
 from __future__ import annotations
 
