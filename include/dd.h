@@ -121,6 +121,11 @@ typedef struct {
                                others stay one dense front.  0 (default): every domain is one dense
                                front; negative: DD_ERR_INVALID_ARG */
   int32_t sparse_leaf;      /* largest leaf front of that dissection (0: 256); negative: DD_ERR_INVALID_ARG */
+  const char* tune_cache;   /* optional path of the autotuner's schedule cache (JSON lines, one per
+                               tuned problem and GPU model; see dd_tune_cache_lookup): dd_setup
+                               applies a cached schedule of this problem, dd_autotune returns it
+                               without timing (configs_tried = 0) or tunes and appends one line.
+                               NULL (default): no cache.  The string is copied at setup. */
 } dd_options;
 
 /* Kernel classes of dd_stats.kernel_ms / kernel_launches / kernel_flops. */

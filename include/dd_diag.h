@@ -133,6 +133,27 @@ int dd_domain_assembly(int32_t n, const int32_t* rowptr, const int32_t* colind, 
 int dd_shard_plan(int32_t n_sub, const dd_subdomain* subs, int32_t n_dual, const dd_options* opt, int32_t n_ranks,
                   int32_t max_fronts, int32_t* n_front, int32_t* front_rank, int32_t* rank_root);
 
+/* Autotuner schedule cache (host only, no device).
+ *
+ * dd_tune_key: the problem key under which dd_setup and dd_autotune file a
+ * schedule: a 64-bit FNV-1a hash of dd_symbolic's front tree (parent, ne, nu
+ * of every front, in order), n_dual, opt->precision and opt->pivoting.  Same
+ * arguments as dd_symbolic; *key written on DD_OK; dd_symbolic's errors.
+ * The cache key adds the GPU: "<key as 16 hex digits>:<device name>:<SMs>".
+ *
+ * The cache file holds JSON lines, one per tuned problem and GPU:
+ *   {"key": "...", "update_panels": P, "ahead_fronts": A, "reserve_sms": R,
+ *    "split_sms": S, "factor_ms": T}
+ * dd_tune_cache_lookup: *found = 1 and *out filled (configs_tried = 0) from
+ * the last well-formed line whose key equals `key` and whose values are in
+ * dd_set_schedule's ranges; *found = 0 when there is none or no file.
+ * Returns DD_OK, or DD_ERR_INVALID_ARG for a NULL argument.
+ * dd_tune_cache_store: appends one line for `key` (no '"' or newline in it)
+ * and `*s` in one write; DD_ERR_INVALID_ARG if the file cannot be written. */
+int dd_tune_key(int32_t n_sub, const dd_subdomain* subs, int32_t n_dual, const dd_options* opt, uint64_t* key);
+int dd_tune_cache_lookup(const char* path, const char* key, dd_schedule* out, int32_t* found);
+int dd_tune_cache_store(const char* path, const char* key, const dd_schedule* s);
+
 #ifdef __cplusplus
 }
 #endif

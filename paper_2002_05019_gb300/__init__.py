@@ -50,7 +50,7 @@ class Options(C.Structure):
                 ("pivoting", C.c_int32), ("tree_parent", C.POINTER(C.c_int32)),
                 ("centroids", C.POINTER(C.c_double)), ("cuda_stream", C.c_void_p), ("device", C.c_int32),
                 ("time_kernels", C.c_int32), ("simt_update", C.c_int32), ("update_panels", C.c_int32),
-                ("sparse_min", C.c_int32), ("sparse_leaf", C.c_int32)]
+                ("sparse_min", C.c_int32), ("sparse_leaf", C.c_int32), ("tune_cache", C.c_char_p)]
 
 KERNEL_CLASSES = ["diag", "trsm", "update", "assemble", "init"]
 
@@ -74,7 +74,8 @@ class Schedule(C.Structure):
 EXPORTS = ["dd_default_options", "dd_setup", "dd_set_values", "dd_factor", "dd_solve", "dd_solve_subset", "dd_get_schur",
            "dd_set_schedule", "dd_autotune",
            "dd_get_stats", "dd_strerror", "dd_free", "dd_dense_solve_noalloc", "dd_selftest_wait_timeout",
-           "dd_symbolic", "dd_domain_symbolic", "dd_domain_assembly", "dd_shard_plan", "dd_selftest_pivot_tile"]
+           "dd_symbolic", "dd_domain_symbolic", "dd_domain_assembly", "dd_shard_plan", "dd_selftest_pivot_tile",
+           "dd_tune_key", "dd_tune_cache_lookup", "dd_tune_cache_store"]
 
 
 def library_path() -> str:
@@ -120,6 +121,9 @@ def load(build_if_missing: bool = True):
                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
     lib.dd_shard_plan.argtypes = [C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_int32, C.c_void_p,
                                   C.c_void_p, C.c_void_p]
+    lib.dd_tune_key.argtypes = [C.c_int32, C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(C.c_uint64)]
+    lib.dd_tune_cache_lookup.argtypes = [C.c_char_p, C.c_char_p, C.POINTER(Schedule), C.POINTER(C.c_int32)]
+    lib.dd_tune_cache_store.argtypes = [C.c_char_p, C.c_char_p, C.POINTER(Schedule)]
     lib.dd_dense_solve_noalloc.argtypes = [C.c_int32, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_int64,
                                            C.c_void_p, C.c_int64, C.c_void_p]
     _lib = lib
@@ -272,6 +276,42 @@ def pivot_tile(tile, precision: str = "dfloat"):
     return out, linv
 
 
+def tune_key(subdomains, n_dual: int, precision: str = "mixed", pivoting: int = 0, tree_parent=None,
+             centroids=None) -> int:
+    """The autotuner cache's problem key of a decomposition (dd_tune_key; host only)."""
+    lib = load()
+    subs, opt, keep = _marshal(subdomains, tree_parent, centroids)
+    opt.precision = PRECISION[precision]
+    opt.pivoting = int(pivoting)
+    key = C.c_uint64(0)
+    _check(lib.dd_tune_key(len(subdomains), subs, int(n_dual), C.byref(opt), C.byref(key)), "dd_tune_key")
+    del keep
+    return key.value
+
+
+def tune_key_problem(p, precision: str = "mixed", pivoting: int = 0) -> int:
+    """tune_key() for a femgen.Problem, with its domain tree."""
+    return tune_key(_problem_subs(p), p.n_dual, precision, pivoting, tree_parent=p.rcb.parent)
+
+
+def tune_cache_lookup(path: str, key: str):
+    """The schedule cached under `key` in the cache file (dd_tune_cache_lookup), or None."""
+    lib = load()
+    sc = Schedule()
+    found = C.c_int32(0)
+    _check(lib.dd_tune_cache_lookup(os.fsencode(path), key.encode(), C.byref(sc), C.byref(found)),
+           "dd_tune_cache_lookup")
+    return {k: getattr(sc, k) for k, _ in Schedule._fields_} if found.value else None
+
+
+def tune_cache_store(path: str, key: str, schedule: dict):
+    """Append one schedule line under `key` (dd_tune_cache_store)."""
+    lib = load()
+    sc = Schedule(int(schedule["update_panels"]), int(schedule["ahead_fronts"]), int(schedule["reserve_sms"]),
+                  float(schedule.get("factor_ms", 0.0)), 0, int(schedule.get("split_sms", 0)))
+    _check(lib.dd_tune_cache_store(os.fsencode(path), key.encode(), C.byref(sc)), "dd_tune_cache_store")
+
+
 def shard_plan(subdomains, n_dual: int, n_ranks: int, tree_parent=None, centroids=None) -> dict:
     """Cut of the front tree into n_ranks subtrees (dd_shard_plan; host only):
     the owner rank of every front and the root front of every rank's subtree."""
@@ -303,7 +343,8 @@ class Solver:
     def __init__(self, subdomains, n_dual: int, precision: str = "fp64", refine_tol: float = 1e-13,
                  max_refine: int | None = None, tree_parent=None, centroids=None, stream=None, device: int = 0,
                  time_kernels: bool | int = False, simt_update: bool = False, pivoting: int | None = None,
-                 update_panels: int | None = None, sparse_min: int | None = None, sparse_leaf: int | None = None):
+                 update_panels: int | None = None, sparse_min: int | None = None, sparse_leaf: int | None = None,
+                 tune_cache: str | None = None):
         lib = load()
         subs, opt, self._keep = _marshal(subdomains, tree_parent, centroids)
         self.n = [int(s["n"]) for s in subdomains]
@@ -328,6 +369,8 @@ class Solver:
             opt.sparse_min = int(sparse_min)   # domains of >= sparse_min unknowns: nested-dissection front trees
         if sparse_leaf is not None:
             opt.sparse_leaf = int(sparse_leaf)
+        if tune_cache is not None:
+            opt.tune_cache = os.fsencode(tune_cache)   # schedule cache file (copied by dd_setup)
         self.precision = precision
         h = C.c_void_p()
         _check(lib.dd_setup(C.byref(h), len(subdomains), subs, self.n_dual, C.byref(opt)), "dd_setup")
@@ -458,4 +501,5 @@ def unstack(problem, u: np.ndarray):
 
 __all__ = ["Solver", "DDError", "load", "library_path", "stacked_loads", "unstack", "symbolic", "symbolic_problem",
            "domain_symbolic", "domain_assembly", "shard_plan", "shard_plan_problem", "pivot_tile",
+           "tune_key", "tune_key_problem", "tune_cache_lookup", "tune_cache_store",
            "EXPORTS", "PRECISION"]

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libdd_gb300.so")
 SOURCES = ["dd_host.cu", "kernels_factor.cu", "kernels_solve.cu", "kernels_tc.cu", "dd_noalloc.cu",
-           "dd_domain_symbolic.cu", "dd_shard.cu"]
+           "dd_domain_symbolic.cu", "dd_shard.cu", "dd_tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

@@ -211,6 +211,8 @@ struct dd_handle {
   int split_sms = 0;               // > 0: the leaf level as two halves on two streams, each update
                                    // leaving this many SMs to the other half's panel chain
   std::vector<Level> halves;       // the leaf level's fronts in two halves of about equal work
+  uint64_t tune_key = 0;           // problem key of the schedule cache (front tree, duals, form)
+  std::string tune_cache;          // path of the schedule cache ("": none)
   int32_t *d_flag_f = nullptr, *d_flag_b = nullptr;
   int64_t n_tiles = 0;
   int epoch = 0;
@@ -1314,6 +1316,16 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
     L.n_bwd = (int)((int64_t)h_bwd.size() - L.bwd_off);
   }
 
+  {
+    std::vector<int32_t> ne_k(n_front_all), nu_k(n_front_all), par_k(n_front_all);
+    for (int x = 0; x < n_front_all; ++x) {
+      ne_k[x] = h->fronts[x].ne;
+      nu_k[x] = h->fronts[x].nu;
+      par_k[x] = par[x];
+    }
+    h->tune_key = tune_problem_key(n_front_all, par_k.data(), ne_k.data(), nu_k.data(), n_dual, opt.precision,
+                                   opt.pivoting);
+  }
   if (sym) {
     *sym->n_front = n_front_all;
     if (sym->max_fronts < n_front_all) return DD_ERR_INVALID_ARG;
@@ -1485,6 +1497,16 @@ int setup_impl(dd_handle** out, int32_t n_sub, const dd_subdomain* subs, int32_t
   h->stats.n_primal = h->n_loc;
   h->stats.bytes_factor = bytes_factor;
   h->stats.bytes_device = (int64_t)A.bytes;
+  // a cached schedule of this problem on this GPU model
+  if (opt.tune_cache && opt.tune_cache[0]) {
+    h->tune_cache = opt.tune_cache;
+    dd_schedule sc{};
+    int32_t found = 0;
+    if (h->use_tc &&
+        dd_tune_cache_lookup(opt.tune_cache, tune_cache_key(h->tune_key, h->device).c_str(), &sc, &found) == DD_OK &&
+        found)
+      dd_set_schedule(h.get(), &sc);
+  }
   h->stats.t_setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_begin).count();
   *out = h.release();
   return DD_OK;
@@ -1921,6 +1943,19 @@ int dd_autotune(dd_handle* h, int32_t repeats, dd_schedule* out) {
     *out = cur;
     return st;
   }
+  // a cached schedule of this problem on this GPU model: no timing
+  const std::string ckey = h->tune_cache.empty() ? std::string() : tune_cache_key(h->tune_key, h->device);
+  if (!ckey.empty()) {
+    dd_schedule sc{};
+    int32_t found = 0;
+    if (dd_tune_cache_lookup(h->tune_cache.c_str(), ckey.c_str(), &sc, &found) == DD_OK && found) {
+      int st = dd_set_schedule(h, &sc);
+      if (st == DD_OK) st = dd_factor(h);
+      sc.configs_tried = 0;
+      *out = sc;
+      return st;
+    }
+  }
   std::vector<dd_schedule> grid;
   for (int panels : {1, 2, 4})
     for (int ahead : {0, 8, 32, 128, 1024})
@@ -1953,6 +1988,8 @@ int dd_autotune(dd_handle* h, int32_t repeats, dd_schedule* out) {
   best.configs_tried = tried;
   int st = dd_set_schedule(h, &best);
   if (st == DD_OK) st = dd_factor(h);
+  // an unwritable cache path costs the tuning nothing; the schedule is still returned
+  if (st == DD_OK && !ckey.empty()) dd_tune_cache_store(h->tune_cache.c_str(), ckey.c_str(), &best);
   *out = best;
   return st;
 }

@@ -15,6 +15,7 @@
 //     blocks and eliminates its separator (Section II: block LDL^T of the
 //     block-wise sparse auxiliary matrix, structure from the clique graph).
 #pragma once
+#include <string>
 
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -83,6 +84,12 @@ struct DevStatus {
   unsigned long long n_swap;      // restricted Bunch-Kaufman: symmetric interchanges
   unsigned long long n_2x2;       // restricted Bunch-Kaufman: 2 x 2 pivots
 };
+
+// autotuner schedule cache (dd_tune.cu): the problem key of a front tree and
+// the cache key adding the device's name and SM count
+uint64_t tune_problem_key(int n_front, const int32_t* parent, const int32_t* ne, const int32_t* nu, int n_dual,
+                          int precision, int pivoting);
+std::string tune_cache_key(uint64_t problem_key, int device);
 
 namespace ddk {
 

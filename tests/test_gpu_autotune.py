@@ -71,3 +71,26 @@ def test_autotune_picks_and_keeps_a_schedule(c1):
     f = dd.Solver.from_problem(p, precision="fp64")
     assert f.autotune(repeats=1)["configs_tried"] == 1
     f.free()
+
+
+def test_autotune_schedule_cache(c1, tmp_path):
+    """A tuned schedule is filed under the problem's key and this GPU; a
+    second handle of the same problem gets it at setup, and its autotune
+    returns it without timing."""
+    p, xo = c1
+    path = str(tmp_path / "tune.jsonl")
+    s = dd.Solver.from_problem(p, precision="mixed", tune_cache=path)
+    r = s.autotune(repeats=1)
+    assert r["configs_tried"] == 42
+    s.free()
+    lines = open(path).read().splitlines()
+    assert len(lines) == 1 and ("%016x" % dd.tune_key_problem(p)) in lines[0]
+    t = dd.Solver.from_problem(p, precision="mixed", tune_cache=path)
+    r2 = t.autotune(repeats=1)
+    assert r2["configs_tried"] == 0
+    assert [r2[k] for k in ("update_panels", "ahead_fronts", "reserve_sms", "split_sms")] == \
+           [r[k] for k in ("update_panels", "ahead_fronts", "reserve_sms", "split_sms")]
+    u, _ = t.solve(dd.stacked_loads(p))
+    assert rel(_x(p, u), xo) <= TOL
+    t.free()
+    assert len(open(path).read().splitlines()) == 1     # a hit appends nothing
