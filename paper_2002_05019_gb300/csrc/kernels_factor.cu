@@ -967,6 +967,17 @@ __global__ void __launch_bounds__(256) k_extend_add(S* pool, const FrontDev* fr,
   }
 }
 
+// two consecutive complex entries, one 16-byte store for complex64
+template <typename S>
+__device__ __forceinline__ void store_pair(S* p, S a, S b) {
+  p[0] = a;
+  p[1] = b;
+}
+template <>
+__device__ __forceinline__ void store_pair<float2>(float2* p, float2 a, float2 b) {
+  *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+
 // Assembly of a separator front by pulling (Section II: the auxiliary
 // matrix's blocks are sums of the children's Schur complements): entry (i, j)
 // of the lower-triangular tiles is the sum over the children of their
@@ -997,18 +1008,22 @@ __global__ void __launch_bounds__(256) k_assemble(S* pool, const FrontDev* fr, c
     S* dst = pool + P.off + (int64_t)i * P.ld;
     const int jend = min(P.ld, (i / T + 1) * T);
     const bool pad = i >= P.ne && i < P.ne_pad;
-    for (int j = lane; j < jend; j += 32) {
-      S v = czero<S>();
+    // two columns per lane (jend is a multiple of 64, rows and map offsets
+    // start on multiples of 64 entries, so the pairs are aligned)
+    for (int j = 2 * lane; j < jend; j += 64) {
+      S v0 = czero<S>(), v1 = czero<S>();
       if (j <= i) {
 #pragma unroll
         for (int s = 0; s < 2; ++s)
           if (src[s]) {
-            const int mj = inv[s][j];
-            if (mj >= 0) v = cadd(v, src[s][mj]);
+            const int2 mj = *reinterpret_cast<const int2*>(inv[s] + j);
+            if (mj.x >= 0) v0 = cadd(v0, src[s][mj.x]);
+            if (j + 1 <= i && mj.y >= 0) v1 = cadd(v1, src[s][mj.y]);
           }
-        if (pad && j == i) v = cmake<S>(1, 0);
+        if (pad && j == i) v0 = cmake<S>(1, 0);
+        if (pad && j + 1 == i) v1 = cmake<S>(1, 0);
       }
-      dst[j] = v;
+      store_pair(dst + j, v0, v1);
     }
   }
 }
